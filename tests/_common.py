@@ -1,0 +1,83 @@
+"""Helpers shared by the tests: views of torch tensors as oracle inputs and
+the parity tolerances.
+
+Tolerances (per score, relative, with an absolute floor of Nq * 1e-3 times
+the relative tolerance for scores near zero):
+  * fp16 / bf16 inputs: 1e-3;
+  * fp32 inputs:        1e-5.
+The floor matters only for scores whose magnitude is below Nq * 1e-3; on
+unit-normalised data the scores are O(Nq * 0.2).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+RTOL = {"f16": 1e-3, "bf16": 1e-3, "f32": 1e-5}
+
+
+def oracle_view(t):
+    """(numpy array, oracle dtype code) for a torch CPU tensor."""
+    import torch
+    t = t.detach().cpu().contiguous()
+    if t.dtype == torch.float16:
+        return t.view(torch.int16).numpy().view(np.uint16), oracle.F16
+    if t.dtype == torch.bfloat16:
+        return t.view(torch.int16).numpy().view(np.uint16), oracle.BF16
+    if t.dtype == torch.float32:
+        return t.numpy(), oracle.F32
+    if t.dtype == torch.float64:
+        return t.numpy(), oracle.F64
+    raise TypeError(t.dtype)
+
+
+def oracle_dense(q, tokens, offsets, lengths, cand_ids):
+    qa, qdt = oracle_view(q)
+    ta, tdt = oracle_view(tokens)
+    return oracle.dense_scores(qa, ta, offsets, lengths, cand_ids, qdtype=qdt, tdtype=tdt)
+
+
+def assert_scores_close(got, want, dtype: str, nq: int):
+    """Element-wise parity: NaN where the oracle has NaN, equal infinities,
+    and |got - want| <= rtol * max(|want|, nq * 1e-3) elsewhere."""
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    assert got.shape == want.shape
+    nan_w = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan_w), "NaN pattern differs"
+    inf_w = np.isinf(want)
+    assert np.array_equal(got[inf_w], want[inf_w]), "infinite scores differ"
+    fin = ~(nan_w | inf_w)
+    rtol = RTOL[dtype]
+    bound = rtol * np.maximum(np.abs(want[fin]), nq * 1e-3)
+    err = np.abs(got[fin] - want[fin])
+    if err.size:
+        worst = int(np.argmax(err / bound))
+        assert np.all(err <= bound), (
+            f"max rel-err {err[worst] / max(abs(want[fin][worst]), 1e-30):.3e} "
+            f"at {worst}: got {got[fin][worst]!r} want {want[fin][worst]!r}")
+
+
+def assert_topk_consistent(got_s, got_p, scores_ref, k: int, tol_abs):
+    """Top-k parity against reference scores: the returned positions must be
+    a valid top-k of ``scores_ref`` up to ties within ``tol_abs``.
+
+    * every returned position is distinct and in range (or -1 padding);
+    * the returned list is sorted by the GPU's own scores (desc);
+    * a reference score outside the returned set is never larger than the
+      k-th reference score in the set by more than tol_abs (no candidate
+      that clearly belongs was dropped).
+    """
+    got_p = np.asarray(got_p)
+    n = len(scores_ref)
+    valid = got_p[got_p >= 0]
+    assert len(valid) == min(k, n)
+    assert len(np.unique(valid)) == len(valid)
+    ref = np.asarray(scores_ref, np.float64)
+    ref_nan_last = np.where(np.isnan(ref), -np.inf, ref)
+    chosen = ref_nan_last[valid]
+    if len(valid) < n and len(valid) > 0:
+        mask = np.ones(n, bool)
+        mask[valid] = False
+        assert ref_nan_last[mask].max() <= chosen.min() + tol_abs
