@@ -1,0 +1,156 @@
+/*
+ * tms.h -- C ABI of libtms, GB300 (sm_103a) late-interaction MaxSim scoring.
+ *
+ * The operations are those of the TileMaxSim paper (arxiv 2606.26439):
+ *   - MaxSim (Section 2.1, Eq. 1):  score(Q, D) = sum_i max_j q_i . d_j,
+ *     computed without materialising the Nq x Nd similarity matrix
+ *     (Section 3, Algorithm 3 "V2-MQ"), with the embedding dimension
+ *     tiled into chunks whose partial dot products are summed before the
+ *     max (Section 3, dimension tiling; Section 6.6, Table dim_scaling);
+ *   - the PQ distance table (Section 4.2, Phase 1) and fused PQ scoring
+ *     through it without decompression (Section 4.2, Phase 2);
+ *   - top-k selection after scoring (Section 6.6, end-to-end retrieval).
+ *
+ * Conventions shared by every entry point:
+ *   - All array arguments are DEVICE pointers on the current CUDA device,
+ *     unless stated otherwise.  The caller owns every buffer; the library
+ *     allocates no per-call memory.
+ *   - Work is enqueued on `stream` and returns without synchronising
+ *     (tms_get_device_error is the one call that synchronises).
+ *   - Errors are returned, never thrown.  Host-side argument checks return
+ *     TMS_ERR_INVALID_ARG or TMS_ERR_UNSUPPORTED before anything is
+ *     enqueued; a failed launch returns TMS_ERR_CUDA.
+ *   - Data errors found on the device never fault: the affected score is
+ *     written as NaN and a bit is set in the per-device error word that
+ *     tms_get_device_error reads and clears.
+ *   - Documents are packed: document `id` owns rows
+ *     [doc_offsets[id], doc_offsets[id] + doc_lengths[id]) of a row-major
+ *     [n_tokens][d] token array.  A document of length 0 scores -inf.
+ *   - Candidate lists of n_queries queries are given in CSR form:
+ *     query q scores cand_ids[cand_offsets[q] .. cand_offsets[q+1]),
+ *     cand_offsets is non-decreasing with cand_offsets[0] = 0 and
+ *     cand_offsets[n_queries] = n_cand, and the score of the candidate at
+ *     flat position c is written to out_scores[c].
+ *   - Scores are fp32, accumulated in fp32.  Each score is written exactly
+ *     once, by one owner, in a fixed summation order: results are bitwise
+ *     reproducible run to run.
+ */
+#ifndef TMS_H
+#define TMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+    TMS_OK = 0,
+    TMS_ERR_INVALID_ARG = -1, /* a size, pointer or alignment check failed  */
+    TMS_ERR_UNSUPPORTED = -2, /* valid, but outside this build's limits     */
+    TMS_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed        */
+    TMS_ERR_DEVICE_FLAG = -5, /* tms_get_device_error found flags set       */
+    TMS_ERR_TIMEOUT = -6      /* a bounded device-side wait ran out         */
+} tms_status;
+
+typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
+
+/* Bits of the per-device error word (see tms_get_device_error). */
+#define TMS_DEVERR_BAD_ID 1u      /* candidate id outside [0, n_docs)          */
+#define TMS_DEVERR_BAD_RANGE 2u   /* negative length/offset or rows past n_tokens */
+#define TMS_DEVERR_TIMEOUT 4u     /* a pipeline wait exceeded its budget       */
+#define TMS_DEVERR_BAD_CSR 8u     /* cand_offsets[n_queries] != n_cand         */
+
+/*
+ * Dense MaxSim (Eq. 1) of n_queries queries over their candidate lists.
+ *
+ *   queries      [n_queries][nq][d] of `dtype`, row-major.
+ *   doc_tokens   [n_tokens][d] of `dtype`, row-major, packed documents.
+ *   doc_offsets  [n_docs] int64 first row;  doc_lengths [n_docs] int32.
+ *   cand_ids     [n_cand] int32 document ids;  cand_offsets [n_queries+1].
+ *   out_scores   [n_cand] fp32.
+ *
+ * Limits: 1 <= nq <= 128; 8 <= d <= 1024 with d % 8 == 0 (16-byte rows);
+ * 1 <= n_queries <= 4096; n_tokens < 2^31; queries, doc_tokens and every
+ * index array 16-byte aligned.  fp16/bf16 run on the tensor cores
+ * (tcgen05, fp32 accumulation in tensor memory); fp32 runs on an exact
+ * fp32 path.  A candidate with a bad id or row range scores NaN and sets
+ * TMS_DEVERR_BAD_ID / TMS_DEVERR_BAD_RANGE.
+ */
+tms_status tms_score_dense(const void *queries, tms_dtype dtype, int n_queries, int nq, int d,
+                           const void *doc_tokens, int64_t n_tokens,
+                           const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                           const int32_t *cand_ids, const int64_t *cand_offsets, int64_t n_cand,
+                           float *out_scores, cudaStream_t stream);
+
+/*
+ * PQ distance table (Section 4.2, Phase 1):
+ *   lut[q][i][mm][kk] = sum_{t < d/m} queries[q][i][mm*(d/m) + t] * codebook[mm][kk][t]
+ * computed in fp32 with fused multiply-adds in ascending t.
+ *
+ *   queries  [n_queries][nq][d] of qdtype;  codebook [m][k][d/m] fp32.
+ *   lut      [n_queries][nq][m][k] fp32 (output).
+ *
+ * Limits: d % m == 0, 1 <= m <= 64, 1 <= k <= 256, 1 <= nq <= 128.
+ */
+tms_status tms_build_pq_lut(const void *queries, tms_dtype qdtype, int n_queries, int nq, int d,
+                            const float *codebook, int m, int k, float *lut, cudaStream_t stream);
+
+/*
+ * Fused PQ MaxSim (Section 4.2, Phase 2):
+ *   score = sum_i max_j sum_mm lut[q][i][mm][codes[j][mm]]
+ * read straight from the uint8 codes through the table held in shared
+ * memory -- no token is decompressed.
+ *
+ *   lut        [n_queries][nq][m][k] fp32 (from tms_build_pq_lut or any
+ *              caller-built table).
+ *   codes      [n_tokens][m] uint8, packed like doc_tokens.
+ *   other arguments as for tms_score_dense.
+ *
+ * Limits: m in {4, 8, 16, 32}; 1 <= k <= 256 with m*k <= 4096; 1 <= nq <= 128;
+ * codes must be < k (a larger code reads an unspecified table entry but
+ * never faults).  The table is processed in chunks of 8 query tokens; the
+ * chunk partial sums are added in ascending chunk order through out_scores.
+ */
+tms_status tms_score_pq(const float *lut, int n_queries, int nq, int m, int k,
+                        const uint8_t *codes, int64_t n_tokens,
+                        const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                        const int32_t *cand_ids, const int64_t *cand_offsets, int64_t n_cand,
+                        float *out_scores, cudaStream_t stream);
+
+/*
+ * Top-k per query over scores laid out like out_scores above (Section 6.6).
+ *
+ *   scores        [n_cand] fp32, query q's list at cand_offsets[q]..[q+1].
+ *   out_scores    [n_queries][topk] fp32;  out_pos [n_queries][topk] int32:
+ *                 the r-th best score and its position within the query's
+ *                 candidate list (the caller maps positions to ids).
+ *
+ * Order: score descending; equal scores by ascending position; NaN after
+ * every number (-inf included).  Lists shorter than topk are padded with
+ * (-inf, -1).  Limits: 1 <= topk <= 1024, list length < 2^31.
+ */
+tms_status tms_topk(const float *scores, const int64_t *cand_offsets, int n_queries, int topk,
+                    float *out_scores, int32_t *out_pos, cudaStream_t stream);
+
+/*
+ * Read and clear the current device's error word after `stream` drains.
+ * *flags (HOST pointer) receives the TMS_DEVERR_* bits.  Returns
+ * TMS_ERR_DEVICE_FLAG when any bit was set, TMS_OK otherwise.  This call
+ * synchronises `stream`.
+ */
+tms_status tms_get_device_error(cudaStream_t stream, int *flags);
+
+/* Static English text for a status code. */
+const char *tms_status_string(tms_status s);
+
+/* Library ABI version (major * 100 + minor). */
+int tms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMS_H */

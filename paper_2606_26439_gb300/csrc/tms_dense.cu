@@ -1,0 +1,730 @@
+// tms_dense.cu -- dense MaxSim on GB300 (sm_103a).
+//
+// Computes Eq. 1 of the TileMaxSim paper, score = sum_i max_j q_i . d_j,
+// for every candidate of every query, in one persistent launch.
+//
+// fp16 / bf16: a warp-specialised tensor-core kernel.
+//   * Producer warp: reads candidate metadata (id -> offset, length), and
+//     streams each document's token rows from HBM into a ring of shared-
+//     memory stages with 2-D TMA box loads (128-byte swizzle).  One stage
+//     holds one 64-element-wide dimension chunk of up to 128 rows of ONE
+//     document; box heights 128/64/32/16/8 cover the rows with at most 7
+//     rows of over-fetch.  Each token is read from HBM once (Theorem 1
+//     with BQ = Nq).
+//   * MMA warp: one elected thread issues tcgen05.mma (M = 128 document
+//     rows, N = Nq padded to 32, K = 16) over every dimension chunk of a
+//     tile, accumulating the partial dot products in tensor memory before
+//     any max is taken -- the paper's dimension tiling (Section 3), with
+//     the K loop running through TMEM instead of registers.
+//   * Four epilogue warps: each reads its 32 TMEM lanes (document rows)
+//     with tcgen05.ld, masks rows past the document end to -inf (never 0),
+//     and reduces the 32 x 32 block to per-query-token column maxima with
+//     a 31-shuffle transposed butterfly.  Running maxima stay in registers
+//     across a document's tiles; at its end the four warps' maxima meet
+//     in shared memory, one warp sums them over the Nq query tokens in a
+//     fixed order and writes the score once.  The Nq x Nd similarity
+//     matrix never reaches HBM and no atomics or memset are needed.
+//
+// fp32: an exact-fp32 CUDA-core kernel (one warp per candidate, lanes =
+// query tokens, query chunk in registers).
+//
+// Every wait is bounded (see tms_common.cuh); a timeout sets
+// TMS_DEVERR_TIMEOUT and the CTA drains its in-flight copies and MMAs,
+// frees its tensor memory and returns.
+#include <algorithm>
+
+#include "tms_common.cuh"
+#include "tms_internal.h"
+
+namespace tms {
+
+namespace dense {
+
+constexpr int kRows = 128;                    // document rows per tile (MMA M)
+constexpr int kChunkElems = 64;               // elements per dimension chunk (one 128-B swizzle row)
+constexpr int kStageBytes = kRows * 128;      // 16 KB per stage
+constexpr int kInfoRing = 16;
+constexpr int kThreads = 192;                 // 6 warps
+constexpr int kMaxStages = 16;
+constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
+
+enum : int { kFirst = 1, kLast = 2, kEnd = 4 };
+
+struct TileInfo {
+    int f;      // flat candidate index
+    int r;      // valid rows in this tile (1..128)
+    int q;      // query index
+    int flags;  // kFirst / kLast / kEnd
+};
+
+struct Args {
+    const int64_t* offsets;
+    const int32_t* lengths;
+    const int32_t* cand_ids;
+    const int64_t* cand_offsets;
+    float* out;
+    unsigned int* err;
+    int64_t n_docs;
+    int64_t n_tokens;
+    int64_t n_cand;
+    int n_queries;
+    int nq;
+    int nchunks;   // ceil(d / 64)
+    int stages;
+    int qslots;
+    uint32_t idesc;
+};
+
+struct Layout {
+    int stage_off, q_off, part_off, info_off, bar_off, misc_off, total;
+};
+
+// Shared-memory carve-up; the same arithmetic runs on host and device.
+__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int NT, int acc) {
+    Layout L;
+    L.stage_off = 0;
+    L.q_off = stages * kStageBytes;
+    L.part_off = L.q_off + qslots * nchunks * NT * 128;
+    L.info_off = L.part_off + 2 * 4 * NT * 4;
+    L.bar_off = L.info_off + kInfoRing * 16;
+    const int nbar = 2 * stages + 2 * acc + 2 * qslots + 2 * kInfoRing + 4 + 1;
+    L.misc_off = L.bar_off + nbar * 8;
+    L.total = L.misc_off + 16;
+    return L;
+}
+
+__host__ __device__ constexpr int acc_buffers(int NT) { return NT <= 64 ? 4 : 2; }
+
+__host__ __device__ constexpr int tmem_cols(int NT) {
+    return (acc_buffers(NT) * NT <= 32) ? 32
+         : (acc_buffers(NT) * NT <= 64) ? 64
+         : (acc_buffers(NT) * NT <= 128) ? 128
+         : (acc_buffers(NT) * NT <= 256) ? 256 : 512;
+}
+
+// Candidate metadata for the producer: lane l of the warp holds the entry
+// of candidate window position l.
+struct Meta {
+    int64_t off;
+    int len;
+    int status;  // 0 ok, 1 bad id, 2 bad range, 3 past the end
+};
+
+__device__ __forceinline__ int load_id(const Args& a, int64_t k) {
+    const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
+    return f < a.n_cand ? __ldg(a.cand_ids + f) : -2;
+}
+
+__device__ __forceinline__ Meta load_meta(const Args& a, int id, int64_t k) {
+    Meta m;
+    m.off = 0;
+    m.len = 0;
+    const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
+    if (f >= a.n_cand) {
+        m.status = 3;
+    } else if (id < 0 || id >= a.n_docs) {
+        m.status = 1;
+    } else {
+        m.off = __ldg(a.offsets + id);
+        m.len = __ldg(a.lengths + id);
+        m.status = (m.len < 0 || m.off < 0 || m.off + m.len > a.n_tokens) ? 2 : 0;
+    }
+    return m;
+}
+
+// Every lane waits (and so acquires the barrier's phase itself); the warp
+// agrees on the outcome.  Returns false on timeout / abort.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned int* err) {
+    const bool ok = mbar_wait(bar, parity, abort_flag, err);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// Drain wait: bounded, but ignores the abort flag (used to let in-flight
+// asynchronous work land before the CTA exits).
+__device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitBudgetCycles) break;
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 1)
+    dense_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_d8,
+                    const __grid_constant__ CUtensorMap tm_d16, const __grid_constant__ CUtensorMap tm_d32,
+                    const __grid_constant__ CUtensorMap tm_d64, const __grid_constant__ CUtensorMap tm_d128,
+                    const Args a) {
+    constexpr int NT = NB * 32;
+    constexpr int A = acc_buffers(NT);
+    constexpr uint32_t TCOLS = tmem_cols(NT);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int S = a.stages;
+    const int QS = a.qslots;
+    const int NCH = a.nchunks;
+    const Layout L = make_layout(S, QS, NCH, NT, A);
+
+    uint8_t* stage_base = smem + L.stage_off;
+    uint8_t* q_base = smem + L.q_off;
+    float* part = reinterpret_cast<float*>(smem + L.part_off);  // [2][4][NT]
+    TileInfo* info = reinterpret_cast<TileInfo*>(smem + L.info_off);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+    uint64_t* full = bars;
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;
+    uint64_t* tempty = tfull + A;
+    uint64_t* qfull = tempty + A;
+    uint64_t* qempty = qfull + QS;
+    uint64_t* ifull = qempty + QS;
+    uint64_t* iempty = ifull + kInfoRing;
+    uint64_t* pfull = iempty + kInfoRing;
+    uint64_t* pempty = pfull + 2;
+    uint64_t* mdone = pempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < A; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 4);
+        }
+        for (int i = 0; i < QS; ++i) {
+            mbar_init(&qfull[i], 1);
+            mbar_init(&qempty[i], 1);
+        }
+        for (int i = 0; i < kInfoRing; ++i) {
+            mbar_init(&ifull[i], 1);
+            mbar_init(&iempty[i], 5);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&pfull[i], 4);
+            mbar_init(&pempty[i], 1);
+        }
+        mbar_init(mdone, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tensormap(&tm_q);
+        prefetch_tensormap(&tm_d8);
+        prefetch_tensormap(&tm_d16);
+        prefetch_tensormap(&tm_d32);
+        prefetch_tensormap(&tm_d64);
+        prefetch_tensormap(&tm_d128);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------ producer
+        const uint64_t pol_stream = policy_evict_first();
+        const uint64_t pol_keep = policy_evict_last();
+        int s = 0;
+        uint32_t ph = 0;
+        int64_t issued = 0;
+        int t = 0;
+        int qi = 0, cur_q = -1;
+        int q = 0;
+        int64_t q_end = 0;
+        bool aborted = false;
+        {
+            const int64_t co_last = __ldg(a.cand_offsets + a.n_queries);
+            if (co_last != a.n_cand && blockIdx.x == 0 && lane == 0) atomicOr(a.err, TMS_DEVERR_BAD_CSR);
+            q_end = __ldg(a.cand_offsets + 1);
+        }
+        // three-window metadata pipeline: ids two windows ahead, offsets
+        // and lengths one window ahead, the current window in registers.
+        int id_next = load_id(a, 32 + lane);
+        Meta cur = load_meta(a, load_id(a, lane), lane);
+        Meta nxt = load_meta(a, id_next, 32 + lane);
+        int id_next2 = load_id(a, 64 + lane);
+
+        for (int64_t k = 0;; ++k) {
+            const int kl = static_cast<int>(k & 31);
+            const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
+            const int status = __shfl_sync(0xffffffffu, cur.status, kl);
+            if (status == 3) break;
+            const int64_t off = __shfl_sync(0xffffffffu, cur.off, kl);
+            const int len = __shfl_sync(0xffffffffu, cur.len, kl);
+            while (f >= q_end && q < a.n_queries - 1) {
+                ++q;
+                q_end = __ldg(a.cand_offsets + q + 1);
+            }
+            if (status != 0 || len == 0) {
+                if (lane == 0) {
+                    if (status != 0) {
+                        a.out[f] = __int_as_float(0x7fc00000);
+                        atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
+                    } else {
+                        a.out[f] = -INFINITY;
+                    }
+                }
+            } else {
+                for (int r0 = 0; r0 < len; r0 += kRows) {
+                    const int r = min(kRows, len - r0);
+                    const int ii = t % kInfoRing;
+                    if (!warp_wait(&iempty[ii], ((t / kInfoRing) & 1) ^ 1, abort_flag, a.err)) {
+                        aborted = true;
+                        break;
+                    }
+                    if (lane == 0) {
+                        TileInfo ti;
+                        ti.f = static_cast<int>(f);
+                        ti.r = r;
+                        ti.q = q;
+                        ti.flags = (r0 == 0 ? kFirst : 0) | (r0 + kRows >= len ? kLast : 0);
+                        info[ii] = ti;
+                        mbar_arrive(&ifull[ii]);
+                    }
+                    ++t;
+                    // A new query's rows go to the next query slot.  The
+                    // tile info is published first: the MMA warp releases
+                    // the old slot only once it sees the new query.
+                    if (q != cur_q) {
+                        const int slot = qi % QS;
+                        if (!warp_wait(&qempty[slot], ((qi / QS) & 1) ^ 1, abort_flag, a.err)) {
+                            aborted = true;
+                            break;
+                        }
+                        if (lane == 0) {
+                            mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(NCH * NT * 128));
+                            uint8_t* qdst = q_base + slot * NCH * NT * 128;
+                            for (int kc = 0; kc < NCH; ++kc)
+                                tma_load_2d(qdst + kc * NT * 128, &tm_q, kc * kChunkElems, q * a.nq,
+                                            &qfull[slot], pol_keep);
+                        }
+                        ++qi;
+                        cur_q = q;
+                    }
+                    const int n8 = (r + 7) & ~7;
+                    const int y0 = static_cast<int>(off) + r0;
+                    for (int kc = 0; kc < NCH; ++kc) {
+                        if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                            aborted = true;
+                            break;
+                        }
+                        if (lane == 0) {
+                            uint8_t* dst = stage_base + s * kStageBytes;
+                            const int x = kc * kChunkElems;
+                            mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(n8 * 128));
+                            if (n8 == 128) {
+                                tma_load_2d(dst, &tm_d128, x, y0, &full[s], pol_stream);
+                            } else {
+                                int rows = 0;
+                                if (n8 & 64) {
+                                    tma_load_2d(dst, &tm_d64, x, y0, &full[s], pol_stream);
+                                    rows += 64;
+                                }
+                                if (n8 & 32) {
+                                    tma_load_2d(dst + rows * 128, &tm_d32, x, y0 + rows, &full[s], pol_stream);
+                                    rows += 32;
+                                }
+                                if (n8 & 16) {
+                                    tma_load_2d(dst + rows * 128, &tm_d16, x, y0 + rows, &full[s], pol_stream);
+                                    rows += 16;
+                                }
+                                if (n8 & 8) {
+                                    tma_load_2d(dst + rows * 128, &tm_d8, x, y0 + rows, &full[s], pol_stream);
+                                }
+                            }
+                        }
+                        ++issued;
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1;
+                        }
+                    }
+                    if (aborted) break;
+                }
+                if (aborted) break;
+            }
+            if (kl == 31) {
+                cur = nxt;
+                nxt = load_meta(a, id_next2, k + 33 + lane);
+                id_next2 = load_id(a, k + 65 + lane);
+            }
+        }
+        if (!aborted) {
+            const int ii = t % kInfoRing;
+            if (warp_wait(&iempty[ii], ((t / kInfoRing) & 1) ^ 1, abort_flag, a.err)) {
+                if (lane == 0) {
+                    TileInfo ti;
+                    ti.f = 0;
+                    ti.r = 0;
+                    ti.q = 0;
+                    ti.flags = kEnd;
+                    info[ii] = ti;
+                    mbar_arrive(&ifull[ii]);
+                }
+            }
+        }
+        // Let every copy still in flight land before the CTA can exit.
+        if (lane == 0) {
+            const int64_t n = issued < S ? issued : S;
+            int ss = s;
+            uint32_t pp = ph;
+            for (int64_t i = 0; i < n; ++i) {
+                if (--ss < 0) {
+                    ss = S - 1;
+                    pp ^= 1;
+                }
+                drain_wait(&full[ss], pp);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA
+        int s = 0;
+        uint32_t ph = 0;
+        int qi = 0, cur_q = -1, qslot = 0;
+        int acc = 0;
+        bool any = false;
+        for (int t = 0;; ++t) {
+            const int ii = t % kInfoRing;
+            if (!warp_wait(&ifull[ii], (t / kInfoRing) & 1, abort_flag, a.err)) break;
+            const TileInfo ti = info[ii];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&iempty[ii]);
+            if (ti.flags & kEnd) break;
+            if (ti.q != cur_q) {
+                if (cur_q >= 0 && lane == 0) mma_commit(&qempty[qslot]);
+                qslot = qi % QS;
+                if (!warp_wait(&qfull[qslot], (qi / QS) & 1, abort_flag, a.err)) break;
+                ++qi;
+                cur_q = ti.q;
+            }
+            const int ab = acc % A;
+            if (!warp_wait(&tempty[ab], ((acc / A) & 1) ^ 1, abort_flag, a.err)) break;
+            tc_fence_after();
+            bool ok = true;
+            const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * NT);
+            const uint32_t q_addr = smem_u32(q_base + qslot * NCH * NT * 128);
+            for (int kc = 0; kc < NCH; ++kc) {
+                if (!warp_wait(&full[s], ph, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t a_addr = smem_u32(stage_base + s * kStageBytes);
+                    const uint32_t b_addr = q_addr + kc * NT * 128;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_f16(d_tmem, desc_sw128(a_addr + kk * 32), desc_sw128(b_addr + kk * 32), a.idesc,
+                                (kc | kk) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                __syncwarp();
+                any = true;
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            if (!ok) break;
+            if (lane == 0) mma_commit(&tfull[ab]);
+            __syncwarp();
+            ++acc;
+        }
+        // Every MMA this thread issued must finish before TMEM is freed.
+        if (any) {
+            if (lane == 0) {
+                mma_commit(mdone);
+                drain_wait(mdone, 0);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ----------------------------------------------------- epilogue
+        const int qd = warp & 3;  // TMEM lane quadrant this warp may read
+        float rm[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) rm[b] = -INFINITY;
+        int acc = 0;
+        int pb = 0;
+        uint32_t uses[2] = {0, 0};
+        for (int t = 0;; ++t) {
+            const int ii = t % kInfoRing;
+            if (!warp_wait(&ifull[ii], (t / kInfoRing) & 1, abort_flag, a.err)) break;
+            const TileInfo ti = info[ii];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&iempty[ii]);
+            if (ti.flags & kEnd) break;
+            if (ti.flags & kFirst) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) rm[b] = -INFINITY;
+            }
+            const int ab = acc % A;
+            if (!warp_wait(&tfull[ab], (acc / A) & 1, abort_flag, a.err)) break;
+            tc_fence_after();
+            const int rows_here = ti.r - qd * 32;
+            if (rows_here > 0) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    float v[32];
+                    tmem_ld32(tbase + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(ab * NT + b * 32),
+                              v);
+                    if (lane >= rows_here) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = -INFINITY;
+                    }
+                    rm[b] = fmaxf(rm[b], butterfly_colmax(v, lane));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[ab]);
+            ++acc;
+            if (ti.flags & kLast) {
+                if (!warp_wait(&pempty[pb], (uses[pb] & 1) ^ 1, abort_flag, a.err)) break;
+                float* pp = part + pb * 4 * NT;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) pp[qd * NT + b * 32 + lane] = rm[b];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&pfull[pb]);
+                if (qd == 0) {
+                    if (!warp_wait(&pfull[pb], uses[pb] & 1, abort_flag, a.err)) break;
+                    float sum = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const int col = b * 32 + lane;
+                        const float m = fmaxf(fmaxf(pp[col], pp[NT + col]), fmaxf(pp[2 * NT + col], pp[3 * NT + col]));
+                        sum += (col < a.nq) ? m : 0.f;
+                    }
+                    sum = warp_sum(sum);
+                    if (lane == 0) a.out[ti.f] = sum;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&pempty[pb]);
+                }
+                ++uses[pb];
+                pb ^= 1;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, TCOLS);
+    }
+}
+
+// ------------------------------------------------------------------ fp32
+
+constexpr int kF32Warps = 8;
+constexpr int kF32Chunk = 64;
+
+// Exact-fp32 MaxSim: one warp per candidate, lane i = query token
+// (blocks of 32), a 64-wide chunk of the query row in registers, each
+// document row broadcast to the warp.  Dot products accumulate in fp32
+// over all dimension chunks before the max.
+__global__ void __launch_bounds__(kF32Warps * 32)
+    dense_f32_kernel(const float* __restrict__ queries, const float* __restrict__ tokens, const Args a, int d) {
+    extern __shared__ float qs[];  // [32][d + 4]
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int pitch = d + 4;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && __ldg(a.cand_offsets + a.n_queries) != a.n_cand)
+        atomicOr(a.err, TMS_DEVERR_BAD_CSR);
+    for (int q = 0; q < a.n_queries; ++q) {
+        int64_t c0 = __ldg(a.cand_offsets + q), c1 = __ldg(a.cand_offsets + q + 1);
+        c0 = c0 < 0 ? 0 : (c0 > a.n_cand ? a.n_cand : c0);
+        c1 = c1 < c0 ? c0 : (c1 > a.n_cand ? a.n_cand : c1);
+        for (int ib = 0; ib < a.nq; ib += 32) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < 32 * d; e += blockDim.x) {
+                const int i = e / d, t = e - i * d;
+                qs[i * pitch + t] = (ib + i < a.nq) ? queries[(static_cast<int64_t>(q) * a.nq + ib + i) * d + t] : 0.f;
+            }
+            __syncthreads();
+            for (int64_t c = c0 + static_cast<int64_t>(blockIdx.x) * kF32Warps + warp; c < c1;
+                 c += static_cast<int64_t>(gridDim.x) * kF32Warps) {
+                const int id = __ldg(a.cand_ids + c);
+                int64_t off = 0;
+                int len = 0;
+                int status = 0;
+                if (id < 0 || id >= a.n_docs) {
+                    status = 1;
+                } else {
+                    off = __ldg(a.offsets + id);
+                    len = __ldg(a.lengths + id);
+                    if (len < 0 || off < 0 || off + len > a.n_tokens) status = 2;
+                }
+                if (status != 0 || len == 0) {
+                    if (ib == 0 && lane == 0) {
+                        if (status) {
+                            a.out[c] = __int_as_float(0x7fc00000);
+                            atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
+                        } else {
+                            a.out[c] = -INFINITY;
+                        }
+                    }
+                    continue;
+                }
+                float best = -INFINITY;
+                for (int j0 = 0; j0 < len; j0 += 32) {
+                    float acc[32];
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) acc[jj] = 0.f;
+                    for (int kc = 0; kc < d; kc += kF32Chunk) {
+                        float qr[kF32Chunk];
+                        const float4* qrow = reinterpret_cast<const float4*>(qs + lane * pitch + kc);
+#pragma unroll
+                        for (int u = 0; u < kF32Chunk / 4; ++u) {
+                            const float4 v = (kc + 4 * u < d) ? qrow[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            qr[4 * u] = v.x;
+                            qr[4 * u + 1] = v.y;
+                            qr[4 * u + 2] = v.z;
+                            qr[4 * u + 3] = v.w;
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (j0 + jj < len) {
+                                const float4* xr =
+                                    reinterpret_cast<const float4*>(tokens + (off + j0 + jj) * d + kc);
+#pragma unroll
+                                for (int u = 0; u < kF32Chunk / 4; ++u) {
+                                    if (kc + 4 * u < d) {
+                                        const float4 x = __ldg(xr + u);
+                                        acc[jj] = fmaf(qr[4 * u], x.x, acc[jj]);
+                                        acc[jj] = fmaf(qr[4 * u + 1], x.y, acc[jj]);
+                                        acc[jj] = fmaf(qr[4 * u + 2], x.z, acc[jj]);
+                                        acc[jj] = fmaf(qr[4 * u + 3], x.w, acc[jj]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj)
+                        if (j0 + jj < len) best = fmaxf(best, acc[jj]);
+                }
+                float v = (ib + lane < a.nq) ? best : 0.f;
+                v = warp_sum(v);
+                if (lane == 0) a.out[c] = (ib == 0) ? v : a.out[c] + v;
+            }
+        }
+    }
+}
+
+}  // namespace dense
+
+namespace {
+
+template <int NB>
+tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                     const void* doc_tokens, int64_t n_tokens, dense::Args a, cudaStream_t stream) {
+    using namespace dense;
+    constexpr int NT = NB * 32;
+    constexpr int A = acc_buffers(NT);
+    const CUtensorMapDataType tdt = dtype == TMS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const uint64_t row_bytes = static_cast<uint64_t>(d) * 2;
+    CUtensorMap tq, t8, t16, t32, t64, t128;
+    tms_status st;
+    if ((st = encode_tmap_2d(&tq, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes, kChunkElems, NT)) != TMS_OK ||
+        (st = encode_tmap_2d(&t8, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 8)) != TMS_OK ||
+        (st = encode_tmap_2d(&t16, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 16)) != TMS_OK ||
+        (st = encode_tmap_2d(&t32, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 32)) != TMS_OK ||
+        (st = encode_tmap_2d(&t64, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 64)) != TMS_OK ||
+        (st = encode_tmap_2d(&t128, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 128)) != TMS_OK)
+        return st;
+    const int limit = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
+    int qslots = 2, stages = 0;
+    for (; qslots >= 1; --qslots) {
+        const Layout L0 = make_layout(0, qslots, a.nchunks, NT, A);
+        // each stage also adds two barriers (16 bytes)
+        stages = std::min(kMaxStages, (limit - L0.total) / (kStageBytes + 16));
+        if (stages >= 4) break;
+    }
+    if (stages < 3) return TMS_ERR_UNSUPPORTED;
+    if (qslots < 1) qslots = 1;
+    a.stages = stages;
+    a.qslots = qslots;
+    a.idesc = make_idesc(kRows, NT, dtype == TMS_BF16 ? 1u : 0u);
+    const Layout L = make_layout(stages, qslots, a.nchunks, NT, A);
+    const int smem = L.total + 1024;
+    auto kern = dense_tc_kernel<NB>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return launch_status(cudaErrorInvalidValue);
+    const int64_t grid = std::min<int64_t>(dev.sm_count, a.n_cand);
+    kern<<<static_cast<unsigned>(grid), kThreads, smem, stream>>>(tq, t8, t16, t32, t64, t128, a);
+    return launch_status(cudaGetLastError());
+}
+
+}  // namespace
+
+}  // namespace tms
+
+extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                      const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
+                                      const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
+                                      const int64_t* cand_offsets, int64_t n_cand, float* out_scores,
+                                      cudaStream_t stream) {
+    using namespace tms;
+    if (dtype != TMS_F16 && dtype != TMS_BF16 && dtype != TMS_F32) return TMS_ERR_INVALID_ARG;
+    if (n_queries < 1 || n_queries > 4096 || nq < 1 || nq > 128 || d < 8 || d > 1024 || d % 8 != 0)
+        return TMS_ERR_INVALID_ARG;
+    if (n_tokens < 0 || n_tokens >= (int64_t(1) << 31) || n_docs < 0 || n_cand < 0 ||
+        n_cand >= (int64_t(1) << 31))
+        return TMS_ERR_INVALID_ARG;
+    if (!queries || !cand_offsets || !aligned16(queries) || !aligned16(cand_offsets)) return TMS_ERR_INVALID_ARG;
+    if (n_cand > 0 && (!cand_ids || !out_scores || !aligned16(cand_ids) || !aligned16(out_scores)))
+        return TMS_ERR_INVALID_ARG;
+    if (n_docs > 0 && (!doc_offsets || !doc_lengths || !aligned16(doc_offsets) || !aligned16(doc_lengths)))
+        return TMS_ERR_INVALID_ARG;
+    if (n_tokens > 0 && (!doc_tokens || !aligned16(doc_tokens))) return TMS_ERR_INVALID_ARG;
+    if (n_cand == 0) return TMS_OK;
+    DeviceInfo dev;
+    tms_status st = current_device(&dev);
+    if (st != TMS_OK) return st;
+
+    dense::Args a{};
+    a.offsets = doc_offsets;
+    a.lengths = doc_lengths;
+    a.cand_ids = cand_ids;
+    a.cand_offsets = cand_offsets;
+    a.out = out_scores;
+    a.err = dev.err;
+    a.n_docs = n_docs;
+    a.n_tokens = n_tokens;
+    a.n_cand = n_cand;
+    a.n_queries = n_queries;
+    a.nq = nq;
+    a.nchunks = (d + dense::kChunkElems - 1) / dense::kChunkElems;
+
+    if (dtype == TMS_F32) {
+        const int smem = 32 * (d + 4) * 4;
+        if (smem > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
+        if (cudaFuncSetAttribute(dense::dense_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess)
+            return launch_status(cudaErrorInvalidValue);
+        const int64_t want = (n_cand + dense::kF32Warps - 1) / dense::kF32Warps;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(int64_t(dev.sm_count) * 4, want));
+        dense::dense_f32_kernel<<<static_cast<unsigned>(grid), dense::kF32Warps * 32, smem, stream>>>(
+            static_cast<const float*>(queries), static_cast<const float*>(doc_tokens), a, d);
+        return launch_status(cudaGetLastError());
+    }
+    const int nb = (nq + 31) / 32;
+    switch (nb) {
+        case 1: return launch_tc<1>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+        case 2: return launch_tc<2>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+        case 3: return launch_tc<3>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+        default: return launch_tc<4>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+    }
+}

@@ -1,0 +1,324 @@
+// tms_pq.cu -- fused PQ MaxSim on GB300 (sm_103a).
+//
+// Phase 1 (Section 4.2): the distance table
+//     T[q][i][m][k] = q_i[m*dsub : (m+1)*dsub] . C[m][k]
+// one thread per entry, fp32 fused multiply-adds in ascending t.
+//
+// Phase 2 (Section 4.2): score = sum_i max_j sum_m T[i][m][code_{j,m}],
+// straight from the uint8 codes; no token is ever decompressed.
+//
+// On GB300 this phase is bound by shared-memory gathers, not HBM: a token
+// costs 16 code bytes of HBM but Nq * M table reads.  The kernel is built
+// around the gathers:
+//   * the table of 8 query tokens (a "chunk", 128 KB for M = 16, K = 256)
+//     lives in shared memory in the layout
+//         word ((m / 4) * K + k) * 32 + (m % 4) * 8 + i,
+//     and lane (g = lane / 8, i = lane % 8) of a warp looks up subspace
+//     m = 4 s + g of query token i at step s.  Whatever the four codes a
+//     warp instruction uses, its 32 addresses fall in 32 distinct banks
+//     (the bank is (m % 4) * 8 + i), so every gather is one wavefront;
+//   * each lane sums its 4 (of 16) subspaces for 4 tokens, and a two-step
+//     transposed shuffle reduction turns that into the full dot of token
+//     (4 j + g) with query token i -- 3 shuffles per 4 tokens;
+//   * the running max stays in registers; tokens past the document end
+//     re-use the last token (a duplicate cannot change a max);
+//   * chunks are processed one after another over the CTA's candidates,
+//     and out_scores itself carries the running sum over chunks, added in
+//     ascending chunk order by the same CTA -- deterministic, no atomics,
+//     no scratch memory.
+#include <algorithm>
+
+#include "tms_common.cuh"
+#include "tms_internal.h"
+
+namespace tms {
+namespace pq {
+
+constexpr int kWarps = 16;
+constexpr int kQC = 8;  // query tokens per chunk
+
+template <typename T>
+__device__ __forceinline__ float to_f32(T v);
+template <>
+__device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) { return v; }
+
+template <typename QT>
+__global__ void lut_kernel(const QT* __restrict__ queries, int d, const float* __restrict__ codebook, int M, int K,
+                           float* __restrict__ lut, int64_t total) {
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int k = static_cast<int>(idx % K);
+    const int m = static_cast<int>((idx / K) % M);
+    const int64_t row = idx / (static_cast<int64_t>(K) * M);  // q * nq + i
+    const int dsub = d / M;
+    const QT* qv = queries + row * d + m * dsub;
+    const float* cv = codebook + (static_cast<int64_t>(m) * K + k) * dsub;
+    float acc = 0.f;
+    for (int t = 0; t < dsub; ++t) acc = fmaf(to_f32(qv[t]), __ldg(cv + t), acc);
+    lut[idx] = acc;
+}
+
+struct Args {
+    const float* lut;
+    const uint8_t* codes;
+    const int64_t* offsets;
+    const int32_t* lengths;
+    const int32_t* cand_ids;
+    const int64_t* cand_offsets;
+    float* out;
+    unsigned int* err;
+    int64_t n_docs;
+    int64_t n_tokens;
+    int64_t n_cand;
+    int n_queries;
+    int nq;
+    int K;
+};
+
+// Codes of one token as M/4 32-bit words (M bytes, 4-byte aligned rows).
+template <int M>
+struct CodeRow {
+    uint32_t w[M / 4];
+};
+
+template <int M>
+__device__ __forceinline__ CodeRow<M> load_codes(const uint8_t* row) {
+    CodeRow<M> c;
+    if constexpr (M == 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row));
+        c.w[0] = v.x;
+        c.w[1] = v.y;
+        c.w[2] = v.z;
+        c.w[3] = v.w;
+    } else if constexpr (M == 32) {
+        const uint4 v0 = __ldg(reinterpret_cast<const uint4*>(row));
+        const uint4 v1 = __ldg(reinterpret_cast<const uint4*>(row) + 1);
+        c.w[0] = v0.x; c.w[1] = v0.y; c.w[2] = v0.z; c.w[3] = v0.w;
+        c.w[4] = v1.x; c.w[5] = v1.y; c.w[6] = v1.z; c.w[7] = v1.w;
+    } else if constexpr (M == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(row));
+        c.w[0] = v.x;
+        c.w[1] = v.y;
+    } else {
+        c.w[0] = __ldg(reinterpret_cast<const uint32_t*>(row));
+    }
+    return c;
+}
+
+// Partial dot of this lane's subspaces {g, g+4, ...} for one token.
+template <int M>
+__device__ __forceinline__ float lane_partial(const float* lut_lane, const CodeRow<M>& c, uint32_t sel, int K) {
+    float p = 0.f;
+#pragma unroll
+    for (int s = 0; s < M / 4; ++s) {
+        const uint32_t code = __byte_perm(c.w[s], 0u, sel);  // byte g of word s
+        p += lut_lane[(s * K + static_cast<int>(code)) * 32];
+    }
+    return p;
+}
+
+template <int M>
+__global__ void __launch_bounds__(kWarps * 32, 1) score_kernel(const Args a) {
+    extern __shared__ float lut_s[];  // [M/4][K][4][8]
+    __shared__ int next_local;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 3;  // subspace group
+    const int i = lane & 7;   // query token within the chunk
+    const uint32_t sel = 0x4440u | static_cast<uint32_t>(g);
+    const float* lut_lane = lut_s + lane;
+    const int K = a.K;
+    const int nchunks = (a.nq + kQC - 1) / kQC;
+    const int words = kQC * M * K;
+
+    if (blockIdx.x == 0 && threadIdx.x == 0 && __ldg(a.cand_offsets + a.n_queries) != a.n_cand)
+        atomicOr(a.err, TMS_DEVERR_BAD_CSR);
+
+    for (int q = 0; q < a.n_queries; ++q) {
+        int64_t c0 = __ldg(a.cand_offsets + q), c1 = __ldg(a.cand_offsets + q + 1);
+        c0 = c0 < 0 ? 0 : (c0 > a.n_cand ? a.n_cand : c0);
+        c1 = c1 < c0 ? c0 : (c1 > a.n_cand ? a.n_cand : c1);
+        // this CTA's candidates of query q: c0 + blockIdx.x + j * gridDim.x
+        if (c0 + blockIdx.x >= c1) continue;
+        const int64_t n_local = (c1 - c0 - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            __syncthreads();
+            // table chunk -> shared memory, transposed to [m/4][k][m%4][i]
+            const float* src = a.lut + static_cast<int64_t>(q) * a.nq * M * K;
+            for (int w = threadIdx.x; w < words; w += blockDim.x) {
+                const int ii = w & 7;
+                const int ml = (w >> 3) & 3;
+                const int rest = w >> 5;
+                const int kk = rest % K;
+                const int mh = rest / K;
+                const int qi = ch * kQC + ii;
+                lut_s[w] = (qi < a.nq) ? __ldg(src + (static_cast<int64_t>(qi) * M + mh * 4 + ml) * K + kk) : 0.f;
+            }
+            if (threadIdx.x == 0) next_local = 0;
+            __syncthreads();
+            for (;;) {
+                int li = 0;
+                if (lane == 0) li = atomicAdd(&next_local, 1);
+                li = __shfl_sync(0xffffffffu, li, 0);
+                if (li >= n_local) break;
+                const int64_t f = c0 + blockIdx.x + static_cast<int64_t>(li) * gridDim.x;
+                const int id = __ldg(a.cand_ids + f);
+                int64_t off = 0;
+                int len = 0;
+                int status = 0;
+                if (id < 0 || id >= a.n_docs) {
+                    status = 1;
+                } else {
+                    off = __ldg(a.offsets + id);
+                    len = __ldg(a.lengths + id);
+                    if (len < 0 || off < 0 || off + len > a.n_tokens) status = 2;
+                }
+                if (status != 0 || len == 0) {
+                    if (ch == 0 && lane == 0) {
+                        if (status) {
+                            a.out[f] = __int_as_float(0x7fc00000);
+                            atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
+                        } else {
+                            a.out[f] = -INFINITY;
+                        }
+                    }
+                    continue;
+                }
+                const uint8_t* base = a.codes + off * M;
+                const int last = len - 1;
+                float rmax = -INFINITY;
+                CodeRow<M> c[4];
+#pragma unroll
+                for (int tt = 0; tt < 4; ++tt) c[tt] = load_codes<M>(base + static_cast<int64_t>(min(tt, last)) * M);
+                for (int j = 0; j < len; j += 4) {
+                    // prefetch the next four tokens' codes
+                    CodeRow<M> nc[4];
+#pragma unroll
+                    for (int tt = 0; tt < 4; ++tt)
+                        nc[tt] = load_codes<M>(base + static_cast<int64_t>(min(j + 4 + tt, last)) * M);
+                    float p[4];
+#pragma unroll
+                    for (int tt = 0; tt < 4; ++tt) p[tt] = lane_partial<M>(lut_lane, c[tt], sel, K);
+                    // transposed reduction over the 4 subspace groups:
+                    // lane (g, i) ends with token 4j + g's full dot with query token i
+                    const bool up16 = (lane & 16) != 0;
+                    float k0 = up16 ? p[2] : p[0];
+                    float k1 = up16 ? p[3] : p[1];
+                    const float s0 = up16 ? p[0] : p[2];
+                    const float s1 = up16 ? p[1] : p[3];
+                    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+                    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+                    const bool up8 = (lane & 8) != 0;
+                    float kk = up8 ? k1 : k0;
+                    const float ss = up8 ? k0 : k1;
+                    kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+                    rmax = fmaxf(rmax, kk);
+#pragma unroll
+                    for (int tt = 0; tt < 4; ++tt) c[tt] = nc[tt];
+                }
+                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 8));
+                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 16));
+                float v = (ch * kQC + i < a.nq) ? rmax : 0.f;
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                if (lane == 0) a.out[f] = (ch == 0) ? v : a.out[f] + v;
+            }
+        }
+    }
+}
+
+}  // namespace pq
+}  // namespace tms
+
+extern "C" tms_status tms_build_pq_lut(const void* queries, tms_dtype qdtype, int n_queries, int nq, int d,
+                                       const float* codebook, int m, int k, float* lut, cudaStream_t stream) {
+    using namespace tms;
+    if (qdtype != TMS_F16 && qdtype != TMS_BF16 && qdtype != TMS_F32) return TMS_ERR_INVALID_ARG;
+    if (n_queries < 1 || nq < 1 || nq > 128 || d < 1 || m < 1 || m > 64 || k < 1 || k > 256 || d % m != 0)
+        return TMS_ERR_INVALID_ARG;
+    if (!queries || !codebook || !lut || !aligned16(queries) || !aligned16(codebook) || !aligned16(lut))
+        return TMS_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    tms_status st = current_device(&dev);
+    if (st != TMS_OK) return st;
+    const int64_t total = static_cast<int64_t>(n_queries) * nq * m * k;
+    const int threads = 256;
+    const int64_t blocks = (total + threads - 1) / threads;
+    if (qdtype == TMS_F16)
+        pq::lut_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(static_cast<const __half*>(queries), d,
+                                                                              codebook, m, k, lut, total);
+    else if (qdtype == TMS_BF16)
+        pq::lut_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
+            static_cast<const __nv_bfloat16*>(queries), d, codebook, m, k, lut, total);
+    else
+        pq::lut_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(static_cast<const float*>(queries), d,
+                                                                              codebook, m, k, lut, total);
+    return launch_status(cudaGetLastError());
+}
+
+extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int m, int k, const uint8_t* codes,
+                                   int64_t n_tokens, const int64_t* doc_offsets, const int32_t* doc_lengths,
+                                   int64_t n_docs, const int32_t* cand_ids, const int64_t* cand_offsets,
+                                   int64_t n_cand, float* out_scores, cudaStream_t stream) {
+    using namespace tms;
+    if (n_queries < 1 || n_queries > 4096 || nq < 1 || nq > 128 || k < 1 || k > 256) return TMS_ERR_INVALID_ARG;
+    if (m != 4 && m != 8 && m != 16 && m != 32) return TMS_ERR_UNSUPPORTED;
+    if (m * k > 4096) return TMS_ERR_UNSUPPORTED;
+    if (n_tokens < 0 || n_docs < 0 || n_cand < 0 || n_cand >= (int64_t(1) << 31)) return TMS_ERR_INVALID_ARG;
+    if (!lut || !cand_offsets || !aligned16(lut) || !aligned16(cand_offsets)) return TMS_ERR_INVALID_ARG;
+    if (n_cand > 0 && (!cand_ids || !out_scores || !aligned16(cand_ids) || !aligned16(out_scores)))
+        return TMS_ERR_INVALID_ARG;
+    if (n_docs > 0 && (!doc_offsets || !doc_lengths || !aligned16(doc_offsets) || !aligned16(doc_lengths)))
+        return TMS_ERR_INVALID_ARG;
+    if (n_tokens > 0 && (!codes || !aligned16(codes))) return TMS_ERR_INVALID_ARG;
+    if (n_cand == 0) return TMS_OK;
+    DeviceInfo dev;
+    tms_status st = current_device(&dev);
+    if (st != TMS_OK) return st;
+    pq::Args a{};
+    a.lut = lut;
+    a.codes = codes;
+    a.offsets = doc_offsets;
+    a.lengths = doc_lengths;
+    a.cand_ids = cand_ids;
+    a.cand_offsets = cand_offsets;
+    a.out = out_scores;
+    a.err = dev.err;
+    a.n_docs = n_docs;
+    a.n_tokens = n_tokens;
+    a.n_cand = n_cand;
+    a.n_queries = n_queries;
+    a.nq = nq;
+    a.K = k;
+    // The last subspace group is sized for 256 codes so that a code >= k
+    // still indexes inside the allocation.
+    const int smem = ((m / 4 - 1) * k + 256) * 32 * 4;
+    if (smem > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(dev.sm_count, n_cand));
+    cudaError_t e = cudaSuccess;
+    switch (m) {
+        case 4:
+            e = cudaFuncSetAttribute(pq::score_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess) pq::score_kernel<4><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
+            break;
+        case 8:
+            e = cudaFuncSetAttribute(pq::score_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess) pq::score_kernel<8><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
+            break;
+        case 16:
+            e = cudaFuncSetAttribute(pq::score_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess) pq::score_kernel<16><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
+            break;
+        default:
+            e = cudaFuncSetAttribute(pq::score_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess) pq::score_kernel<32><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
+            break;
+    }
+    if (e != cudaSuccess) return launch_status(e);
+    return launch_status(cudaGetLastError());
+}

@@ -1,0 +1,208 @@
+"""ctypes binding of libtms (C ABI declared in ``include/tms.h``).
+
+Argument marshalling only: every step of the scoring path runs in the CUDA
+library.  The raw entry points keep the C names (``tms_score_dense`` and so
+on) and take integer device pointers; the thin helpers below take torch
+CUDA tensors and pass their ``data_ptr()`` and the current stream.  There
+is no CPU fallback -- if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+TMS_OK = 0
+TMS_ERR_INVALID_ARG = -1
+TMS_ERR_UNSUPPORTED = -2
+TMS_ERR_CUDA = -3
+TMS_ERR_DEVICE_FLAG = -5
+TMS_ERR_TIMEOUT = -6
+
+TMS_F16, TMS_BF16, TMS_F32 = 0, 1, 2
+
+TMS_DEVERR_BAD_ID = 1
+TMS_DEVERR_BAD_RANGE = 2
+TMS_DEVERR_TIMEOUT = 4
+TMS_DEVERR_BAD_CSR = 8
+
+#: every symbol include/tms.h declares
+EXPORTS = ("tms_score_dense", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
+           "tms_get_device_error", "tms_status_string", "tms_version")
+
+_lib = None
+_lock = threading.Lock()
+
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+class TmsError(RuntimeError):
+    def __init__(self, name, status):
+        self.status = status
+        super().__init__(f"{name} failed: {status_string(status)} ({status})")
+
+
+def lib(build_if_missing: bool = True):
+    """Load libtms.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libtms.so is missing and could not be built")
+            L = ctypes.CDLL(path)
+            L.tms_score_dense.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_build_pq_lut.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _p]
+            L.tms_score_pq.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
+            L.tms_get_device_error.argtypes = [_p, ctypes.POINTER(ctypes.c_int)]
+            L.tms_status_string.argtypes = [_i32]
+            L.tms_status_string.restype = ctypes.c_char_p
+            L.tms_version.argtypes = []
+            for name in ("tms_score_dense", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
+                         "tms_get_device_error", "tms_version"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().tms_status_string(int(status)).decode()
+
+
+def _check(name, status):
+    if status != TMS_OK:
+        raise TmsError(name, status)
+
+
+# ------------------------------------------------------------ raw C ABI
+
+def tms_score_dense(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets, doc_lengths,
+                    n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream) -> int:
+    return lib().tms_score_dense(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets,
+                                 doc_lengths, n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream)
+
+
+def tms_build_pq_lut(queries, qdtype, n_queries, nq, d, codebook, m, k, lut, stream) -> int:
+    return lib().tms_build_pq_lut(queries, qdtype, n_queries, nq, d, codebook, m, k, lut, stream)
+
+
+def tms_score_pq(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs,
+                 cand_ids, cand_offsets, n_cand, out_scores, stream) -> int:
+    return lib().tms_score_pq(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs,
+                              cand_ids, cand_offsets, n_cand, out_scores, stream)
+
+
+def tms_topk(scores, cand_offsets, n_queries, topk, out_scores, out_pos, stream) -> int:
+    return lib().tms_topk(scores, cand_offsets, n_queries, topk, out_scores, out_pos, stream)
+
+
+def tms_get_device_error(stream=None):
+    """(status, flags) after draining ``stream``; clears the error word."""
+    flags = ctypes.c_int(0)
+    st = lib().tms_get_device_error(stream, ctypes.byref(flags))
+    return st, flags.value
+
+
+def tms_version() -> int:
+    return lib().tms_version()
+
+
+# ------------------------------------------------- torch tensor helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    return {torch.float16: TMS_F16, torch.bfloat16: TMS_BF16, torch.float32: TMS_F32}[t.dtype]
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dev(t, dtype=None):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def score_dense(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, cand_offsets, out=None,
+                stream=None):
+    """Dense MaxSim.  queries [n_queries][nq][d]; doc_tokens [n_tokens][d];
+    cand_offsets int64 [n_queries + 1] (CUDA).  Returns out [n_cand] fp32."""
+    torch = _torch()
+    nQ, nq, d = queries.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty(n_cand, dtype=torch.float32, device=queries.device)
+    _check("tms_score_dense", tms_score_dense(
+        _dev(queries), _dtype_code(queries), nQ, nq, d, _dev(doc_tokens, queries.dtype), doc_tokens.shape[0],
+        _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
+        _dev(cand_ids, torch.int32), _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32),
+        _stream_ptr(stream)))
+    return out
+
+
+def build_pq_lut(queries, codebook, out=None, stream=None):
+    """PQ table [n_queries][nq][m][k] fp32 from queries [n_queries][nq][d]."""
+    torch = _torch()
+    nQ, nq, d = queries.shape
+    m, k, _ = codebook.shape
+    if out is None:
+        out = torch.empty((nQ, nq, m, k), dtype=torch.float32, device=queries.device)
+    _check("tms_build_pq_lut", tms_build_pq_lut(
+        _dev(queries), _dtype_code(queries), nQ, nq, d, _dev(codebook, torch.float32), m, k,
+        _dev(out, torch.float32), _stream_ptr(stream)))
+    return out
+
+
+def score_pq(lut, codes, doc_offsets, doc_lengths, cand_ids, cand_offsets, out=None, stream=None):
+    """Fused PQ MaxSim from a table [n_queries][nq][m][k] and codes [n_tokens][m]."""
+    torch = _torch()
+    nQ, nq, m, k = lut.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty(n_cand, dtype=torch.float32, device=lut.device)
+    _check("tms_score_pq", tms_score_pq(
+        _dev(lut, torch.float32), nQ, nq, m, k, _dev(codes, torch.uint8), codes.shape[0],
+        _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
+        _dev(cand_ids, torch.int32), _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32),
+        _stream_ptr(stream)))
+    return out
+
+
+def topk(scores, cand_offsets, k, out_scores=None, out_pos=None, stream=None):
+    """Per-query top-k: ([n_queries][k] fp32 scores, [n_queries][k] int32 positions)."""
+    torch = _torch()
+    nQ = cand_offsets.shape[0] - 1
+    if out_scores is None:
+        out_scores = torch.empty((nQ, k), dtype=torch.float32, device=scores.device)
+    if out_pos is None:
+        out_pos = torch.empty((nQ, k), dtype=torch.int32, device=scores.device)
+    _check("tms_topk", tms_topk(_dev(scores, torch.float32), _dev(cand_offsets, torch.int64), nQ, k,
+                                _dev(out_scores, torch.float32), _dev(out_pos, torch.int32),
+                                _stream_ptr(stream)))
+    return out_scores, out_pos
+
+
+def device_error(stream=None) -> int:
+    """TMS_DEVERR_* flags raised since the last call (synchronises ``stream``)."""
+    st, flags = tms_get_device_error(_stream_ptr(stream))
+    if st not in (TMS_OK, TMS_ERR_DEVICE_FLAG):
+        raise TmsError("tms_get_device_error", st)
+    return flags

@@ -124,9 +124,6 @@ def nearest_codes(x: np.ndarray, cb: np.ndarray) -> np.ndarray:
 
 # -------------------------------------------------------------- device side
 
-_TORCH_DT = None
-
-
 def _tdt(dtype: str):
     return {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[dtype]
 
@@ -178,16 +175,15 @@ def device_pq_corpus(lengths: np.ndarray, M: int, K: int, dsub: int, seed: int,
     g = _gen(device, seed, 14)
     cb = torch.randn((M, K, dsub), generator=g, device=device, dtype=torch.float32)
     codes = torch.empty((n_tok, M), dtype=torch.uint8, device=device)
-    cb_sq = (cb.double() ** 2).sum(-1)  # [M][K]
+    cb_sq = (cb * cb).sum(-1)  # [M][K]
     for r0 in range(0, n_tok, chunk_rows):
         r1 = min(n_tok, r0 + chunk_rows)
         pick = torch.randint(0, K, (r1 - r0, M), generator=g, device=device)
         x = cb[torch.arange(M, device=device)[None, :], pick]
         x += noise * torch.randn(x.shape, generator=g, device=device, dtype=torch.float32)
-        xd = x.double()
         for m in range(M):
             # argmin_k ||x - c_k||^2 = argmin_k (||c_k||^2 - 2 x.c_k); ties -> first index
-            dist = cb_sq[m][None, :] - 2.0 * (xd[:, m, :] @ cb[m].double().T)
+            dist = cb_sq[m][None, :] - 2.0 * (x[:, m, :] @ cb[m].T)
             codes[r0:r1, m] = torch.argmin(dist, dim=1).to(torch.uint8)
-        del x, xd, pick
+        del x, pick
     return cb, codes, torch.from_numpy(off).to(device), torch.from_numpy(lengths).to(device)

@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads without a GPU, exports every symbol that
+include/tms.h declares, and rejects invalid arguments on the host before
+touching the device."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2606_26439_gb300 import build as tms_build
+from paper_2606_26439_gb300 import tms
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tms.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tms_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return tms.lib()
+
+
+def test_library_built_in_tree(lib):
+    assert os.path.dirname(tms_build.LIB) == os.path.join(ROOT, "paper_2606_26439_gb300")
+    assert os.path.exists(tms_build.LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert set(names) == set(tms.EXPORTS), names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    assert tms.status_string(tms.TMS_OK) == "ok"
+    assert "invalid" in tms.status_string(tms.TMS_ERR_INVALID_ARG)
+    assert tms.status_string(-99) == "unknown status"
+    assert tms.tms_version() >= 100
+
+
+NULL = None
+DUMMY = 0x1000  # 16-byte aligned non-null address; never dereferenced by the host checks
+
+
+@pytest.mark.parametrize("nq,d,dtype", [(0, 128, 0), (129, 128, 0), (32, 0, 0), (32, 12, 0),
+                                        (32, 1032, 0), (32, 128, 7)])
+def test_dense_rejects_bad_shapes(lib, nq, d, dtype):
+    st = tms.tms_score_dense(DUMMY, dtype, 1, nq, d, DUMMY, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL)
+    assert st == tms.TMS_ERR_INVALID_ARG
+
+
+def test_dense_rejects_misaligned_and_null(lib):
+    st = tms.tms_score_dense(DUMMY + 4, 0, 1, 32, 128, DUMMY, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL)
+    assert st == tms.TMS_ERR_INVALID_ARG
+    st = tms.tms_score_dense(DUMMY, 0, 1, 32, 128, NULL, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL)
+    assert st == tms.TMS_ERR_INVALID_ARG
+    st = tms.tms_score_dense(DUMMY, 0, 0, 32, 128, DUMMY, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL)
+    assert st == tms.TMS_ERR_INVALID_ARG
+
+
+def test_dense_empty_candidate_list_is_noop(lib):
+    # n_cand == 0: valid, nothing to launch
+    st = tms.tms_score_dense(DUMMY, 0, 1, 32, 128, DUMMY, 10, DUMMY, DUMMY, 1, NULL, DUMMY, 0, NULL, NULL)
+    assert st == tms.TMS_OK
+
+
+@pytest.mark.parametrize("m,k", [(3, 256), (16, 300), (64, 256), (16, 0)])
+def test_pq_rejects_bad_shapes(lib, m, k):
+    st = tms.tms_score_pq(DUMMY, 1, 32, m, k, DUMMY, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL)
+    assert st in (tms.TMS_ERR_INVALID_ARG, tms.TMS_ERR_UNSUPPORTED)
+
+
+def test_pq_lut_rejects_indivisible_d(lib):
+    st = tms.tms_build_pq_lut(DUMMY, 0, 1, 32, 100, DUMMY, 16, 256, DUMMY, NULL)
+    assert st == tms.TMS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("k", [0, 1025])
+def test_topk_rejects_bad_k(lib, k):
+    st = tms.tms_topk(DUMMY, DUMMY, 1, k, DUMMY, DUMMY, NULL)
+    assert st == tms.TMS_ERR_INVALID_ARG
+
+
+def test_get_device_error_rejects_null(lib):
+    assert lib.tms_get_device_error(None, ctypes.POINTER(ctypes.c_int)()) == tms.TMS_ERR_INVALID_ARG

@@ -1,0 +1,170 @@
+"""Fused PQ scoring and the PQ distance table on the GPU against the oracle.
+
+* table: within the fp32 rounding bound of the exact FP64 table;
+* code gathering: bit-exact -- with an integer-valued table every sum is
+  exact, so the GPU score must equal the oracle's exact table-sum score;
+* scores: within 1e-3 relative of FP64 decompress-then-dot (fp16 queries).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import gpu_cases as gc
+from tests._common import assert_scores_close, oracle_view
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_lut(Q, cb):
+    import torch
+    from paper_2606_26439_gb300 import tms
+    q_d, cb_d = gc.to_dev(Q, cb)
+    lut = tms.build_pq_lut(q_d, cb_d)
+    torch.cuda.synchronize()
+    return lut
+
+
+def _gpu_pq(lut_d, codes, off, ln, cands):
+    import torch
+    from paper_2606_26439_gb300 import tms
+    flat, co = gc.csr(cands)
+    c_d, o_d, l_d, f_d, co_d = gc.to_dev(codes, off, ln, flat, co)
+    out = torch.full((len(flat),), 12345.0, dtype=torch.float32, device="cuda")
+    tms.score_pq(lut_d, c_d, o_d, l_d, f_d, co_d, out=out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), tms.device_error()
+
+
+@pytest.mark.parametrize("qdtype", ["f16", "bf16", "f32"])
+@pytest.mark.parametrize("nq,d,M,K", [(32, 128, 16, 256), (5, 64, 4, 16), (33, 256, 32, 128), (8, 96, 8, 100)])
+def test_pq_lut_within_fp32_bound(cuda_lib, qdtype, nq, d, M, K):
+    """|T_gpu - T_exact| <= 2 dsub u sum_t |q_t c_t| (u = 2^-24, fma chain)."""
+    n_queries = 2
+    Q = synth.queries(n_queries, nq, d, qdtype, 40 + M)
+    cb = np.random.default_rng(M).standard_normal((M, K, d // M)).astype(np.float32)
+    got = _gpu_lut(Q, cb).cpu().numpy()
+    qa, qdt = oracle_view(Q)
+    dsub = d // M
+    for qi in range(n_queries):
+        want = oracle.pq_lut(qa[qi], cb, qdtype=qdt)
+        qd = np.abs(Q[qi].double().numpy()).reshape(nq, M, dsub)
+        mag = np.einsum("imt,mkt->imk", qd, np.abs(cb.astype(np.float64)))
+        bound = 2 * dsub * 2.0 ** -24 * mag + 1e-30
+        assert np.all(np.abs(got[qi] - want) <= bound)
+
+
+@pytest.mark.parametrize("M", [4, 8, 16, 32])
+@pytest.mark.parametrize("nq", [1, 7, 8, 9, 32, 33])
+def test_pq_gather_bit_exact_integer_table(cuda_lib, M, nq):
+    """Integer-valued table: every partial sum is exact in fp32, so the GPU
+    result must equal the exact score bit for bit (a wrong code byte, wrong
+    subspace or wrong query token would change it)."""
+    import torch
+    K = 256 if M <= 16 else 128
+    g = np.random.default_rng(M * 100 + nq)
+    n_queries = 2
+    T = g.integers(-1000, 1001, size=(n_queries, nq, M, K)).astype(np.float32)
+    lengths = np.array(gc.EDGE_LENGTHS + list(g.integers(1, 150, 60)) + [77], np.int32)
+    off = synth.offsets_of(lengths)
+    codes = g.integers(0, K, size=(int(lengths.sum()), M)).astype(np.uint8)
+    n_docs = len(lengths)
+    cands = gc.edge_candidates(n_docs, n_queries, M + nq)
+    lut_d = torch.from_numpy(T).cuda()
+    got, flags = _gpu_pq(lut_d, codes, off, lengths, cands)
+    want = np.concatenate([oracle.pq_lut_scores(T[qi], codes, off, lengths, c) for qi, c in enumerate(cands)])
+    fin = np.isfinite(want)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    assert np.array_equal(got[~fin & ~np.isnan(want)], want[~fin & ~np.isnan(want)])
+    assert np.array_equal(got[fin].astype(np.float64), want[fin])
+
+
+@pytest.mark.parametrize("nq", [32, 9])
+def test_pq_scores_vs_decompress(cuda_lib, nq):
+    """GPU table (tms_build_pq_lut) + fused scoring vs FP64
+    decompress-then-dot on the same fp16 queries and fp32 codebook."""
+    M, K, dsub = 16, 256, 8
+    d = M * dsub
+    lengths = synth.lengths_uniform(400, 1, 180, 50)
+    cb, codes, _, off, ln = synth.pq_corpus(lengths, M, K, dsub, 50)
+    Q = synth.queries(3, nq, d, "f16", 50)
+    cands = [synth.candidates(400, n, 50, i) for i, n in enumerate((400, 250, 37))]
+    lut_d = _gpu_lut(Q, cb)
+    got, flags = _gpu_pq(lut_d, codes, off, ln, cands)
+    assert flags == 0
+    qa, qdt = oracle_view(Q)
+    want = np.concatenate([oracle.pq_decompress_scores(qa[i], cb, codes, off, ln, c, qdtype=qdt)
+                           for i, c in enumerate(cands)])
+    assert_scores_close(got, want, "f16", nq)
+
+
+def test_pq_edge_documents_and_flags(cuda_lib):
+    """Empty documents score -inf, bad ids NaN with the error flag raised."""
+    from paper_2606_26439_gb300 import tms
+    import torch
+    M, K, nq = 16, 256, 32
+    lengths = np.array([0, 3, 0, 5], np.int32)
+    off = synth.offsets_of(lengths)
+    codes = np.random.default_rng(1).integers(0, K, size=(8, M)).astype(np.uint8)
+    T = np.random.default_rng(2).standard_normal((1, nq, M, K)).astype(np.float32)
+    got, flags = _gpu_pq(torch.from_numpy(T).cuda(), codes, off, lengths,
+                         [np.array([0, 1, 2, 3, -5, 4], np.int32)])
+    assert got[0] == -np.inf and got[2] == -np.inf
+    assert np.isnan(got[4]) and np.isnan(got[5])
+    assert np.isfinite(got[1]) and np.isfinite(got[3])
+    assert flags & tms.TMS_DEVERR_BAD_ID
+
+
+def test_pq_bitwise_repeatable(cuda_lib):
+    M, K, dsub = 16, 256, 8
+    lengths = synth.lengths_uniform(3000, 32, 180, 51)
+    cb, codes, _, off, ln = synth.pq_corpus(lengths, M, K, dsub, 51)
+    Q = synth.queries(2, 32, M * dsub, "f16", 51)
+    cands = [synth.candidates(3000, 3000, 51, 0), synth.candidates(3000, 1000, 51, 1)]
+    lut_d = _gpu_lut(Q, cb)
+    a, _ = _gpu_pq(lut_d, codes, off, ln, cands)
+    b, _ = _gpu_pq(lut_d, codes, off, ln, cands)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.slow
+def test_config4_pq_full_size_sampled(cuda_lib):
+    """1,000,000 documents, Nd ~ U[32, 180], M = 16, K = 256, dsub = 8,
+    Gaussian centroids + N(0, 0.05) noise, nearest-centroid codes; 64 fp16
+    queries each over all documents.  Sampled parity vs decompress-then-dot."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    n_docs, M, K, dsub, nq, n_queries = 1_000_000, 16, 256, 8, 32, 64
+    d = M * dsub
+    lengths = synth.lengths_uniform(n_docs, 32, 180, 4)
+    cb_d, codes_d, off_d, ln_d = synth.device_pq_corpus(lengths, M, K, dsub, 4)
+    Q = synth.queries(n_queries, nq, d, "f16", 4)
+    q_d = gc.to_dev(Q)[0]
+    lut_d = tms.build_pq_lut(q_d, cb_d)
+    cands = [np.arange(n_docs, dtype=np.int32)] * n_queries
+    flat, co = gc.csr(cands)
+    f_d, co_d = gc.to_dev(flat, co)
+    out = tms.score_pq(lut_d, codes_d, off_d, ln_d, f_d, co_d)
+    torch.cuda.synchronize()
+    assert tms.device_error() == 0
+    scores = out.cpu().numpy()
+    assert np.isfinite(scores).all()
+    g = np.random.default_rng(5)
+    pos = np.sort(g.choice(len(flat), 512, replace=False))
+    qidx = pos // n_docs
+    ids = flat[pos]
+    off = synth.offsets_of(lengths)
+    rows = np.concatenate([np.arange(off[i], off[i] + lengths[i]) for i in ids])
+    sub_codes = codes_d[torch.from_numpy(rows).cuda()].cpu().numpy()
+    sub_len = lengths[ids]
+    sub_off = synth.offsets_of(sub_len)
+    cb = cb_d.cpu().numpy()
+    qa, qdt = oracle_view(Q)
+    want = np.empty(len(pos))
+    for qi in np.unique(qidx):
+        sel = np.nonzero(qidx == qi)[0]
+        want[sel] = oracle.pq_decompress_scores(qa[qi], cb, sub_codes, sub_off, sub_len, sel.astype(np.int32),
+                                                qdtype=qdt)
+    assert_scores_close(scores[pos], want, "f16", nq)
