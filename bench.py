@@ -1,0 +1,507 @@
+#!/usr/bin/env python3
+"""Benchmark of the MaxSim scoring path on GB300.
+
+Workload (the headline): dense MaxSim at scale -- 500,000 packed documents
+with Nd ~ uniform integer [32, 180], d = 128, fp16 unit-normalised
+Gaussian embeddings (13.6 GB resident in HBM, far larger than the 129 MB
+L2, so no flush is needed between steps); 16 queries of Nq = 32 tokens,
+each scoring its own random 100,000-document candidate subset.  One step
+= one tms_score_dense launch over all 16 x 100,000 candidates plus one
+tms_topk launch (top-10 per query).  Metric: documents scored per second.
+
+Also reported (N = 1 only): the same workload in bf16 and fp32, dimension
+tiling at d = 64/256/512/768 (200,000 docs, 32 queries over all of them,
+bf16, top-100) and fused PQ (1,000,000 docs, M = 16, K = 256, 64 queries
+over all of them).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tms|reference]
+
+``--impl reference`` times the FP64 CPU oracle on this host's cores on
+bounded samples of the same workload (the one reference this project has).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from paper_2606_26439_gb300 import iomodel  # noqa: E402
+
+N_DOCS, LO, HI, D, NQ, N_QUERIES, N_CAND, TOPK = 500_000, 32, 180, 128, 32, 16, 100_000, 10
+METRIC = "docs scored/sec"
+WORKLOAD = ("dense MaxSim at scale: 500,000 docs, Nd~U[32,180], d=128, packed; "
+            "16 queries Nq=32 x 100,000-doc random candidate subsets; top-10")
+KERNEL_SRC = os.path.join(ROOT, "paper_2606_26439_gb300", "csrc", "tms_dense.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dense_tc_kernel_500k_docs_fp16.txt")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["tms", "reference"], default="tms")
+    p.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
+    p.add_argument("--workload", choices=["headline", "small"], default="headline",
+                   help="small: 100,000 docs, 1 query x 100,000 candidates (sized for ncu captures)")
+    args = p.parse_args()
+    if args.workload == "small":
+        global N_DOCS, N_QUERIES, WORKLOAD
+        N_DOCS, N_QUERIES = 100_000, 1
+        WORKLOAD = ("dense MaxSim, small profiling case: 100,000 docs, Nd~U[32,180], d=128, packed; "
+                    "1 query Nq=32 x 100,000 candidates; top-10")
+        args.no_rows = True
+    return args
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), float(j["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+def kernel_sha():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic_per_token():
+    """DRAM bytes per processed document token for the dense kernel, from the
+    committed ncu summary -- None if absent or taken on another source."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256_16") != kernel_sha():
+            return None
+        return float(kv["dram_bytes_per_token"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(", ") for r in self.file.read().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for n, v in zip(names, r[3:7]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if args.impl == "tms" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- workloads
+
+def headline_inputs(seed=0):
+    lengths = synth.lengths_uniform(N_DOCS, LO, HI, seed)
+    cands = [synth.candidates(N_DOCS, N_CAND, seed, q) for q in range(N_QUERIES)]
+    return lengths, cands
+
+
+def cpu_sample(lengths, cands, n_sample, seed=1):
+    """Host copy of a bounded sample of the headline workload: the first
+    n_sample candidates of query 0, their documents generated on the host
+    with the same recipe (same lengths, same distribution)."""
+    ids = cands[0][:n_sample]
+    sub_len = lengths[ids]
+    import torch
+    tok, off, ln = synth.dense_corpus(len(ids), sub_len, D, "f16", seed)
+    Q = synth.queries(1, NQ, D, "f16", seed)
+    q = Q[0].view(torch.int16).numpy().view(np.uint16)
+    t = tok.view(torch.int16).numpy().view(np.uint16)
+    return q, t, off, ln, np.arange(len(ids), dtype=np.int32)
+
+
+def time_oracle(lengths, cands, target_s):
+    """Docs/s of the FP64 oracle on this host's cores (calibrated sample)."""
+    import oracle
+    q, t, off, ln, c = cpu_sample(lengths, cands, 300)
+    t0 = time.perf_counter()
+    oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
+    rate = len(c) / (time.perf_counter() - t0)
+    n = int(max(300, min(N_CAND, rate * target_s)))
+    q, t, off, ln, c = cpu_sample(lengths, cands, n)
+    t0 = time.perf_counter()
+    oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, oracle.max_threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    lengths, cands = headline_inputs()
+    # calibrate so that warmup + steps stay within ~2 minutes
+    q, t, off, ln, c = cpu_sample(lengths, cands, 200)
+    t0 = time.perf_counter()
+    oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
+    rate = len(c) / (time.perf_counter() - t0)
+    per_step_s = min(2.0, 120.0 / max(1, args.steps + args.warmup))
+    n = int(max(16, min(N_CAND, rate * per_step_s)))
+    q, t, off, ln, c = cpu_sample(lengths, cands, n)
+    for _ in range(args.warmup):
+        oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = n / dt
+    sample = f"first {n} candidates of query 0 per step (Nq=32, d=128, fp16 stored values, FP64 arithmetic)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "docs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (plain C + OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": "docs/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "docs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def dense_workload(dtype, lengths, cands, device):
+    import torch
+    tok_d, off_d, ln_d = synth.device_dense_corpus(lengths, D, dtype, 0, device)
+    Q = synth.queries(N_QUERIES, NQ, D, dtype, 0)
+    flat = np.concatenate(cands).astype(np.int32)
+    co = np.zeros(N_QUERIES + 1, np.int64)
+    co[1:] = np.cumsum([len(c) for c in cands])
+    return dict(tok=tok_d, off=off_d, ln=ln_d, Q=Q, q=Q.to(device), flat=flat, co=co,
+                f=torch.from_numpy(flat).to(device), c=torch.from_numpy(co).to(device),
+                tokens=int(lengths[flat].astype(np.int64).sum()))
+
+
+def time_dense(w, steps, warmup, stream):
+    """Device-resident steps: (ms per step, dense-kernel ms per launch)."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    out = torch.empty(len(w["flat"]), dtype=torch.float32, device=w["q"].device)
+    ts = torch.empty((N_QUERIES, TOPK), dtype=torch.float32, device=w["q"].device)
+    tp = torch.empty((N_QUERIES, TOPK), dtype=torch.int32, device=w["q"].device)
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        tms.score_dense(w["q"], w["tok"], w["off"], w["ln"], w["f"], w["c"], out=out, stream=stream)
+        if evs is not None:
+            evs[1].record(stream)
+        tms.topk(out, w["c"], TOPK, ts, tp, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for i in range(steps):
+            step(kev[i])
+        e1.record(stream)
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    kern = [a.elapsed_time(b) for a, b in kev]
+    return total / steps, statistics.mean(kern), out
+
+
+def time_dense_e2e(w, steps, warmup, stream):
+    """End to end through the public API from pinned host buffers: per step
+    H2D of the queries, candidate ids and CSR offsets, both launches, and
+    D2H of all scores and the top-k."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    dev = w["q"].device
+    hq = w["Q"].contiguous().pin_memory()
+    hf = torch.from_numpy(w["flat"]).pin_memory()
+    hc = torch.from_numpy(w["co"]).pin_memory()
+    q = torch.empty_like(hq, device=dev)
+    f = torch.empty_like(hf, device=dev)
+    c = torch.empty_like(hc, device=dev)
+    out = torch.empty(len(w["flat"]), dtype=torch.float32, device=dev)
+    ts = torch.empty((N_QUERIES, TOPK), dtype=torch.float32, device=dev)
+    tp = torch.empty((N_QUERIES, TOPK), dtype=torch.int32, device=dev)
+    hs = torch.empty(len(w["flat"]), dtype=torch.float32).pin_memory()
+    hts = torch.empty((N_QUERIES, TOPK), dtype=torch.float32).pin_memory()
+    htp = torch.empty((N_QUERIES, TOPK), dtype=torch.int32).pin_memory()
+
+    def step():
+        q.copy_(hq, non_blocking=True)
+        f.copy_(hf, non_blocking=True)
+        c.copy_(hc, non_blocking=True)
+        tms.score_dense(q, w["tok"], w["off"], w["ln"], f, c, out=out, stream=stream)
+        tms.topk(out, c, TOPK, ts, tp, stream=stream)
+        hs.copy_(out, non_blocking=True)
+        hts.copy_(ts, non_blocking=True)
+        htp.copy_(tp, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    h2d = hq.numel() * hq.element_size() + hf.numel() * 4 + hc.numel() * 8
+    d2h = hs.numel() * 4 + hts.numel() * 4 + htp.numel() * 4
+    return e0.elapsed_time(e1) / steps, h2d, d2h
+
+
+def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
+    """bf16/fp32 of the headline workload, dimension tiling, fused PQ."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    rows = {}
+    dev = torch.device("cuda")
+    for dtype, steps in (("bf16", 50), ("f32", 10)):
+        w = dense_workload(dtype, lengths, cands, dev)
+        ms, kms, _ = time_dense(w, steps, 3, stream)
+        elem = 2 if dtype == "bf16" else 4
+        alg = iomodel.dense_alg_bytes(w["tokens"], len(w["flat"]), N_QUERIES, NQ, D, elem)
+        rows[f"dense_{dtype}"] = {
+            "docs_per_s": len(w["flat"]) / (ms * 1e-3), "ms_per_step": ms, "kernel_ms": kms,
+            "achieved_gbs": alg / (kms * 1e-3) / 1e9, "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak}
+        del w
+        torch.cuda.empty_cache()
+    # dimension tiling: 200K docs, 32 queries over all docs, bf16, top-100
+    n3 = 200_000
+    len3 = synth.lengths_uniform(n3, LO, HI, 2)
+    for d in (64, 256, 512, 768):
+        tok, off, ln = synth.device_dense_corpus(len3, d, "bf16", 2, dev)
+        Q = synth.queries(32, NQ, d, "bf16", 2).to(dev)
+        f = torch.arange(n3, dtype=torch.int32, device=dev).repeat(32)
+        c = torch.arange(0, 33 * n3, n3, dtype=torch.int64, device=dev)
+        out = torch.empty(32 * n3, dtype=torch.float32, device=dev)
+        ts = torch.empty((32, 100), dtype=torch.float32, device=dev)
+        tp = torch.empty((32, 100), dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                tms.score_dense(Q, tok, off, ln, f, c, out=out, stream=stream)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            e[0].record(stream)
+            for _ in range(3):
+                tms.score_dense(Q, tok, off, ln, f, c, out=out, stream=stream)
+            e[1].record(stream)
+            tms.topk(out, c, 100, ts, tp, stream=stream)
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        kms = e[0].elapsed_time(e[1]) / 3
+        alg = iomodel.dense_alg_bytes(int(len3.astype(np.int64).sum()) * 32, 32 * n3, 32, NQ, d, 2)
+        rows[f"dtile_bf16_d{d}"] = {"docs_per_s": 32 * n3 / (kms * 1e-3), "kernel_ms": kms,
+                                   "topk100_ms": e[1].elapsed_time(e[2]),
+                                   "achieved_gbs": alg / (kms * 1e-3) / 1e9,
+                                   "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak}
+        del tok, off, ln, Q, f, out
+        torch.cuda.empty_cache()
+    # fused PQ: 1M docs, M=16, K=256, dsub=8, 64 fp16 queries over all docs
+    n4, M, K, dsub, nQ4 = 1_000_000, 16, 256, 8, 64
+    len4 = synth.lengths_uniform(n4, LO, HI, 4)
+    cb, codes, off, ln = synth.device_pq_corpus(len4, M, K, dsub, 4, device=dev)
+    Q = synth.queries(nQ4, NQ, M * dsub, "f16", 4).to(dev)
+    f = torch.arange(n4, dtype=torch.int32, device=dev).repeat(nQ4)
+    c = torch.arange(0, (nQ4 + 1) * n4, n4, dtype=torch.int64, device=dev)
+    out = torch.empty(nQ4 * n4, dtype=torch.float32, device=dev)
+    lut = torch.empty((nQ4, NQ, M, K), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        tms.build_pq_lut(Q, cb, out=lut, stream=stream)
+        tms.score_pq(lut, codes, off, ln, f, c, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = 2
+    with torch.cuda.stream(stream):
+        e[0].record(stream)
+        for _ in range(reps):
+            tms.build_pq_lut(Q, cb, out=lut, stream=stream)
+        e[1].record(stream)
+        for _ in range(reps):
+            tms.score_pq(lut, codes, off, ln, f, c, out=out, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    lut_ms = e[0].elapsed_time(e[1]) / reps
+    pq_ms = e[1].elapsed_time(e[2]) / reps
+    tok4 = int(len4.astype(np.int64).sum()) * nQ4
+    alg = iomodel.pq_alg_bytes(tok4, nQ4 * n4, nQ4, NQ, M, K)
+    lds = iomodel.pq_lut_reads_bytes(tok4, NQ, M)
+    lds_peak = 152 * 128 * (sm_mhz or 1900.0) * 1e6 / 1e9  # GB/s of shared-memory loads
+    rows["pq_m16_k256"] = {"docs_per_s": nQ4 * n4 / (pq_ms * 1e-3), "kernel_ms": pq_ms, "lut_ms": lut_ms,
+                           "achieved_gbs": alg / (pq_ms * 1e-3) / 1e9,
+                           "frac_hbm": alg / (pq_ms * 1e-3) / 1e9 / hbm_peak,
+                           "lds_gbs": lds / (pq_ms * 1e-3) / 1e9, "lds_peak_gbs": lds_peak,
+                           "frac_lds": lds / (pq_ms * 1e-3) / 1e9 / lds_peak}
+    return rows
+
+
+def run_tms(args, ws, rank, local):
+    import torch
+    from paper_2606_26439_gb300 import tms
+    torch.cuda.set_device(local)
+    tms.lib(build_if_missing=True)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    hbm_peak, _, peak_kind = measured_peaks()
+    lengths, cands = headline_inputs()
+    w = dense_workload("f16", lengths, cands, dev)
+    n_docs_step = len(w["flat"])
+
+    # headline: device-resident, CUDA events, clocks sampled during the run
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, kms, out = time_dense(w, args.steps, args.warmup, stream)
+    clk = clocks.stop()
+    assert tms.device_error(stream) == 0, "device error flags raised during the benchmark"
+    assert bool(torch.isfinite(out).all())
+    barrier(ws)
+    ms_max = max_over_ranks(ms, ws)
+    kms_max = max_over_ranks(kms, ws)
+    value = ws * n_docs_step / (ms_max * 1e-3)
+
+    e2e_ms, h2d, d2h = time_dense_e2e(w, max(10, args.steps // 4), max(3, args.warmup), stream)
+    e2e_ms = max_over_ranks(e2e_ms, ws)
+
+    alg = iomodel.dense_alg_bytes(w["tokens"], n_docs_step, N_QUERIES, NQ, D, 2)
+    achieved = alg / (kms_max * 1e-3) / 1e9
+    tpt = recorded_traffic_per_token()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": (tpt * w["tokens"] if tpt else None),
+                "peak_kind": f"of {peak_kind} (copy bandwidth)", "alg_bytes_per_launch": alg,
+                "kernel": "tms::dense::dense_tc_kernel<1>", "kernel_ms": kms_max}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "docs/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_docs": N_DOCS, "n_queries": N_QUERIES, "nq": NQ, "d": D,
+                   "cand_per_query": N_CAND, "topk": TOPK, "tokens_per_step": w["tokens"],
+                   "l2": f"inputs larger than L2 ({w['tok'].numel() * 2 / 1e9:.1f} GB fp16 corpus, "
+                         f"{w['tokens'] * D * 2 / 1e9:.1f} GB read per step)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline,
+        "e2e": {"value": ws * n_docs_step / (e2e_ms * 1e-3), "unit": "docs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": 2 * args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+    }
+    del w, out
+    torch.cuda.empty_cache()
+    if ws == 1 and rank == 0 and args.workload == "headline":
+        rate, n, dt, cores = time_oracle(lengths, cands, 15.0)
+        line["cpu_baseline"] = {"value": rate, "unit": "docs/s", "cores": cores, "kind": "oracle",
+                                "sample": f"first {n} candidates of query 0 ({dt:.1f} s, FP64, fp16 stored values)"}
+        if not args.no_rows:
+            line["rows"] = secondary_rows(lengths, cands, stream, hbm_peak, clk["sm_mhz"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_tms(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
