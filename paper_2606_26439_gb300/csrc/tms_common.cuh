@@ -222,21 +222,12 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Transposed warp max: on entry lane l holds row l's 32 values v[0..31];
-// on exit v[0] of lane l is max over all 32 rows of column l.  31 shuffles.
-__device__ __forceinline__ float butterfly_colmax(float (&v)[32], int lane) {
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const bool upper = (lane & w) != 0;
-#pragma unroll
-        for (int j = 0; j < w; ++j) {
-            const float keep = upper ? v[j + w] : v[j];
-            const float send = upper ? v[j] : v[j + w];
-            const float other = __shfl_xor_sync(0xffffffffu, send, w);
-            v[j] = fmaxf(keep, other);
-        }
-    }
-    return v[0];
+// Max of v over the lanes in `mask` (every lane in mask must execute it),
+// returned to each of them.  NaN inputs are ignored like fmaxf.
+__device__ __forceinline__ float redux_max(float v, unsigned mask) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, %2;" : "=f"(r) : "f"(v), "r"(mask));
+    return r;
 }
 
 }  // namespace tms

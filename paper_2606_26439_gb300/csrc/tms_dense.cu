@@ -102,34 +102,37 @@ __host__ __device__ constexpr int tmem_cols(int NT) {
          : (acc_buffers(NT) * NT <= 256) ? 256 : 512;
 }
 
-// Candidate metadata for the producer: lane l of the warp holds the entry
-// of candidate window position l.
+// Candidate metadata for the producer: lane l of the warp holds the raw
+// entry of candidate window position l.  Loads are only issued here; they
+// are classified (meta_status) when the window becomes current, one window
+// later, so the producer never waits on them.
 struct Meta {
     int64_t off;
     int len;
-    int status;  // 0 ok, 1 bad id, 2 bad range, 3 past the end
+    int id;
 };
 
 __device__ __forceinline__ int load_id(const Args& a, int64_t k) {
     const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
-    return f < a.n_cand ? __ldg(a.cand_ids + f) : -2;
+    return f < a.n_cand ? __ldg(a.cand_ids + f) : -1;
 }
 
-__device__ __forceinline__ Meta load_meta(const Args& a, int id, int64_t k) {
+__device__ __forceinline__ Meta load_meta(const Args& a, int id) {
     Meta m;
+    m.id = id;
     m.off = 0;
     m.len = 0;
-    const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
-    if (f >= a.n_cand) {
-        m.status = 3;
-    } else if (id < 0 || id >= a.n_docs) {
-        m.status = 1;
-    } else {
+    if (id >= 0 && id < a.n_docs) {
         m.off = __ldg(a.offsets + id);
         m.len = __ldg(a.lengths + id);
-        m.status = (m.len < 0 || m.off < 0 || m.off + m.len > a.n_tokens) ? 2 : 0;
     }
     return m;
+}
+
+// 0 ok, 1 bad id, 2 bad row range.
+__device__ __forceinline__ int meta_status(const Args& a, int id, int64_t off, int len) {
+    if (id < 0 || id >= a.n_docs) return 1;
+    return (len < 0 || off < 0 || off + len > a.n_tokens) ? 2 : 0;
 }
 
 // Every lane waits (and so acquires the barrier's phase itself); the warp
@@ -250,17 +253,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         // three-window metadata pipeline: ids two windows ahead, offsets
         // and lengths one window ahead, the current window in registers.
         int id_next = load_id(a, 32 + lane);
-        Meta cur = load_meta(a, load_id(a, lane), lane);
-        Meta nxt = load_meta(a, id_next, 32 + lane);
+        Meta cur = load_meta(a, load_id(a, lane));
+        Meta nxt = load_meta(a, id_next);
         int id_next2 = load_id(a, 64 + lane);
 
         for (int64_t k = 0;; ++k) {
             const int kl = static_cast<int>(k & 31);
             const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
-            const int status = __shfl_sync(0xffffffffu, cur.status, kl);
-            if (status == 3) break;
+            if (f >= a.n_cand) break;
+            const int cid = __shfl_sync(0xffffffffu, cur.id, kl);
             const int64_t off = __shfl_sync(0xffffffffu, cur.off, kl);
             const int len = __shfl_sync(0xffffffffu, cur.len, kl);
+            const int status = meta_status(a, cid, off, len);
             while (f >= q_end && q < a.n_queries - 1) {
                 ++q;
                 q_end = __ldg(a.cand_offsets + q + 1);
@@ -355,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (kl == 31) {
                 cur = nxt;
-                nxt = load_meta(a, id_next2, k + 33 + lane);
+                nxt = load_meta(a, id_next2);
                 id_next2 = load_id(a, k + 65 + lane);
             }
         }
@@ -451,13 +455,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else {
         // ----------------------------------------------------- epilogue
+        // Thread = document row (TMEM lane), register c = query token c.
+        // The column max over the tile's valid rows is one redux.sync.max
+        // per column whose member mask is exactly those rows, so rows past
+        // the document end never take part; the running maxima are held
+        // warp-uniform (lane 0 always participates when any row is valid).
         const int qd = warp & 3;  // TMEM lane quadrant this warp may read
-        float rm[NB];
+        float rm[NB][32];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) rm[b] = -INFINITY;
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
         int acc = 0;
-        int pb = 0;
-        uint32_t uses[2] = {0, 0};
+        uint32_t docs = 0;  // documents finished; buffer = docs & 1, its use count = docs >> 1
         for (int t = 0;; ++t) {
             const int ii = t % kInfoRing;
             if (!warp_wait(&ifull[ii], (t / kInfoRing) & 1, abort_flag, a.err)) break;
@@ -467,23 +477,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (ti.flags & kEnd) break;
             if (ti.flags & kFirst) {
 #pragma unroll
-                for (int b = 0; b < NB; ++b) rm[b] = -INFINITY;
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
             }
             const int ab = acc % A;
             if (!warp_wait(&tfull[ab], (acc / A) & 1, abort_flag, a.err)) break;
             tc_fence_after();
             const int rows_here = ti.r - qd * 32;
             if (rows_here > 0) {
+                const unsigned vmask = rows_here >= 32 ? 0xffffffffu : ((1u << rows_here) - 1u);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     float v[32];
                     tmem_ld32(tbase + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(ab * NT + b * 32),
                               v);
-                    if (lane >= rows_here) {
+                    if (lane < rows_here) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = -INFINITY;
+                        for (int c = 0; c < 32; ++c) rm[b][c] = fmaxf(rm[b][c], redux_max(v[c], vmask));
                     }
-                    rm[b] = fmaxf(rm[b], butterfly_colmax(v, lane));
+                    __syncwarp();
                 }
             }
             tc_fence_before();
@@ -491,14 +504,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive(&tempty[ab]);
             ++acc;
             if (ti.flags & kLast) {
-                if (!warp_wait(&pempty[pb], (uses[pb] & 1) ^ 1, abort_flag, a.err)) break;
+                const int pb = docs & 1;
+                const uint32_t use = docs >> 1;
+                if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
                 float* pp = part + pb * 4 * NT;
+                if (lane == 0) {
 #pragma unroll
-                for (int b = 0; b < NB; ++b) pp[qd * NT + b * 32 + lane] = rm[b];
+                    for (int b = 0; b < NB; ++b)
+#pragma unroll
+                        for (int c = 0; c < 32; c += 4)
+                            *reinterpret_cast<float4*>(pp + qd * NT + b * 32 + c) =
+                                make_float4(rm[b][c], rm[b][c + 1], rm[b][c + 2], rm[b][c + 3]);
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&pfull[pb]);
                 if (qd == 0) {
-                    if (!warp_wait(&pfull[pb], uses[pb] & 1, abort_flag, a.err)) break;
+                    if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) break;
                     float sum = 0.f;
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
@@ -511,8 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&pempty[pb]);
                 }
-                ++uses[pb];
-                pb ^= 1;
+                ++docs;
             }
         }
     }

@@ -61,7 +61,10 @@ def edge_candidates(n_docs, n_queries, seed):
     """Query 0: every document in shuffled order, duplicates and bad ids;
     further queries: random subsets (one empty list included)."""
     g = np.random.default_rng(seed + 99)
-    c0 = list(g.permutation(n_docs)) + [0, 0, n_docs - 1, -1, n_docs, 2 ** 31 - 1]
+    c0 = list(g.permutation(n_docs)) + [0, 0, n_docs - 1]
+    # bad ids scattered through the list, not only at its end
+    for bad in (-1, -2, n_docs, 2 ** 31 - 1, -(2 ** 31)):
+        c0.insert(int(g.integers(0, len(c0) + 1)), bad)
     cands = [np.array(c0, np.int32)]
     for qi in range(1, n_queries):
         n = 0 if qi == 2 else int(g.integers(1, n_docs))
