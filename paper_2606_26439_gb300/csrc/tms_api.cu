@@ -47,22 +47,40 @@ tms_status current_device(DeviceInfo* out) {
     return TMS_OK;
 }
 
+namespace {
+bool load_encoder() {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_encode == nullptr) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || fn == nullptr) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    return true;
+}
+}  // namespace
+
+tms_status encode_tmap_rows_chunks(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int nchunks,
+                                   uint64_t rows, uint64_t row_bytes, uint32_t box_rows) {
+    if (!load_encoder()) return TMS_ERR_CUDA;
+    const cuuint64_t dims[3] = {64, rows > 0 ? rows : 1, static_cast<cuuint64_t>(nchunks)};
+    const cuuint64_t strides[2] = {row_bytes, 128};
+    const cuuint32_t box[3] = {64, box_rows, 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, dtype, 3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? TMS_OK : TMS_ERR_INVALID_ARG;
+}
+
 tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
                           uint64_t rows, uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows) {
-    {
-        std::lock_guard<std::mutex> lock(g_mutex);
-        if (g_encode == nullptr) {
-            void* fn = nullptr;
-            cudaDriverEntryPointQueryResult q{};
-            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                    cudaSuccess ||
-                q != cudaDriverEntryPointSuccess || fn == nullptr) {
-                (void)cudaGetLastError();
-                return TMS_ERR_CUDA;
-            }
-            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-        }
-    }
+    if (!load_encoder()) return TMS_ERR_CUDA;
     // A zero-row tensor is not encodable; callers never load from it then,
     // so describe one row (the box reads zero fill beyond it).
     const cuuint64_t dims[2] = {cols, rows > 0 ? rows : 1};

@@ -42,9 +42,13 @@ namespace dense {
 
 constexpr int kRows = 128;                    // document rows per tile (MMA M)
 constexpr int kChunkElems = 64;               // elements per dimension chunk (one 128-B swizzle row)
-constexpr int kStageBytes = kRows * 128;      // 16 KB per stage
+constexpr int kChunkBytes = kRows * 128;      // 16 KB: 128 rows x one 64-element chunk
+constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kInfoRing = 16;
-constexpr int kThreads = 192;                 // 6 warps
+// Epilogue groups of 4 warps that alternate documents: two when the query
+// tile is at most 64 wide, one above (register budget).
+__host__ __device__ constexpr int epi_groups(int NT) { return NT <= 64 ? 2 : 1; }
+__host__ __device__ constexpr int num_threads(int NT) { return 64 + 128 * epi_groups(NT); }
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
 
@@ -70,6 +74,7 @@ struct Args {
     int n_queries;
     int nq;
     int nchunks;   // ceil(d / 64)
+    int cps;       // dimension chunks per stage: 2 with the 3-D tensor view (d % 64 == 0), else 1
     int stages;
     int qslots;
     uint32_t idesc;
@@ -80,20 +85,20 @@ struct Layout {
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
-__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int NT, int acc) {
+__host__ __device__ inline Layout make_layout(int stages, int cps, int qslots, int nchunks, int NT, int acc) {
     Layout L;
     L.stage_off = 0;
-    L.q_off = stages * kStageBytes;
+    L.q_off = stages * cps * kChunkBytes;
     L.part_off = L.q_off + qslots * nchunks * NT * 128;
-    L.info_off = L.part_off + 2 * 4 * NT * 4;
+    L.info_off = L.part_off + epi_groups(NT) * 2 * 4 * NT * 4;
     L.bar_off = L.info_off + kInfoRing * 16;
-    const int nbar = 2 * stages + 2 * acc + 2 * qslots + 2 * kInfoRing + 4 + 1;
+    const int nbar = 2 * stages + 2 * acc + 2 * qslots + 2 * kInfoRing + epi_groups(NT) * 4 + 1;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
 }
 
-__host__ __device__ constexpr int acc_buffers(int NT) { return NT <= 64 ? 4 : 2; }
+__host__ __device__ constexpr int acc_buffers(int NT) { return NT <= 32 ? 8 : (NT <= 64 ? 4 : 2); }
 
 __host__ __device__ constexpr int tmem_cols(int NT) {
     return (acc_buffers(NT) * NT <= 32) ? 32
@@ -152,13 +157,22 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
     }
 }
 
+// Tensor maps of one launch.  doc[h] covers document rows with a box of
+// 8 (h + 1) rows, so a tile of r rows is always ONE box (at most 7 rows of
+// over-fetch).  With cps == 2 the document maps are the 3-D view
+// {64 elements, rows, chunk} of the [n_tokens][d] array (chunk stride 128
+// bytes): one box brings two 64-element chunks of r rows, landing as
+// [chunk][row][128 B] -- already the 128-byte-swizzle K-major layout.
+struct Maps {
+    CUtensorMap q;
+    CUtensorMap doc[kBoxKinds];
+};
+
 template <int NB>
-__global__ void __launch_bounds__(kThreads, 1)
-    dense_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_d8,
-                    const __grid_constant__ CUtensorMap tm_d16, const __grid_constant__ CUtensorMap tm_d32,
-                    const __grid_constant__ CUtensorMap tm_d64, const __grid_constant__ CUtensorMap tm_d128,
-                    const Args a) {
+__global__ void __launch_bounds__(num_threads(NB * 32), 1)
+    dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
     constexpr int NT = NB * 32;
+    constexpr int kEpiGroups = epi_groups(NT);
     constexpr int A = acc_buffers(NT);
     constexpr uint32_t TCOLS = tmem_cols(NT);
 
@@ -167,11 +181,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int S = a.stages;
     const int QS = a.qslots;
     const int NCH = a.nchunks;
-    const Layout L = make_layout(S, QS, NCH, NT, A);
+    const int CPS = a.cps;
+    const int stage_bytes = CPS * kChunkBytes;
+    const int stages_per_tile = (NCH + CPS - 1) / CPS;
+    const Layout L = make_layout(S, CPS, QS, NCH, NT, A);
 
     uint8_t* stage_base = smem + L.stage_off;
     uint8_t* q_base = smem + L.q_off;
-    float* part = reinterpret_cast<float*>(smem + L.part_off);  // [2][4][NT]
+    float* part = reinterpret_cast<float*>(smem + L.part_off);  // [group][2][4][NT]
     TileInfo* info = reinterpret_cast<TileInfo*>(smem + L.info_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;
@@ -182,9 +199,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* qempty = qfull + QS;
     uint64_t* ifull = qempty + QS;
     uint64_t* iempty = ifull + kInfoRing;
-    uint64_t* pfull = iempty + kInfoRing;
-    uint64_t* pempty = pfull + 2;
-    uint64_t* mdone = pempty + 2;
+    uint64_t* pfull = iempty + kInfoRing;       // [group][2]
+    uint64_t* pempty = pfull + 2 * kEpiGroups;  // [group][2]
+    uint64_t* mdone = pempty + 2 * kEpiGroups;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
 
@@ -206,9 +223,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int i = 0; i < kInfoRing; ++i) {
             mbar_init(&ifull[i], 1);
-            mbar_init(&iempty[i], 5);
+            mbar_init(&iempty[i], 1 + 4 * kEpiGroups);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < 2 * kEpiGroups; ++i) {
             mbar_init(&pfull[i], 4);
             mbar_init(&pempty[i], 1);
         }
@@ -216,13 +233,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) {
-        prefetch_tensormap(&tm_q);
-        prefetch_tensormap(&tm_d8);
-        prefetch_tensormap(&tm_d16);
-        prefetch_tensormap(&tm_d32);
-        prefetch_tensormap(&tm_d64);
-        prefetch_tensormap(&tm_d128);
+    if (warp == 0) {
+        if (lane <= kBoxKinds) prefetch_tensormap(lane == 0 ? &maps.q : &maps.doc[lane - 1]);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, TCOLS);
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(NCH * NT * 128));
                             uint8_t* qdst = q_base + slot * NCH * NT * 128;
                             for (int kc = 0; kc < NCH; ++kc)
-                                tma_load_2d(qdst + kc * NT * 128, &tm_q, kc * kChunkElems, q * a.nq,
+                                tma_load_2d(qdst + kc * NT * 128, &maps.q, kc * kChunkElems, q * a.nq,
                                             &qfull[slot], pol_keep);
                         }
                         ++qi;
@@ -317,35 +329,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     const int n8 = (r + 7) & ~7;
                     const int y0 = static_cast<int>(off) + r0;
-                    for (int kc = 0; kc < NCH; ++kc) {
+                    const CUtensorMap* dmap = &maps.doc[(n8 >> 3) - 1];
+                    for (int st = 0; st < stages_per_tile; ++st) {
                         if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
                             aborted = true;
                             break;
                         }
                         if (lane == 0) {
-                            uint8_t* dst = stage_base + s * kStageBytes;
-                            const int x = kc * kChunkElems;
-                            mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(n8 * 128));
-                            if (n8 == 128) {
-                                tma_load_2d(dst, &tm_d128, x, y0, &full[s], pol_stream);
-                            } else {
-                                int rows = 0;
-                                if (n8 & 64) {
-                                    tma_load_2d(dst, &tm_d64, x, y0, &full[s], pol_stream);
-                                    rows += 64;
-                                }
-                                if (n8 & 32) {
-                                    tma_load_2d(dst + rows * 128, &tm_d32, x, y0 + rows, &full[s], pol_stream);
-                                    rows += 32;
-                                }
-                                if (n8 & 16) {
-                                    tma_load_2d(dst + rows * 128, &tm_d16, x, y0 + rows, &full[s], pol_stream);
-                                    rows += 16;
-                                }
-                                if (n8 & 8) {
-                                    tma_load_2d(dst + rows * 128, &tm_d8, x, y0 + rows, &full[s], pol_stream);
-                                }
-                            }
+                            uint8_t* dst = stage_base + s * stage_bytes;
+                            mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(n8 * 128 * CPS));
+                            if (CPS == 2)
+                                tma_load_3d(dst, dmap, 0, y0, 2 * st, &full[s], pol_stream);
+                            else
+                                tma_load_2d(dst, dmap, st * kChunkElems, y0, &full[s], pol_stream);
                         }
                         ++issued;
                         if (++s == S) {
@@ -418,19 +414,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * NT);
             const uint32_t q_addr = smem_u32(q_base + qslot * NCH * NT * 128);
-            for (int kc = 0; kc < NCH; ++kc) {
+            const int n8 = (ti.r + 7) & ~7;
+            for (int st = 0; st < stages_per_tile; ++st) {
                 if (!warp_wait(&full[s], ph, abort_flag, a.err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 if (lane == 0) {
-                    const uint32_t a_addr = smem_u32(stage_base + s * kStageBytes);
-                    const uint32_t b_addr = q_addr + kc * NT * 128;
+                    // chunk c of the stage starts c * n8 rows in: its rows
+                    // past n8 (and the tile's rows past r) are masked later.
+                    const uint32_t s_addr = smem_u32(stage_base + s * stage_bytes);
+                    for (int c = 0; c < CPS; ++c) {
+                        const int kc = st * CPS + c;
+                        if (kc >= NCH) break;
+                        const uint32_t a_addr = s_addr + c * n8 * 128;
+                        const uint32_t b_addr = q_addr + kc * NT * 128;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        mma_f16(d_tmem, desc_sw128(a_addr + kk * 32), desc_sw128(b_addr + kk * 32), a.idesc,
-                                (kc | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_f16(d_tmem, desc_sw128(a_addr + kk * 32), desc_sw128(b_addr + kk * 32), a.idesc,
+                                    (kc | kk) != 0 ? 1u : 0u);
+                    }
                     mma_commit(&empty[s]);
                 }
                 __syncwarp();
@@ -460,7 +464,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // per column whose member mask is exactly those rows, so rows past
         // the document end never take part; the running maxima are held
         // warp-uniform (lane 0 always participates when any row is valid).
+        // Group g (warps 2+4g .. 5+4g) takes the documents whose ordinal is
+        // g mod kEpiGroups; both groups read every tile's info.
         const int qd = warp & 3;  // TMEM lane quadrant this warp may read
+        const int grp = (warp - 2) >> 2;
+        float* gpart = part + grp * 2 * 4 * NT;
+        uint64_t* gpfull = pfull + 2 * grp;
+        uint64_t* gpempty = pempty + 2 * grp;
+        uint32_t doc_ord = 0;  // ordinal of the current document (all groups count all documents)
+        bool mine = false;
         float rm[NB][32];
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -476,12 +488,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive(&iempty[ii]);
             if (ti.flags & kEnd) break;
             if (ti.flags & kFirst) {
+                mine = (doc_ord % kEpiGroups) == static_cast<uint32_t>(grp);
+                ++doc_ord;
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
 #pragma unroll
                     for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
             }
             const int ab = acc % A;
+            if (!mine) {  // another group's tile: only keep the accumulator count
+                ++acc;
+                continue;
+            }
             if (!warp_wait(&tfull[ab], (acc / A) & 1, abort_flag, a.err)) break;
             tc_fence_after();
             const int rows_here = ti.r - qd * 32;
@@ -506,8 +524,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (ti.flags & kLast) {
                 const int pb = docs & 1;
                 const uint32_t use = docs >> 1;
-                if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
-                float* pp = part + pb * 4 * NT;
+                if (!warp_wait(&gpempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
+                float* pp = gpart + pb * 4 * NT;
                 if (lane == 0) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
@@ -517,9 +535,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 make_float4(rm[b][c], rm[b][c + 1], rm[b][c + 2], rm[b][c + 3]);
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&pfull[pb]);
+                if (lane == 0) mbar_arrive(&gpfull[pb]);
                 if (qd == 0) {
-                    if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) break;
+                    if (!warp_wait(&gpfull[pb], use & 1, abort_flag, a.err)) break;
                     float sum = 0.f;
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
@@ -530,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     sum = warp_sum(sum);
                     if (lane == 0) a.out[ti.f] = sum;
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&pempty[pb]);
+                    if (lane == 0) mbar_arrive(&gpempty[pb]);
                 }
                 ++docs;
             }
@@ -655,35 +673,38 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     constexpr int A = acc_buffers(NT);
     const CUtensorMapDataType tdt = dtype == TMS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const uint64_t row_bytes = static_cast<uint64_t>(d) * 2;
-    CUtensorMap tq, t8, t16, t32, t64, t128;
-    tms_status st;
-    if ((st = encode_tmap_2d(&tq, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes, kChunkElems, NT)) != TMS_OK ||
-        (st = encode_tmap_2d(&t8, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 8)) != TMS_OK ||
-        (st = encode_tmap_2d(&t16, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 16)) != TMS_OK ||
-        (st = encode_tmap_2d(&t32, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 32)) != TMS_OK ||
-        (st = encode_tmap_2d(&t64, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 64)) != TMS_OK ||
-        (st = encode_tmap_2d(&t128, tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, 128)) != TMS_OK)
-        return st;
+    Maps maps;
+    tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
+                                   kChunkElems, NT);
+    if (st != TMS_OK) return st;
+    a.cps = (d % kChunkElems == 0 && a.nchunks >= 2) ? 2 : 1;
+    for (int h = 0; h < kBoxKinds; ++h) {
+        const uint32_t rows = static_cast<uint32_t>(8 * (h + 1));
+        st = a.cps == 2 ? encode_tmap_rows_chunks(&maps.doc[h], tdt, doc_tokens, a.nchunks, n_tokens, row_bytes, rows)
+                        : encode_tmap_2d(&maps.doc[h], tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, rows);
+        if (st != TMS_OK) return st;
+    }
+    const int stage_bytes = a.cps * kChunkBytes;
     const int limit = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
     int qslots = 2, stages = 0;
     for (; qslots >= 1; --qslots) {
-        const Layout L0 = make_layout(0, qslots, a.nchunks, NT, A);
+        const Layout L0 = make_layout(0, a.cps, qslots, a.nchunks, NT, A);
         // each stage also adds two barriers (16 bytes)
-        stages = std::min(kMaxStages, (limit - L0.total) / (kStageBytes + 16));
-        if (stages >= 4) break;
+        stages = std::min(kMaxStages, (limit - L0.total) / (stage_bytes + 16));
+        if (stages * a.cps >= 6) break;
     }
-    if (stages < 3) return TMS_ERR_UNSUPPORTED;
     if (qslots < 1) qslots = 1;
+    if (stages < 2) return TMS_ERR_UNSUPPORTED;
     a.stages = stages;
     a.qslots = qslots;
     a.idesc = make_idesc(kRows, NT, dtype == TMS_BF16 ? 1u : 0u);
-    const Layout L = make_layout(stages, qslots, a.nchunks, NT, A);
+    const Layout L = make_layout(stages, a.cps, qslots, a.nchunks, NT, A);
     const int smem = L.total + 1024;
     auto kern = dense_tc_kernel<NB>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
     const int64_t grid = std::min<int64_t>(dev.sm_count, a.n_cand);
-    kern<<<static_cast<unsigned>(grid), kThreads, smem, stream>>>(tq, t8, t16, t32, t64, t128, a);
+    kern<<<static_cast<unsigned>(grid), num_threads(NT), smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
 }
 
