@@ -98,13 +98,19 @@ __host__ __device__ inline Layout make_layout(int stages, int cps, int qslots, i
     return L;
 }
 
-__host__ __device__ constexpr int acc_buffers(int NT) { return NT <= 32 ? 8 : (NT <= 64 ? 4 : 2); }
+// A tile's K-steps are spread round-robin over `partials(NT)` accumulators
+// so that consecutive MMAs never depend on each other (a chain of tiny
+// M=128 x N=32 x K=16 MMAs into one accumulator is latency-bound); the
+// epilogue adds the partials before the max.  acc_buffers tiles are in
+// flight, each owning partials * NT TMEM columns.
+__host__ __device__ constexpr int partials(int NT) { return NT <= 64 ? 4 : 2; }
+__host__ __device__ constexpr int acc_buffers(int NT) { return NT <= 32 ? 4 : 2; }
 
 __host__ __device__ constexpr int tmem_cols(int NT) {
-    return (acc_buffers(NT) * NT <= 32) ? 32
-         : (acc_buffers(NT) * NT <= 64) ? 64
-         : (acc_buffers(NT) * NT <= 128) ? 128
-         : (acc_buffers(NT) * NT <= 256) ? 256 : 512;
+    return (acc_buffers(NT) * partials(NT) * NT <= 32) ? 32
+         : (acc_buffers(NT) * partials(NT) * NT <= 64) ? 64
+         : (acc_buffers(NT) * partials(NT) * NT <= 128) ? 128
+         : (acc_buffers(NT) * partials(NT) * NT <= 256) ? 256 : 512;
 }
 
 // Candidate metadata for the producer: lane l of the warp holds the raw
@@ -174,6 +180,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
     constexpr int NT = NB * 32;
     constexpr int kEpiGroups = epi_groups(NT);
     constexpr int A = acc_buffers(NT);
+    constexpr int P = partials(NT);
     constexpr uint32_t TCOLS = tmem_cols(NT);
 
     extern __shared__ uint8_t smem_raw[];
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
             if (!warp_wait(&tempty[ab], ((acc / A) & 1) ^ 1, abort_flag, a.err)) break;
             tc_fence_after();
             bool ok = true;
-            const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * NT);
+            const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * P * NT);
             const uint32_t q_addr = smem_u32(q_base + qslot * NCH * NT * 128);
             const int n8 = (ti.r + 7) & ~7;
             for (int st = 0; st < stages_per_tile; ++st) {
@@ -432,8 +439,11 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
                         const uint32_t b_addr = q_addr + kc * NT * 128;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_f16(d_tmem, desc_sw128(a_addr + kk * 32), desc_sw128(b_addr + kk * 32), a.idesc,
-                                    (kc | kk) != 0 ? 1u : 0u);
+                        {
+                            const int ks = kc * 4 + kk;  // K-step of the tile
+                            mma_f16(d_tmem + static_cast<uint32_t>((ks % P) * NT), desc_sw128(a_addr + kk * 32),
+                                    desc_sw128(b_addr + kk * 32), a.idesc, ks >= P ? 1u : 0u);
+                        }
                     }
                     mma_commit(&empty[s]);
                 }
@@ -503,13 +513,25 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
             if (!warp_wait(&tfull[ab], (acc / A) & 1, abort_flag, a.err)) break;
             tc_fence_after();
             const int rows_here = ti.r - qd * 32;
+            const int ksteps = NCH * 4;
             if (rows_here > 0) {
                 const unsigned vmask = rows_here >= 32 ? 0xffffffffu : ((1u << rows_here) - 1u);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
+                    // sum the partial accumulators that received any K-step
+                    const uint32_t tl = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
+                                        static_cast<uint32_t>(ab * P * NT + b * 32);
                     float v[32];
-                    tmem_ld32(tbase + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(ab * NT + b * 32),
-                              v);
+                    tmem_ld32(tl, v);
+#pragma unroll
+                    for (int pp = 1; pp < P; ++pp) {
+                        if (pp < ksteps) {
+                            float w[32];
+                            tmem_ld32(tl + static_cast<uint32_t>(pp * NT), w);
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) v[c] += w[c];
+                        }
+                    }
                     if (lane < rows_here) {
 #pragma unroll
                         for (int c = 0; c < 32; ++c) rm[b][c] = fmaxf(rm[b][c], redux_max(v[c], vmask));
