@@ -101,16 +101,23 @@ __host__ __device__ inline Layout make_layout(int stages, int cps, int qslots, i
 // A tile's K-steps are spread round-robin over `partials(NT)` accumulators
 // so that consecutive MMAs never depend on each other (a chain of tiny
 // M=128 x N=32 x K=16 MMAs into one accumulator is latency-bound); the
-// epilogue adds the partials before the max.  acc_buffers tiles are in
-// flight, each owning partials * NT TMEM columns.
-__host__ __device__ constexpr int partials(int NT) { return NT <= 64 ? 4 : 2; }
-__host__ __device__ constexpr int acc_buffers(int NT) { return NT <= 32 ? 4 : 2; }
+// epilogue adds the partials before the max.
+//
+// Each epilogue group owns its own ring of acc_buffers(NT) accumulators,
+// used in the order of that group's tiles.  (With one shared ring a group
+// that skips the other group's tiles could wait on the second use of an
+// accumulator whose barrier has not finished its first phase -- and an
+// mbarrier parity wait cannot tell those apart.)
+__host__ __device__ constexpr int partials(int NT) { return NT <= 32 ? 4 : 2; }
+__host__ __device__ constexpr int acc_buffers(int NT) { return 2; }
+
+__host__ __device__ constexpr int acc_total(int NT) { return epi_groups(NT) * acc_buffers(NT); }
 
 __host__ __device__ constexpr int tmem_cols(int NT) {
-    return (acc_buffers(NT) * partials(NT) * NT <= 32) ? 32
-         : (acc_buffers(NT) * partials(NT) * NT <= 64) ? 64
-         : (acc_buffers(NT) * partials(NT) * NT <= 128) ? 128
-         : (acc_buffers(NT) * partials(NT) * NT <= 256) ? 256 : 512;
+    return (acc_total(NT) * partials(NT) * NT <= 32) ? 32
+         : (acc_total(NT) * partials(NT) * NT <= 64) ? 64
+         : (acc_total(NT) * partials(NT) * NT <= 128) ? 128
+         : (acc_total(NT) * partials(NT) * NT <= 256) ? 256 : 512;
 }
 
 // Candidate metadata for the producer: lane l of the warp holds the raw
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
     dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
     constexpr int NT = NB * 32;
     constexpr int kEpiGroups = epi_groups(NT);
-    constexpr int A = acc_buffers(NT);
+    constexpr int A = acc_buffers(NT);   // per epilogue group
     constexpr int P = partials(NT);
     constexpr uint32_t TCOLS = tmem_cols(NT);
 
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
     const int CPS = a.cps;
     const int stage_bytes = CPS * kChunkBytes;
     const int stages_per_tile = (NCH + CPS - 1) / CPS;
-    const Layout L = make_layout(S, CPS, QS, NCH, NT, A);
+    const Layout L = make_layout(S, CPS, QS, NCH, NT, acc_total(NT));
 
     uint8_t* stage_base = smem + L.stage_off;
     uint8_t* q_base = smem + L.q_off;
@@ -201,8 +208,8 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
     uint64_t* full = bars;
     uint64_t* empty = full + S;
     uint64_t* tfull = empty + S;
-    uint64_t* tempty = tfull + A;
-    uint64_t* qfull = tempty + A;
+    uint64_t* tempty = tfull + acc_total(NT);
+    uint64_t* qfull = tempty + acc_total(NT);
     uint64_t* qempty = qfull + QS;
     uint64_t* ifull = qempty + QS;
     uint64_t* iempty = ifull + kInfoRing;
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < A; ++i) {
+        for (int i = 0; i < acc_total(NT); ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], 4);
         }
@@ -399,7 +406,9 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
         int s = 0;
         uint32_t ph = 0;
         int qi = 0, cur_q = -1, qslot = 0;
-        int acc = 0;
+        int acc0 = 0, acc1 = 0;   // tiles issued for epilogue group 0 / 1
+        uint32_t doc_ord = 0;
+        int owner = 0;
         bool any = false;
         for (int t = 0;; ++t) {
             const int ii = t % kInfoRing;
@@ -415,8 +424,13 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
                 ++qi;
                 cur_q = ti.q;
             }
-            const int ab = acc % A;
-            if (!warp_wait(&tempty[ab], ((acc / A) & 1) ^ 1, abort_flag, a.err)) break;
+            if (ti.flags & kFirst) {
+                owner = static_cast<int>(doc_ord % kEpiGroups);
+                ++doc_ord;
+            }
+            const int k = owner == 0 ? acc0 : acc1;
+            const int ab = owner * A + k % A;
+            if (!warp_wait(&tempty[ab], ((k / A) & 1) ^ 1, abort_flag, a.err)) break;
             tc_fence_after();
             bool ok = true;
             const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * P * NT);
@@ -457,7 +471,10 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
             if (!ok) break;
             if (lane == 0) mma_commit(&tfull[ab]);
             __syncwarp();
-            ++acc;
+            if (owner == 0)
+                ++acc0;
+            else
+                ++acc1;
         }
         // Every MMA this thread issued must finish before TMEM is freed.
         if (any) {
@@ -505,11 +522,8 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
 #pragma unroll
                     for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
             }
-            const int ab = acc % A;
-            if (!mine) {  // another group's tile: only keep the accumulator count
-                ++acc;
-                continue;
-            }
+            if (!mine) continue;  // another group's tile
+            const int ab = grp * A + acc % A;
             if (!warp_wait(&tfull[ab], (acc / A) & 1, abort_flag, a.err)) break;
             tc_fence_after();
             const int rows_here = ti.r - qd * 32;
@@ -692,7 +706,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
                      const void* doc_tokens, int64_t n_tokens, dense::Args a, cudaStream_t stream) {
     using namespace dense;
     constexpr int NT = NB * 32;
-    constexpr int A = acc_buffers(NT);
+    constexpr int A = acc_total(NT);   // all epilogue groups
     const CUtensorMapDataType tdt = dtype == TMS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const uint64_t row_bytes = static_cast<uint64_t>(d) * 2;
     Maps maps;
