@@ -403,82 +403,79 @@ __global__ void __launch_bounds__(num_threads(NB * 32), 1)
         __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA
-        int s = 0;
-        uint32_t ph = 0;
-        int qi = 0, cur_q = -1, qslot = 0;
-        int acc0 = 0, acc1 = 0;   // tiles issued for epilogue group 0 / 1
-        uint32_t doc_ord = 0;
-        int owner = 0;
-        bool any = false;
-        for (int t = 0;; ++t) {
-            const int ii = t % kInfoRing;
-            if (!warp_wait(&ifull[ii], (t / kInfoRing) & 1, abort_flag, a.err)) break;
-            const TileInfo ti = info[ii];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&iempty[ii]);
-            if (ti.flags & kEnd) break;
-            if (ti.q != cur_q) {
-                if (cur_q >= 0 && lane == 0) mma_commit(&qempty[qslot]);
-                qslot = qi % QS;
-                if (!warp_wait(&qfull[qslot], (qi / QS) & 1, abort_flag, a.err)) break;
-                ++qi;
-                cur_q = ti.q;
-            }
-            if (ti.flags & kFirst) {
-                owner = static_cast<int>(doc_ord % kEpiGroups);
-                ++doc_ord;
-            }
-            const int k = owner == 0 ? acc0 : acc1;
-            const int ab = owner * A + k % A;
-            if (!warp_wait(&tempty[ab], ((k / A) & 1) ^ 1, abort_flag, a.err)) break;
-            tc_fence_after();
-            bool ok = true;
-            const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * P * NT);
-            const uint32_t q_addr = smem_u32(q_base + qslot * NCH * NT * 128);
-            const int n8 = (ti.r + 7) & ~7;
-            for (int st = 0; st < stages_per_tile; ++st) {
-                if (!warp_wait(&full[s], ph, abort_flag, a.err)) {
-                    ok = false;
-                    break;
+        // One thread runs this role: every wait is its own (no warp votes),
+        // and descriptors advance by adding the 16-byte-unit offset of each
+        // K-step to a per-stage base.
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int qi = 0, cur_q = -1, qslot = 0;
+            int acc0 = 0, acc1 = 0;  // tiles issued for epilogue group 0 / 1
+            uint32_t doc_ord = 0;
+            int owner = 0;
+            bool any = false;
+            for (int t = 0;; ++t) {
+                const int ii = t % kInfoRing;
+                if (!mbar_wait(&ifull[ii], (t / kInfoRing) & 1, abort_flag, a.err)) break;
+                const TileInfo ti = info[ii];
+                mbar_arrive(&iempty[ii]);
+                if (ti.flags & kEnd) break;
+                if (ti.q != cur_q) {
+                    if (cur_q >= 0) mma_commit(&qempty[qslot]);
+                    qslot = qi % QS;
+                    if (!mbar_wait(&qfull[qslot], (qi / QS) & 1, abort_flag, a.err)) break;
+                    ++qi;
+                    cur_q = ti.q;
                 }
+                if (ti.flags & kFirst) {
+                    owner = static_cast<int>(doc_ord % kEpiGroups);
+                    ++doc_ord;
+                }
+                const int k = owner == 0 ? acc0 : acc1;
+                const int ab = owner * A + k % A;
+                if (!mbar_wait(&tempty[ab], ((k / A) & 1) ^ 1, abort_flag, a.err)) break;
                 tc_fence_after();
-                if (lane == 0) {
+                bool ok = true;
+                const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * P * NT);
+                const uint64_t q_desc = desc_sw128(smem_u32(q_base + qslot * NCH * NT * 128));
+                const int n8 = (ti.r + 7) & ~7;
+                for (int st = 0; st < stages_per_tile; ++st) {
+                    if (!mbar_wait(&full[s], ph, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     // chunk c of the stage starts c * n8 rows in: its rows
                     // past n8 (and the tile's rows past r) are masked later.
-                    const uint32_t s_addr = smem_u32(stage_base + s * stage_bytes);
+                    const uint64_t s_desc = desc_sw128(smem_u32(stage_base + s * stage_bytes));
                     for (int c = 0; c < CPS; ++c) {
                         const int kc = st * CPS + c;
                         if (kc >= NCH) break;
-                        const uint32_t a_addr = s_addr + c * n8 * 128;
-                        const uint32_t b_addr = q_addr + kc * NT * 128;
+                        const uint64_t a_desc = s_desc + static_cast<uint64_t>((c * n8 * 128) >> 4);
+                        const uint64_t b_desc = q_desc + static_cast<uint64_t>((kc * NT * 128) >> 4);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                        {
+                        for (int kk = 0; kk < 4; ++kk) {
                             const int ks = kc * 4 + kk;  // K-step of the tile
-                            mma_f16(d_tmem + static_cast<uint32_t>((ks % P) * NT), desc_sw128(a_addr + kk * 32),
-                                    desc_sw128(b_addr + kk * 32), a.idesc, ks >= P ? 1u : 0u);
+                            mma_f16(d_tmem + static_cast<uint32_t>((ks % P) * NT), a_desc + 2 * kk, b_desc + 2 * kk,
+                                    a.idesc, ks >= P ? 1u : 0u);
                         }
                     }
                     mma_commit(&empty[s]);
+                    any = true;
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1;
+                    }
                 }
-                __syncwarp();
-                any = true;
-                if (++s == S) {
-                    s = 0;
-                    ph ^= 1;
-                }
+                if (!ok) break;
+                mma_commit(&tfull[ab]);
+                if (owner == 0)
+                    ++acc0;
+                else
+                    ++acc1;
             }
-            if (!ok) break;
-            if (lane == 0) mma_commit(&tfull[ab]);
-            __syncwarp();
-            if (owner == 0)
-                ++acc0;
-            else
-                ++acc1;
-        }
-        // Every MMA this thread issued must finish before TMEM is freed.
-        if (any) {
-            if (lane == 0) {
+            // Every MMA this thread issued must finish before TMEM is freed.
+            if (any) {
                 mma_commit(mdone);
                 drain_wait(mdone, 0);
             }
