@@ -47,7 +47,13 @@ constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kInfoRing = 16;
 // Epilogue groups of 4 warps that alternate documents: two when the query
 // tile is at most 64 wide, one above (register budget).
-__host__ __device__ constexpr int epi_groups(int NT) { return NT <= 64 ? 2 : 1; }
+// One epilogue group of 4 warps per CTA.  (The kernel keeps the general
+// multi-group bookkeeping; two CTAs per SM -- each a full producer / MMA /
+// epilogue pipeline -- replace a second group: the tensor core accepts one
+// small MMA per ~84 cycles whatever its N, and the issuing thread blocks
+// meanwhile, so a second CTA's MMA thread fills the tensor pipe while the
+// first one waits or does its per-tile bookkeeping.)
+__host__ __device__ constexpr int epi_groups(int NT) { return 1; }
 __host__ __device__ constexpr int num_threads(int NT) { return 64 + 128 * epi_groups(NT); }
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
@@ -181,8 +187,8 @@ struct Maps {
     CUtensorMap doc[kBoxKinds];
 };
 
-template <int NB>
-__global__ void __launch_bounds__(num_threads(NB * 32), 1)
+template <int NB, int CTAS>
+__global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
     dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
     constexpr int NT = NB * 32;
     constexpr int kEpiGroups = epi_groups(NT);
@@ -718,25 +724,34 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         if (st != TMS_OK) return st;
     }
     const int stage_bytes = a.cps * kChunkBytes;
-    const int limit = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
-    int qslots = 2, stages = 0;
-    for (; qslots >= 1; --qslots) {
-        const Layout L0 = make_layout(0, a.cps, qslots, a.nchunks, NT, A);
-        // each stage also adds two barriers (16 bytes)
-        stages = std::min(kMaxStages, (limit - L0.total) / (stage_bytes + 16));
-        if (stages * a.cps >= 6) break;
+    a.idesc = make_idesc(kRows, NT, dtype == TMS_BF16 ? 1u : 0u);
+    // Pick the shared-memory plan: two CTAs per SM when each still gets a
+    // useful ring (at least 4 dimension chunks of stages), else one.
+    auto plan = [&](int per_cta_limit, int min_chunks, int& stages, int& qslots) {
+        for (qslots = 2; qslots >= 1; --qslots) {
+            const Layout L0 = make_layout(0, a.cps, qslots, a.nchunks, NT, A);
+            stages = std::min(kMaxStages, (per_cta_limit - L0.total) / (stage_bytes + 16));
+            if (stages * a.cps >= min_chunks) return true;
+        }
+        qslots = 1;
+        return stages >= 2;
+    };
+    int stages = 0, qslots = 1, ctas = 1;
+    const int limit1 = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
+    const int limit2 = dev.smem_per_sm / 2 - dev.smem_reserved - 1024;
+    if (NT <= 64 && plan(limit2, 4, stages, qslots) && stages * a.cps >= 4) {
+        ctas = 2;
+    } else if (!plan(limit1, 6, stages, qslots)) {
+        return TMS_ERR_UNSUPPORTED;
     }
-    if (qslots < 1) qslots = 1;
-    if (stages < 2) return TMS_ERR_UNSUPPORTED;
     a.stages = stages;
     a.qslots = qslots;
-    a.idesc = make_idesc(kRows, NT, dtype == TMS_BF16 ? 1u : 0u);
     const Layout L = make_layout(stages, a.cps, qslots, a.nchunks, NT, A);
     const int smem = L.total + 1024;
-    auto kern = dense_tc_kernel<NB>;
+    auto kern = ctas == 2 ? dense_tc_kernel<NB, (NB <= 2 ? 2 : 1)> : dense_tc_kernel<NB, 1>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
-    const int64_t grid = std::min<int64_t>(dev.sm_count, a.n_cand);
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_cand);
     kern<<<static_cast<unsigned>(grid), num_threads(NT), smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
 }

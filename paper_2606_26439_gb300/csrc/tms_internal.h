@@ -14,6 +14,8 @@ struct DeviceInfo {
     int ordinal;
     int sm_count;
     int max_smem_optin;       // largest dynamic shared memory a CTA may request
+    int smem_per_sm;          // shared memory of one SM
+    int smem_reserved;        // shared memory the system reserves per CTA
     unsigned int* err;        // device address of the error word (file-scope __device__)
 };
 
