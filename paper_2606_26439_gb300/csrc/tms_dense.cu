@@ -716,34 +716,46 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
                                    kChunkElems, NT);
     if (st != TMS_OK) return st;
-    a.cps = (d % kChunkElems == 0 && a.nchunks >= 2) ? 2 : 1;
+    // Shared-memory plan.  Prefer two CTAs per SM (NT <= 64) when each
+    // still gets a ring of at least 4 dimension chunks; within a plan take
+    // the query-slot count (2, else 1) that gives the most stage chunks.
+    const bool can3d = d % kChunkElems == 0 && a.nchunks >= 2;
+    auto plan = [&](int per_cta_limit, int cps, int& stages, int& qslots) {
+        int best = -1;
+        for (int qs = 2; qs >= 1; --qs) {
+            const Layout L0 = make_layout(0, cps, qs, a.nchunks, NT, A);
+            const int sts = std::min(kMaxStages, (per_cta_limit - L0.total) / (cps * kChunkBytes + 16));
+            if (sts * cps > best) {
+                best = sts * cps;
+                stages = sts;
+                qslots = qs;
+            }
+        }
+        return best;
+    };
+    int stages = 0, qslots = 1, ctas = 1;
+    const int limit1 = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
+    const int limit2 = dev.smem_per_sm / 2 - dev.smem_reserved - 1024;
+    a.cps = can3d ? 2 : 1;
+    if (NT <= 64 && plan(limit2, a.cps, stages, qslots) >= 4 && stages >= 2) {
+        ctas = 2;
+    } else if (NT <= 64 && can3d && plan(limit2, 1, stages, qslots) >= 4) {
+        ctas = 2;
+        a.cps = 1;
+    } else {
+        a.cps = can3d ? 2 : 1;
+        if (plan(limit1, a.cps, stages, qslots) < 2 || stages < 2) {
+            a.cps = 1;
+            if (plan(limit1, 1, stages, qslots) < 2) return TMS_ERR_UNSUPPORTED;
+        }
+    }
     for (int h = 0; h < kBoxKinds; ++h) {
         const uint32_t rows = static_cast<uint32_t>(8 * (h + 1));
         st = a.cps == 2 ? encode_tmap_rows_chunks(&maps.doc[h], tdt, doc_tokens, a.nchunks, n_tokens, row_bytes, rows)
                         : encode_tmap_2d(&maps.doc[h], tdt, doc_tokens, d, n_tokens, row_bytes, kChunkElems, rows);
         if (st != TMS_OK) return st;
     }
-    const int stage_bytes = a.cps * kChunkBytes;
     a.idesc = make_idesc(kRows, NT, dtype == TMS_BF16 ? 1u : 0u);
-    // Pick the shared-memory plan: two CTAs per SM when each still gets a
-    // useful ring (at least 4 dimension chunks of stages), else one.
-    auto plan = [&](int per_cta_limit, int min_chunks, int& stages, int& qslots) {
-        for (qslots = 2; qslots >= 1; --qslots) {
-            const Layout L0 = make_layout(0, a.cps, qslots, a.nchunks, NT, A);
-            stages = std::min(kMaxStages, (per_cta_limit - L0.total) / (stage_bytes + 16));
-            if (stages * a.cps >= min_chunks) return true;
-        }
-        qslots = 1;
-        return stages >= 2;
-    };
-    int stages = 0, qslots = 1, ctas = 1;
-    const int limit1 = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
-    const int limit2 = dev.smem_per_sm / 2 - dev.smem_reserved - 1024;
-    if (NT <= 64 && plan(limit2, 4, stages, qslots) && stages * a.cps >= 4) {
-        ctas = 2;
-    } else if (!plan(limit1, 6, stages, qslots)) {
-        return TMS_ERR_UNSUPPORTED;
-    }
     a.stages = stages;
     a.qslots = qslots;
     const Layout L = make_layout(stages, a.cps, qslots, a.nchunks, NT, A);

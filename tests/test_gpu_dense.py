@@ -16,7 +16,7 @@ from tests._common import assert_scores_close, assert_topk_consistent, oracle_vi
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(32, 128), (1, 64), (7, 72), (33, 200), (64, 384), (128, 128), (32, 768), (16, 8), (96, 256)]
+SHAPES = [(32, 128), (1, 64), (7, 72), (33, 200), (64, 384), (128, 128), (32, 768), (16, 8), (96, 256), (128, 768), (64, 512)]
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16", "f32"])
