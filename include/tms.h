@@ -74,7 +74,11 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
  *
  * Limits: 1 <= nq <= 128; 8 <= d <= 1024 with d % 8 == 0 (16-byte rows);
  * 1 <= n_queries <= 4096; n_tokens < 2^31; queries, doc_tokens and every
- * index array 16-byte aligned.  fp16/bf16 run on the tensor cores
+ * index array 16-byte aligned.  For fp16/bf16 the whole query tile stays
+ * in one CTA's shared memory next to at least two 16 KB stages: with nq
+ * rounded up to a multiple of 32 and d to a multiple of 64, their product
+ * must stay below 98,304 (nq 128 at d >= 768 and nq 96 at d 1024 return
+ * TMS_ERR_UNSUPPORTED).  fp16/bf16 run on the tensor cores
  * (tcgen05, fp32 accumulation in tensor memory); fp32 runs on an exact
  * fp32 path.  A candidate with a bad id or row range scores NaN and sets
  * TMS_DEVERR_BAD_ID / TMS_DEVERR_BAD_RANGE.
