@@ -232,6 +232,231 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel(const Args a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Staged variant for M in {16, 32}: every warp streams its documents' code
+// rows into a private double-buffered shared-memory piece buffer with
+// cp.async.bulk (TMA) and reads them back as broadcast 128-bit loads, so the
+// gather loop never waits on global memory.  While a piece is scored, the
+// warp has already issued the copy of the next piece (of this document or of
+// the next one, whose metadata was fetched one document ahead).
+constexpr int kPieceBytes = 2048;  // per buffer: 128 tokens at M = 16
+
+template <int M>
+__device__ __forceinline__ CodeRow<M> smem_codes(const uint8_t* row) {
+    CodeRow<M> c;
+    const uint4 v = *reinterpret_cast<const uint4*>(row);
+    c.w[0] = v.x;
+    c.w[1] = v.y;
+    c.w[2] = v.z;
+    c.w[3] = v.w;
+    if constexpr (M == 32) {
+        const uint4 u = *reinterpret_cast<const uint4*>(row + 16);
+        c.w[4] = u.x;
+        c.w[5] = u.y;
+        c.w[6] = u.z;
+        c.w[7] = u.w;
+    }
+    return c;
+}
+
+struct PendingMeta {
+    int64_t li;  // local candidate index (>= n_local: none)
+    int id;
+    int64_t off;
+    int len;
+};
+
+template <int M>
+__global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args a, int lut_bytes) {
+    constexpr int kPiece = kPieceBytes / M;  // tokens per piece
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    float* lut_s = reinterpret_cast<float*>(smem_raw);
+    uint8_t* bufs = smem_raw + lut_bytes;  // [kWarps][2][kPieceBytes]
+    __shared__ uint64_t bars[kWarps][2];
+    __shared__ int next_local;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 3;
+    const int i = lane & 7;
+    const uint32_t sel = 0x4440u | static_cast<uint32_t>(g);
+    const float* lut_lane = lut_s + lane;
+    const int K = a.K;
+    const int nchunks = (a.nq + kQC - 1) / kQC;
+    const int words = kQC * M * K;
+    uint8_t* wbuf = bufs + warp * 2 * kPieceBytes;
+    uint64_t* wbar = bars[warp];
+
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < kWarps; ++w) {
+            mbar_init(&bars[w][0], 1);
+            mbar_init(&bars[w][1], 1);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && __ldg(a.cand_offsets + a.n_queries) != a.n_cand)
+        atomicOr(a.err, TMS_DEVERR_BAD_CSR);
+    uint32_t issued = 0, consumed = 0;  // pieces of this warp (buffer = count & 1)
+
+    for (int q = 0; q < a.n_queries; ++q) {
+        int64_t c0 = __ldg(a.cand_offsets + q), c1 = __ldg(a.cand_offsets + q + 1);
+        c0 = c0 < 0 ? 0 : (c0 > a.n_cand ? a.n_cand : c0);
+        c1 = c1 < c0 ? c0 : (c1 > a.n_cand ? a.n_cand : c1);
+        if (c0 + blockIdx.x >= c1) continue;
+        const int64_t n_local = (c1 - c0 - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            __syncthreads();
+            const float* src = a.lut + static_cast<int64_t>(q) * a.nq * M * K;
+            for (int w = threadIdx.x; w < words; w += blockDim.x) {
+                const int ii = w & 7;
+                const int ml = (w >> 3) & 3;
+                const int rest = w >> 5;
+                const int kk = rest % K;
+                const int mh = rest / K;
+                const int qi = ch * kQC + ii;
+                lut_s[w] = (qi < a.nq) ? __ldg(src + (static_cast<int64_t>(qi) * M + mh * 4 + ml) * K + kk) : 0.f;
+            }
+            if (threadIdx.x == 0) next_local = 0;
+            __syncthreads();
+
+            auto grab = [&]() -> int64_t {
+                int li = 0;
+                if (lane == 0) li = atomicAdd(&next_local, 1);
+                return __shfl_sync(0xffffffffu, li, 0);
+            };
+            auto fetch = [&](int64_t li) {  // issue the metadata loads of candidate li
+                PendingMeta m;
+                m.li = li;
+                m.id = -1;
+                m.off = 0;
+                m.len = 0;
+                if (li < n_local) {
+                    const int64_t f = c0 + blockIdx.x + li * gridDim.x;
+                    m.id = __ldg(a.cand_ids + f);
+                    if (m.id >= 0 && m.id < a.n_docs) {
+                        m.off = __ldg(a.offsets + m.id);
+                        m.len = __ldg(a.lengths + m.id);
+                    }
+                }
+                return m;
+            };
+            // next valid document: (f, off, len) with f = -1 at the end;
+            // empty and invalid candidates met on the way are written here.
+            PendingMeta pend = fetch(grab());
+            auto take = [&](int64_t& f, int64_t& off, int& len) {
+                for (;;) {
+                    if (pend.li >= n_local) {
+                        f = -1;
+                        return;
+                    }
+                    const PendingMeta cur = pend;
+                    pend = fetch(grab());
+                    f = c0 + blockIdx.x + cur.li * gridDim.x;
+                    int status = 0;
+                    if (cur.id < 0 || cur.id >= a.n_docs)
+                        status = 1;
+                    else if (cur.len < 0 || cur.off < 0 || cur.off + cur.len > a.n_tokens)
+                        status = 2;
+                    if (status == 0 && cur.len > 0) {
+                        off = cur.off;
+                        len = cur.len;
+                        return;
+                    }
+                    if (ch == 0 && lane == 0) {
+                        if (status) {
+                            a.out[f] = __int_as_float(0x7fc00000);
+                            atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
+                        } else {
+                            a.out[f] = -INFINITY;
+                        }
+                    }
+                }
+            };
+            auto issue = [&](int64_t off, int start, int cnt) {
+                const int b = issued & 1;
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    const uint32_t bytes = static_cast<uint32_t>(cnt * M);
+                    mbar_arrive_expect_tx(&wbar[b], bytes);
+                    bulk_load(wbuf + b * kPieceBytes, a.codes + (off + start) * M, bytes, &wbar[b]);
+                }
+                ++issued;
+            };
+
+            int64_t f, off;
+            int len = 0;
+            take(f, off, len);
+            if (f >= 0) issue(off, 0, min(kPiece, len));
+            bool ok = true;
+            while (f >= 0 && ok) {
+                int64_t nf = -1, noff = 0;
+                int nlen = 0;
+                float rmax = -INFINITY;
+                for (int start = 0; start < len; start += kPiece) {
+                    const int cnt = min(kPiece, len - start);
+                    if (start + kPiece < len) {
+                        issue(off, start + kPiece, min(kPiece, len - start - kPiece));
+                    } else {
+                        take(nf, noff, nlen);
+                        if (nf >= 0) issue(noff, 0, min(kPiece, nlen));
+                    }
+                    const int b = consumed & 1;
+                    const bool got = mbar_wait(&wbar[b], (consumed >> 1) & 1, &abort_flag, a.err);
+                    ++consumed;
+                    if (!__all_sync(0xffffffffu, got)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint8_t* base = wbuf + b * kPieceBytes;
+                    const int last = cnt - 1;
+                    for (int j = 0; j < cnt; j += 4) {
+                        CodeRow<M> c[4];
+#pragma unroll
+                        for (int tt = 0; tt < 4; ++tt) c[tt] = smem_codes<M>(base + min(j + tt, last) * M);
+                        float p[4];
+#pragma unroll
+                        for (int tt = 0; tt < 4; ++tt) p[tt] = lane_partial<M>(lut_lane, c[tt], sel, K);
+                        const bool up16 = (lane & 16) != 0;
+                        float k0 = up16 ? p[2] : p[0];
+                        float k1 = up16 ? p[3] : p[1];
+                        const float s0 = up16 ? p[0] : p[2];
+                        const float s1 = up16 ? p[1] : p[3];
+                        k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+                        k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+                        const bool up8 = (lane & 8) != 0;
+                        float kk = up8 ? k1 : k0;
+                        const float ss = up8 ? k0 : k1;
+                        kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+                        rmax = fmaxf(rmax, kk);
+                    }
+                    __syncwarp();
+                }
+                if (!ok) break;
+                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 8));
+                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 16));
+                float v = (ch * kQC + i < a.nq) ? rmax : 0.f;
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                if (lane == 0) a.out[f] = (ch == 0) ? v : a.out[f] + v;
+                f = nf;
+                off = noff;
+                len = nlen;
+            }
+            // a timed-out warp lets its copies land before anything reuses the buffers
+            while (consumed < issued) {
+                const int b = consumed & 1;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&wbar[b], (consumed >> 1) & 1) && clock64() - t0 < kWaitBudgetCycles) {
+                }
+                ++consumed;
+            }
+        }
+    }
+}
+
 }  // namespace pq
 }  // namespace tms
 
@@ -298,7 +523,8 @@ extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int 
     // The last subspace group is sized for 256 codes so that a code >= k
     // still indexes inside the allocation.
     const int smem = ((m / 4 - 1) * k + 256) * 32 * 4;
-    if (smem > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
+    const int smem_st = smem + pq::kWarps * 2 * pq::kPieceBytes;  // staged variant: table + piece buffers
+    if ((m >= 16 ? smem_st : smem) > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(dev.sm_count, n_cand));
     cudaError_t e = cudaSuccess;
     switch (m) {
@@ -311,12 +537,14 @@ extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int 
             if (e == cudaSuccess) pq::score_kernel<8><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
             break;
         case 16:
-            e = cudaFuncSetAttribute(pq::score_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e == cudaSuccess) pq::score_kernel<16><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
+            e = cudaFuncSetAttribute(pq::score_kernel_staged<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
+            if (e == cudaSuccess)
+                pq::score_kernel_staged<16><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, smem);
             break;
         default:
-            e = cudaFuncSetAttribute(pq::score_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e == cudaSuccess) pq::score_kernel<32><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
+            e = cudaFuncSetAttribute(pq::score_kernel_staged<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
+            if (e == cudaSuccess)
+                pq::score_kernel_staged<32><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, smem);
             break;
     }
     if (e != cudaSuccess) return launch_status(e);

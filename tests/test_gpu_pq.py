@@ -119,10 +119,10 @@ def test_pq_edge_documents_and_flags(cuda_lib):
 
 def test_pq_bitwise_repeatable(cuda_lib):
     M, K, dsub = 16, 256, 8
-    lengths = synth.lengths_uniform(3000, 32, 180, 51)
+    lengths = synth.lengths_uniform(800, 32, 300, 51)
     cb, codes, _, off, ln = synth.pq_corpus(lengths, M, K, dsub, 51)
     Q = synth.queries(2, 32, M * dsub, "f16", 51)
-    cands = [synth.candidates(3000, 3000, 51, 0), synth.candidates(3000, 1000, 51, 1)]
+    cands = [synth.candidates(800, 800, 51, 0), synth.candidates(800, 300, 51, 1)]
     lut_d = _gpu_lut(Q, cb)
     a, _ = _gpu_pq(lut_d, codes, off, ln, cands)
     b, _ = _gpu_pq(lut_d, codes, off, ln, cands)
