@@ -389,6 +389,37 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
                                    "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak}
         del tok, off, ln, Q, f, out
         torch.cuda.empty_cache()
+    # the same workload in the shared-candidate schedule (queries stacked in N)
+    for d in (64, 256, 512, 768):
+        tok, off, ln = synth.device_dense_corpus(len3, d, "bf16", 2, dev)
+        Q = synth.queries(32, NQ, d, "bf16", 2).to(dev)
+        f = torch.arange(n3, dtype=torch.int32, device=dev)
+        c = torch.arange(0, 33 * n3, n3, dtype=torch.int64, device=dev)
+        out = torch.empty((32, n3), dtype=torch.float32, device=dev)
+        ts = torch.empty((32, 100), dtype=torch.float32, device=dev)
+        tp = torch.empty((32, 100), dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                tms.score_dense_shared(Q, tok, off, ln, f, out=out, stream=stream)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            e[0].record(stream)
+            for _ in range(5):
+                tms.score_dense_shared(Q, tok, off, ln, f, out=out, stream=stream)
+            e[1].record(stream)
+            tms.topk(out.view(-1), c, 100, ts, tp, stream=stream)
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        kms = e[0].elapsed_time(e[1]) / 5
+        tok3 = int(len3.astype(np.int64).sum())
+        fl = iomodel.dense_alg_flops(tok3 * 32, NQ, d)
+        rows[f"dtile_shared_bf16_d{d}"] = {"docs_per_s": 32 * n3 / (kms * 1e-3), "kernel_ms": kms,
+                                          "topk100_ms": e[1].elapsed_time(e[2]),
+                                          "tflops": fl / (kms * 1e-3) / 1e12,
+                                          "corpus_reads_gbs": tok3 * d * 2 / (kms * 1e-3) / 1e9}
+        del tok, off, ln, Q, f, out
+        torch.cuda.empty_cache()
     # fused PQ: 1M docs, M=16, K=256, dsub=8, 64 fp16 queries over all docs
     n4, M, K, dsub, nQ4 = 1_000_000, 16, 256, 8, 64
     len4 = synth.lengths_uniform(n4, LO, HI, 4)

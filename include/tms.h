@@ -90,6 +90,29 @@ tms_status tms_score_dense(const void *queries, tms_dtype dtype, int n_queries, 
                            float *out_scores, cudaStream_t stream);
 
 /*
+ * Dense MaxSim of n_queries queries that all score ONE candidate list
+ * (e.g. every query over the whole corpus, the dimension-scaling workload
+ * of Section 6.6).  Same arithmetic as tms_score_dense, but queries are
+ * processed in groups of up to 8 stacked in the tensor-core N dimension,
+ * so each document tile is read from HBM once per group instead of once
+ * per query (Theorem 1 with BQ = 32 x group).
+ *
+ *   cand_ids     [n_cand] int32, shared by all queries.
+ *   out_scores   [n_queries][n_cand] fp32: score of query q for cand_ids[c]
+ *                at out_scores[q * n_cand + c].
+ *   other arguments as for tms_score_dense.
+ *
+ * Limits: fp16 / bf16 only, 1 <= nq <= 32, n_queries / group * n_cand
+ * < 2^31; larger d uses smaller groups (down to 2) so the stacked query tile
+ * fits shared memory.  fp32 or nq > 32 return TMS_ERR_UNSUPPORTED.
+ */
+tms_status tms_score_dense_shared(const void *queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                  const void *doc_tokens, int64_t n_tokens,
+                                  const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                                  const int32_t *cand_ids, int64_t n_cand, float *out_scores,
+                                  cudaStream_t stream);
+
+/*
  * PQ distance table (Section 4.2, Phase 1):
  *   lut[q][i][mm][kk] = sum_{t < d/m} queries[q][i][mm*(d/m) + t] * codebook[mm][kk][t]
  * computed in fp32 with fused multiply-adds in ascending t.

@@ -76,7 +76,9 @@ struct Args {
     unsigned int* err;
     int64_t n_docs;
     int64_t n_tokens;
-    int64_t n_cand;
+    int64_t n_cand;    // entries of cand_ids
+    int64_t n_flat;    // work items: n_cand, or n_groups * n_cand in shared mode
+    int group;         // shared mode: queries per group (each a 32-column block); 0 otherwise
     int n_queries;
     int nq;
     int nchunks;   // ceil(d / 64)
@@ -114,7 +116,7 @@ __host__ __device__ inline Layout make_layout(int stages, int cps, int qslots, i
 // that skips the other group's tiles could wait on the second use of an
 // accumulator whose barrier has not finished its first phase -- and an
 // mbarrier parity wait cannot tell those apart.)
-__host__ __device__ constexpr int partials(int NT) { return NT <= 32 ? 4 : 2; }
+__host__ __device__ constexpr int partials(int NT) { return NT <= 32 ? 4 : (NT <= 128 ? 2 : 1); }
 __host__ __device__ constexpr int acc_buffers(int NT) { return 2; }
 
 __host__ __device__ constexpr int acc_total(int NT) { return epi_groups(NT) * acc_buffers(NT); }
@@ -138,7 +140,8 @@ struct Meta {
 
 __device__ __forceinline__ int load_id(const Args& a, int64_t k) {
     const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
-    return f < a.n_cand ? __ldg(a.cand_ids + f) : -1;
+    if (f >= a.n_flat) return -1;
+    return __ldg(a.cand_ids + (a.group ? f % a.n_cand : f));
 }
 
 __device__ __forceinline__ Meta load_meta(const Args& a, int id) {
@@ -187,7 +190,11 @@ struct Maps {
     CUtensorMap doc[kBoxKinds];
 };
 
-template <int NB, int CTAS>
+// SH (shared mode): the launch's queries all score one candidate list; a
+// "query" of the pipeline is then a group of up to NB queries stacked in
+// the MMA's N dimension (32 columns each), so each document tile is read
+// once per group, and the epilogue writes one score per query of the group.
+template <int NB, int CTAS, bool SH>
 __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
     dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
     constexpr int NT = NB * 32;
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
         int q = 0;
         int64_t q_end = 0;
         bool aborted = false;
-        {
+        if (!SH) {
             const int64_t co_last = __ldg(a.cand_offsets + a.n_queries);
             if (co_last != a.n_cand && blockIdx.x == 0 && lane == 0) atomicOr(a.err, TMS_DEVERR_BAD_CSR);
             q_end = __ldg(a.cand_offsets + 1);
@@ -292,24 +299,30 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
         for (int64_t k = 0;; ++k) {
             const int kl = static_cast<int>(k & 31);
             const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
-            if (f >= a.n_cand) break;
+            if (f >= a.n_flat) break;
             const int cid = __shfl_sync(0xffffffffu, cur.id, kl);
             const int64_t off = __shfl_sync(0xffffffffu, cur.off, kl);
             const int len = __shfl_sync(0xffffffffu, cur.len, kl);
             const int status = meta_status(a, cid, off, len);
-            while (f >= q_end && q < a.n_queries - 1) {
-                ++q;
-                q_end = __ldg(a.cand_offsets + q + 1);
+            if (SH) {
+                q = static_cast<int>(f / a.n_cand);
+            } else {
+                while (f >= q_end && q < a.n_queries - 1) {
+                    ++q;
+                    q_end = __ldg(a.cand_offsets + q + 1);
+                }
             }
             if (status != 0 || len == 0) {
-                if (lane == 0) {
-                    if (status != 0) {
-                        a.out[f] = __int_as_float(0x7fc00000);
-                        atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
-                    } else {
-                        a.out[f] = -INFINITY;
-                    }
+                const float v = status != 0 ? __int_as_float(0x7fc00000) : -INFINITY;
+                if (SH) {
+                    const int64_t fc = f % a.n_cand;
+                    if (lane < a.group && q * a.group + lane < a.n_queries)
+                        a.out[static_cast<int64_t>(q * a.group + lane) * a.n_cand + fc] = v;
+                } else if (lane == 0) {
+                    a.out[f] = v;
                 }
+                if (status != 0 && lane == 0)
+                    atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
             } else {
                 for (int r0 = 0; r0 < len; r0 += kRows) {
                     const int r = min(kRows, len - r0);
@@ -340,9 +353,16 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                         if (lane == 0) {
                             mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(NCH * NT * 128));
                             uint8_t* qdst = q_base + slot * NCH * NT * 128;
-                            for (int kc = 0; kc < NCH; ++kc)
-                                tma_load_2d(qdst + kc * NT * 128, &maps.q, kc * kChunkElems, q * a.nq,
-                                            &qfull[slot], pol_keep);
+                            for (int kc = 0; kc < NCH; ++kc) {
+                                if (SH) {  // one 32-row box per query of the group
+                                    for (int g = 0; g < NB; ++g)
+                                        tma_load_2d(qdst + kc * NT * 128 + g * 32 * 128, &maps.q, kc * kChunkElems,
+                                                    (q * a.group + g) * a.nq, &qfull[slot], pol_keep);
+                                } else {
+                                    tma_load_2d(qdst + kc * NT * 128, &maps.q, kc * kChunkElems, q * a.nq,
+                                                &qfull[slot], pol_keep);
+                                }
+                            }
                         }
                         ++qi;
                         cur_q = q;
@@ -503,11 +523,15 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
         uint64_t* gpempty = pempty + 2 * grp;
         uint32_t doc_ord = 0;  // ordinal of the current document (all groups count all documents)
         bool mine = false;
-        float rm[NB][32];
+        constexpr int RB = SH ? 1 : NB;  // blocks of warp-uniform maxima (normal mode)
+        float rm[RB][32];
+        float rmd[NB];                    // per-lane maxima (shared mode)
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
+        for (int b = 0; b < RB; ++b)
 #pragma unroll
             for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) rmd[b] = -INFINITY;
         int acc = 0;
         uint32_t docs = 0;  // documents finished; buffer = docs & 1, its use count = docs >> 1
         for (int t = 0;; ++t) {
@@ -521,9 +545,11 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                 mine = (doc_ord % kEpiGroups) == static_cast<uint32_t>(grp);
                 ++doc_ord;
 #pragma unroll
-                for (int b = 0; b < NB; ++b)
+                for (int b = 0; b < RB; ++b)
 #pragma unroll
                     for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) rmd[b] = -INFINITY;
             }
             if (!mine) continue;  // another group's tile
             const int ab = grp * A + acc % A;
@@ -549,7 +575,18 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                             for (int c = 0; c < 32; ++c) v[c] += w[c];
                         }
                     }
-                    if (lane < rows_here) {
+                    if (SH) {
+                        // running max kept per lane: lane c owns column c of block b
+                        if (rows_here < 32 && lane >= rows_here) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) v[c] = -INFINITY;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const float m = redux_max(v[c], 0xffffffffu);
+                            if (lane == c) rmd[b] = fmaxf(rmd[b], m);
+                        }
+                    } else if (lane < rows_here) {
 #pragma unroll
                         for (int c = 0; c < 32; ++c) rm[b][c] = fmaxf(rm[b][c], redux_max(v[c], vmask));
                     }
@@ -565,9 +602,12 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                 const uint32_t use = docs >> 1;
                 if (!warp_wait(&gpempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
                 float* pp = gpart + pb * 4 * NT;
-                if (lane == 0) {
+                if (SH) {
 #pragma unroll
-                    for (int b = 0; b < NB; ++b)
+                    for (int b = 0; b < NB; ++b) pp[qd * NT + b * 32 + lane] = rmd[b];
+                } else if (lane == 0) {
+#pragma unroll
+                    for (int b = 0; b < RB; ++b)
 #pragma unroll
                         for (int c = 0; c < 32; c += 4)
                             *reinterpret_cast<float4*>(pp + qd * NT + b * 32 + c) =
@@ -577,15 +617,30 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                 if (lane == 0) mbar_arrive(&gpfull[pb]);
                 if (qd == 0) {
                     if (!warp_wait(&gpfull[pb], use & 1, abort_flag, a.err)) break;
-                    float sum = 0.f;
+                    if (SH) {
+                        const int64_t fc = static_cast<int64_t>(ti.f) % a.n_cand;
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const int col = b * 32 + lane;
-                        const float m = fmaxf(fmaxf(pp[col], pp[NT + col]), fmaxf(pp[2 * NT + col], pp[3 * NT + col]));
-                        sum += (col < a.nq) ? m : 0.f;
+                        for (int b = 0; b < NB; ++b) {
+                            const int col = b * 32 + lane;
+                            const float m =
+                                fmaxf(fmaxf(pp[col], pp[NT + col]), fmaxf(pp[2 * NT + col], pp[3 * NT + col]));
+                            const float sum = warp_sum(lane < a.nq ? m : 0.f);
+                            const int qq = ti.q * a.group + b;
+                            if (lane == 0 && b < a.group && qq < a.n_queries)
+                                a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
+                        }
+                    } else {
+                        float sum = 0.f;
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) {
+                            const int col = b * 32 + lane;
+                            const float m =
+                                fmaxf(fmaxf(pp[col], pp[NT + col]), fmaxf(pp[2 * NT + col], pp[3 * NT + col]));
+                            sum += (col < a.nq) ? m : 0.f;
+                        }
+                        sum = warp_sum(sum);
+                        if (lane == 0) a.out[ti.f] = sum;
                     }
-                    sum = warp_sum(sum);
-                    if (lane == 0) a.out[ti.f] = sum;
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&gpempty[pb]);
                 }
@@ -704,7 +759,7 @@ __global__ void __launch_bounds__(kF32Warps * 32)
 
 namespace {
 
-template <int NB>
+template <int NB, bool SH>
 tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
                      const void* doc_tokens, int64_t n_tokens, dense::Args a, cudaStream_t stream) {
     using namespace dense;
@@ -714,7 +769,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     const uint64_t row_bytes = static_cast<uint64_t>(d) * 2;
     Maps maps;
     tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
-                                   kChunkElems, NT);
+                                   kChunkElems, SH ? 32 : NT);
     if (st != TMS_OK) return st;
     // Shared-memory plan.  Prefer two CTAs per SM (NT <= 64) when each
     // still gets a ring of at least 4 dimension chunks; within a plan take
@@ -760,10 +815,10 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.qslots = qslots;
     const Layout L = make_layout(stages, a.cps, qslots, a.nchunks, NT, A);
     const int smem = L.total + 1024;
-    auto kern = ctas == 2 ? dense_tc_kernel<NB, (NB <= 2 ? 2 : 1)> : dense_tc_kernel<NB, 1>;
+    auto kern = ctas == 2 ? dense_tc_kernel<NB, (NB <= 2 ? 2 : 1), SH> : dense_tc_kernel<NB, 1, SH>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
-    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_cand);
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
     kern<<<static_cast<unsigned>(grid), num_threads(NT), smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
 }
@@ -805,6 +860,8 @@ extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int 
     a.n_docs = n_docs;
     a.n_tokens = n_tokens;
     a.n_cand = n_cand;
+    a.n_flat = n_cand;
+    a.group = 0;
     a.n_queries = n_queries;
     a.nq = nq;
     a.nchunks = (d + dense::kChunkElems - 1) / dense::kChunkElems;
@@ -823,9 +880,59 @@ extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int 
     }
     const int nb = (nq + 31) / 32;
     switch (nb) {
-        case 1: return launch_tc<1>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
-        case 2: return launch_tc<2>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
-        case 3: return launch_tc<3>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
-        default: return launch_tc<4>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+        case 1: return launch_tc<1, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+        case 2: return launch_tc<2, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+        case 3: return launch_tc<3, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+        default: return launch_tc<4, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
     }
+}
+
+extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                             const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
+                                             const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
+                                             int64_t n_cand, float* out_scores, cudaStream_t stream) {
+    using namespace tms;
+    if (dtype != TMS_F16 && dtype != TMS_BF16 && dtype != TMS_F32) return TMS_ERR_INVALID_ARG;
+    if (n_queries < 1 || n_queries > 4096 || nq < 1 || nq > 128 || d < 8 || d > 1024 || d % 8 != 0)
+        return TMS_ERR_INVALID_ARG;
+    if (dtype == TMS_F32 || nq > 32) return TMS_ERR_UNSUPPORTED;
+    if (n_tokens < 0 || n_tokens >= (int64_t(1) << 31) || n_docs < 0 || n_cand < 0) return TMS_ERR_INVALID_ARG;
+    if (!queries || !aligned16(queries)) return TMS_ERR_INVALID_ARG;
+    if (n_cand > 0 && (!cand_ids || !out_scores || !aligned16(cand_ids) || !aligned16(out_scores)))
+        return TMS_ERR_INVALID_ARG;
+    if (n_docs > 0 && (!doc_offsets || !doc_lengths || !aligned16(doc_offsets) || !aligned16(doc_lengths)))
+        return TMS_ERR_INVALID_ARG;
+    if (n_tokens > 0 && (!doc_tokens || !aligned16(doc_tokens))) return TMS_ERR_INVALID_ARG;
+    if (n_cand == 0) return TMS_OK;
+    DeviceInfo dev;
+    tms_status st = current_device(&dev);
+    if (st != TMS_OK) return st;
+    dense::Args a{};
+    a.offsets = doc_offsets;
+    a.lengths = doc_lengths;
+    a.cand_ids = cand_ids;
+    a.cand_offsets = nullptr;
+    a.out = out_scores;
+    a.err = dev.err;
+    a.n_docs = n_docs;
+    a.n_tokens = n_tokens;
+    a.n_cand = n_cand;
+    a.n_queries = n_queries;
+    a.nq = nq;
+    a.nchunks = (d + dense::kChunkElems - 1) / dense::kChunkElems;
+    // Queries per group (32 MMA columns each): up to 8; a smaller group when
+    // the stacked query tile would not fit shared memory at this d.
+    for (int group = n_queries >= 5 ? 8 : (n_queries >= 3 ? 4 : 2); group >= 2; group /= 2) {
+        const int64_t n_groups = (n_queries + group - 1) / group;
+        if (n_groups * n_cand >= (int64_t(1) << 31)) return TMS_ERR_UNSUPPORTED;
+        a.n_flat = n_groups * n_cand;
+        a.group = group;
+        switch (group) {
+            case 2: st = launch_tc<2, true>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream); break;
+            case 4: st = launch_tc<4, true>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream); break;
+            default: st = launch_tc<8, true>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream); break;
+        }
+        if (st != TMS_ERR_UNSUPPORTED) return st;
+    }
+    return TMS_ERR_UNSUPPORTED;
 }

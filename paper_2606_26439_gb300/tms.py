@@ -29,7 +29,7 @@ TMS_DEVERR_TIMEOUT = 4
 TMS_DEVERR_BAD_CSR = 8
 
 #: every symbol include/tms.h declares
-EXPORTS = ("tms_score_dense", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
+EXPORTS = ("tms_score_dense", "tms_score_dense_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
            "tms_get_device_error", "tms_status_string", "tms_version")
 
 _lib = None
@@ -58,6 +58,7 @@ def lib(build_if_missing: bool = True):
                 raise RuntimeError("libtms.so is missing and could not be built")
             L = ctypes.CDLL(path)
             L.tms_score_dense.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_score_dense_shared.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p]
             L.tms_build_pq_lut.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _p]
             L.tms_score_pq.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
             L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
@@ -65,7 +66,7 @@ def lib(build_if_missing: bool = True):
             L.tms_status_string.argtypes = [_i32]
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
-            for name in ("tms_score_dense", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
+            for name in ("tms_score_dense", "tms_score_dense_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
                          "tms_get_device_error", "tms_version"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -87,6 +88,12 @@ def tms_score_dense(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_
                     n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream) -> int:
     return lib().tms_score_dense(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets,
                                  doc_lengths, n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream)
+
+
+def tms_score_dense_shared(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets, doc_lengths,
+                           n_docs, cand_ids, n_cand, out_scores, stream) -> int:
+    return lib().tms_score_dense_shared(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets,
+                                        doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream)
 
 
 def tms_build_pq_lut(queries, qdtype, n_queries, nq, d, codebook, m, k, lut, stream) -> int:
@@ -155,6 +162,20 @@ def score_dense(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, cand_of
         _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
         _dev(cand_ids, torch.int32), _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32),
         _stream_ptr(stream)))
+    return out
+
+
+def score_dense_shared(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, out=None, stream=None):
+    """Dense MaxSim of every query over ONE candidate list; out [n_queries][n_cand]."""
+    torch = _torch()
+    nQ, nq, d = queries.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty((nQ, n_cand), dtype=torch.float32, device=queries.device)
+    _check("tms_score_dense_shared", tms_score_dense_shared(
+        _dev(queries), _dtype_code(queries), nQ, nq, d, _dev(doc_tokens, queries.dtype), doc_tokens.shape[0],
+        _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
+        _dev(cand_ids, torch.int32), n_cand, _dev(out, torch.float32), _stream_ptr(stream)))
     return out
 
 
