@@ -26,7 +26,7 @@ import numpy as np
 
 from . import build as _build
 
-F16, BF16, F32, F64 = 0, 1, 2, 3
+F16, BF16, F32, F64, E4M3 = 0, 1, 2, 3, 4
 
 _lib = None
 _lock = threading.Lock()
@@ -45,6 +45,11 @@ def _load():
             lib.tmso_f16_to_f64.argtypes = [ctypes.c_uint16]
             lib.tmso_bf16_to_f64.restype = ctypes.c_double
             lib.tmso_bf16_to_f64.argtypes = [ctypes.c_uint16]
+            lib.tmso_e4m3_to_f64.restype = ctypes.c_double
+            lib.tmso_e4m3_to_f64.argtypes = [ctypes.c_uint8]
+            lib.tmso_dense_scores_scaled.argtypes = [
+                _p, _i32, _p, _i32, _i32, _p, _i32, _p, _i64, _p, _p, _i64, _p, _i64, _p]
+            lib.tmso_dense_scores_scaled.restype = ctypes.c_int
             lib.tmso_max_threads.restype = ctypes.c_int
             lib.tmso_set_threads.argtypes = [ctypes.c_int]
             lib.tmso_dense_scores.argtypes = [
@@ -98,6 +103,31 @@ def f16_to_f64(bits: int) -> float:
 
 def bf16_to_f64(bits: int) -> float:
     return float(_load().tmso_bf16_to_f64(int(bits)))
+
+
+def e4m3_to_f64(bits: int) -> float:
+    return float(_load().tmso_e4m3_to_f64(int(bits)))
+
+
+def dense_scores_scaled(queries, q_scales, tokens, t_scales, offsets, lengths, cand_ids, *,
+                        qdtype=None, tdtype=None):
+    """Eq. 1 on row-scaled stored values (a per-token scaled store, e.g. FP8
+    E4M3 codes given as uint8 with dtype code E4M3); None scales mean 1."""
+    q, qdt = _typed(queries, qdtype)
+    t, tdt = _typed(tokens, tdtype)
+    nq, d = q.shape
+    qs = None if q_scales is None else _c(q_scales, np.float32)
+    ts = None if t_scales is None else _c(t_scales, np.float32)
+    off = _c(offsets, np.int64)
+    ln = _c(lengths, np.int32)
+    cid = _c(cand_ids, np.int32)
+    out = np.empty(cid.shape[0], np.float64)
+    rc = _load().tmso_dense_scores_scaled(_ptr(q), qdt, None if qs is None else _ptr(qs), nq, d,
+                                          _ptr(t), tdt, None if ts is None else _ptr(ts), t.shape[0],
+                                          _ptr(off), _ptr(ln), off.shape[0], _ptr(cid), cid.shape[0], _ptr(out))
+    if rc:
+        raise ValueError("oracle dense_scores_scaled rejected its arguments")
+    return out
 
 
 def dense_scores(queries, tokens, offsets, lengths, cand_ids, *, qdtype=None, tdtype=None):

@@ -48,7 +48,7 @@
 #include <omp.h>
 #endif
 
-enum { TMSO_F16 = 0, TMSO_BF16 = 1, TMSO_F32 = 2, TMSO_F64 = 3 };
+enum { TMSO_F16 = 0, TMSO_BF16 = 1, TMSO_F32 = 2, TMSO_F64 = 3, TMSO_E4M3 = 4 };
 
 /* ---- exact decoding of stored element types ------------------------- */
 
@@ -79,9 +79,29 @@ double tmso_bf16_to_f64(uint16_t h)
     return (double)f;
 }
 
+/* OCP FP8 E4M3 ("e4m3fn"): 1 sign bit, 4 exponent bits (bias 7), 3 fraction
+ * bits.  Exponent 0 encodes zero and subnormals (fraction * 2^-9); there
+ * are no infinities, and S.1111.111 is NaN (max finite 448). */
+double tmso_e4m3_to_f64(uint8_t b)
+{
+    int sign = (b >> 7) & 1;
+    int expo = (b >> 3) & 0xf;
+    int frac = b & 0x7;
+    double v;
+    if (expo == 15 && frac == 7)
+        v = NAN;
+    else if (expo == 0)
+        v = ldexp((double)frac, -9);
+    else
+        v = ldexp((double)(frac | 0x8), expo - 10);
+    return sign ? -v : v;
+}
+
 static double load_elem(const void *base, int dtype, int64_t idx)
 {
     switch (dtype) {
+    case TMSO_E4M3:
+        return tmso_e4m3_to_f64(((const uint8_t *)base)[idx]);
     case TMSO_F16:
         return tmso_f16_to_f64(((const uint16_t *)base)[idx]);
     case TMSO_BF16:
@@ -100,7 +120,7 @@ static void load_row(const void *base, int dtype, int64_t idx, int n, double *ds
         dst[t] = load_elem(base, dtype, idx + t);
 }
 
-static int dtype_ok(int dt) { return dt >= TMSO_F16 && dt <= TMSO_F64; }
+static int dtype_ok(int dt) { return dt >= TMSO_F16 && dt <= TMSO_E4M3; }
 
 int tmso_max_threads(void)
 {
@@ -201,6 +221,67 @@ int tmso_dense_scores(const void *queries, int qdtype, int nq, int d,
             }
             for (int64_t j = 0; j < len; ++j)
                 load_row(tokens, tdtype, (off + j) * d, d, X + j * d);
+            out[c] = maxsim_one(Q, nq, d, X, len);
+        }
+        free(X);
+    }
+    free(Q);
+    return failed ? -1 : 0;
+}
+
+/*
+ * Dense MaxSim (Eq. 1) on row-scaled stored values: the vectors scored are
+ * q_i = q_scales[i] * Q[i][:] and d_j = t_scales[row] * X[row][:] (a NULL
+ * scale array means 1).  This is the definition of a per-token scaled
+ * store (e.g. FP8 E4M3 codes with an fp32 scale per token): dequantize,
+ * then Eq. 1.
+ */
+int tmso_dense_scores_scaled(const void *queries, int qdtype, const float *q_scales, int nq, int d,
+                             const void *tokens, int tdtype, const float *t_scales, int64_t n_tokens,
+                             const int64_t *offsets, const int32_t *lengths, int64_t n_docs,
+                             const int32_t *cand_ids, int64_t n_cand, double *out)
+{
+    if (nq <= 0 || d <= 0 || n_cand < 0 || !dtype_ok(qdtype) || !dtype_ok(tdtype))
+        return -1;
+    double *Q = (double *)malloc(sizeof(double) * (size_t)nq * (size_t)d);
+    if (!Q)
+        return -1;
+    for (int i = 0; i < nq; ++i) {
+        load_row(queries, qdtype, (int64_t)i * d, d, Q + (int64_t)i * d);
+        double sc = q_scales ? (double)q_scales[i] : 1.0;
+        for (int t = 0; t < d; ++t)
+            Q[(int64_t)i * d + t] *= sc;
+    }
+    int failed = 0;
+#pragma omp parallel
+    {
+        double *X = NULL;
+        int64_t cap = 0;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t c = 0; c < n_cand; ++c) {
+            int64_t off, len;
+            if (doc_range(cand_ids[c], offsets, lengths, n_docs, n_tokens, &off, &len)) {
+                out[c] = NAN;
+                continue;
+            }
+            if (len > cap) {
+                free(X);
+                cap = len;
+                X = (double *)malloc(sizeof(double) * (size_t)len * (size_t)d);
+                if (!X) {
+#pragma omp atomic write
+                    failed = 1;
+                    cap = 0;
+                    out[c] = NAN;
+                    continue;
+                }
+            }
+            for (int64_t j = 0; j < len; ++j) {
+                load_row(tokens, tdtype, (off + j) * d, d, X + j * d);
+                double sc = t_scales ? (double)t_scales[off + j] : 1.0;
+                for (int t = 0; t < d; ++t)
+                    X[j * d + t] *= sc;
+            }
             out[c] = maxsim_one(Q, nq, d, X, len);
         }
         free(X);

@@ -339,3 +339,43 @@ def test_topk_matches_python_sort(seed):
         for (ws, wp), gs, gp in zip(want, got_s, got_p):
             assert gp == wp
             assert (math.isnan(ws) and math.isnan(gs)) or gs == ws
+
+
+# --------------------------------------------------------------- FP8 E4M3
+
+def test_e4m3_decode_exhaustive():
+    """All 256 E4M3 patterns decode as torch's float8_e4m3fn -> float64."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8")
+    bits = np.arange(256, dtype=np.uint8)
+    want = torch.from_numpy(bits.copy()).view(torch.float8_e4m3fn).double().numpy()
+    got = np.array([oracle.e4m3_to_f64(int(b)) for b in bits])
+    same = (got == want) | (np.isnan(got) & np.isnan(want))
+    assert same.all()
+    assert oracle.e4m3_to_f64(0x7E) == 448.0 and oracle.e4m3_to_f64(0x01) == 2.0 ** -9
+
+
+def test_scaled_scores_match_explicit_dequantization():
+    """Scaled-store scoring equals Eq. 1 on the explicitly dequantized fp64
+    vectors (row scales for both the query and document tokens)."""
+    g = np.random.default_rng(30)
+    codes_t = g.integers(0, 256, size=(40, 16)).astype(np.uint8)
+    codes_t[(codes_t & 0x7F) == 0x7F] = 0x11          # no NaN codes
+    codes_q = g.integers(0, 256, size=(5, 16)).astype(np.uint8)
+    codes_q[(codes_q & 0x7F) == 0x7F] = 0x22
+    ts = g.uniform(0.01, 2.0, 40).astype(np.float32)
+    qs = g.uniform(0.01, 2.0, 5).astype(np.float32)
+    lengths = np.array([7, 0, 13, 20], np.int32)
+    off = synth.offsets_of(lengths)
+    cand = np.array([3, 1, 0, 2, 2], np.int32)
+    got = oracle.dense_scores_scaled(codes_q, qs, codes_t, ts, off, lengths, cand,
+                                     qdtype=oracle.E4M3, tdtype=oracle.E4M3)
+    dec = np.vectorize(oracle.e4m3_to_f64)
+    Xd = dec(codes_t) * ts[:, None].astype(np.float64)
+    Qd = dec(codes_q) * qs[:, None].astype(np.float64)
+    want = oracle.dense_scores(Qd, Xd, off, lengths, cand)
+    assert np.array_equal(got, want)
+    # and with unit scales it is the plain decode
+    plain = oracle.dense_scores_scaled(Qd, None, Xd, None, off, lengths, cand)
+    assert np.array_equal(plain, want)
