@@ -50,6 +50,10 @@ def _load():
             lib.tmso_dense_scores_scaled.argtypes = [
                 _p, _i32, _p, _i32, _i32, _p, _i32, _p, _i64, _p, _p, _i64, _p, _i64, _p]
             lib.tmso_dense_scores_scaled.restype = ctypes.c_int
+            lib.tmso_e4m3_encode.argtypes = [ctypes.c_float]
+            lib.tmso_e4m3_encode.restype = ctypes.c_uint8
+            lib.tmso_quantize_e4m3.argtypes = [_p, _i32, _i64, _i32, _p, _p]
+            lib.tmso_quantize_e4m3.restype = ctypes.c_int
             lib.tmso_max_threads.restype = ctypes.c_int
             lib.tmso_set_threads.argtypes = [ctypes.c_int]
             lib.tmso_dense_scores.argtypes = [
@@ -107,6 +111,21 @@ def bf16_to_f64(bits: int) -> float:
 
 def e4m3_to_f64(bits: int) -> float:
     return float(_load().tmso_e4m3_to_f64(int(bits)))
+
+
+def e4m3_encode(v: float) -> int:
+    return int(_load().tmso_e4m3_encode(float(v)))
+
+
+def quantize_e4m3(x, *, dtype=None):
+    """Per-row E4M3 codes [rows][d] (uint8) and fp32 scales [rows]."""
+    a, dt = _typed(x, dtype)
+    rows, d = a.shape
+    codes = np.empty((rows, d), np.uint8)
+    scales = np.empty(rows, np.float32)
+    if _load().tmso_quantize_e4m3(_ptr(a), dt, rows, d, _ptr(codes), _ptr(scales)):
+        raise ValueError("oracle quantize_e4m3 rejected its arguments")
+    return codes, scales
 
 
 def dense_scores_scaled(queries, q_scales, tokens, t_scales, offsets, lengths, cand_ids, *,

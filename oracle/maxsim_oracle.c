@@ -24,6 +24,11 @@
  *     and the approximate similarity  q_i . d^_j = sum_m T[i][m][code_{j,m}].
  *   - Top-k after scoring (Section 6.6, end-to-end retrieval): the k largest
  *     scores of a query's candidate list.
+ *   - A per-token scaled FP8 store (an extension of Section 6.6's precision
+ *     discussion; the paper itself scores fp16/bf16): each stored row is
+ *     E4M3 codes with one fp32 scale, the vector it stands for is
+ *     scale * decode(codes), and MaxSim is Eq. 1 on those vectors -- the
+ *     row scale multiplies each similarity before the max.
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - Inner product, not cosine: Eq. 1 is a raw dot product; normalisation is
@@ -121,6 +126,66 @@ static void load_row(const void *base, int dtype, int64_t idx, int n, double *ds
 }
 
 static int dtype_ok(int dt) { return dt >= TMSO_F16 && dt <= TMSO_E4M3; }
+
+/* ---- FP8 E4M3 quantization ------------------------------------------ */
+
+/* Magnitude code (0..126) of the finite E4M3 value nearest to a >= 0: the
+ * nearest of the 127 finite non-negative values by exhaustive search, an
+ * exact tie going to the even code (round to nearest, ties to even).
+ * Anything above 448 is nearest to 448 -- the saturating conversion. */
+static int e4m3_nearest_code(double a)
+{
+    int best = 0;
+    double best_err = fabs(a);
+    for (int c = 1; c <= 126; ++c) {
+        double err = fabs(tmso_e4m3_to_f64((uint8_t)c) - a);
+        if (err < best_err || (err == best_err && (c & 1) == 0)) {
+            best = c;
+            best_err = err;
+        }
+    }
+    return best;
+}
+
+/* E4M3 code of the fp32 value v: sign bit of v, magnitude by nearest-even. */
+uint8_t tmso_e4m3_encode(float v)
+{
+    int sign = signbit(v) ? 1 : 0;
+    return (uint8_t)((sign << 7) | e4m3_nearest_code(fabs((double)v)));
+}
+
+/*
+ * Per-row FP8 E4M3 quantization with one fp32 scale per row.  For row r,
+ * in fp32 arithmetic: amax = max_t |x[r][t]|, s = amax / 448 (the largest
+ * finite E4M3 magnitude) and code[r][t] = encode(x[r][t] / s), both
+ * divisions IEEE fp32.  A row whose s is 0 gets all-zero codes.  Inputs are
+ * finite fp16 / bf16 / fp32 values.
+ */
+int tmso_quantize_e4m3(const void *x, int dtype, int64_t rows, int d, uint8_t *codes, float *scales)
+{
+    if (rows < 0 || d <= 0 || (dtype != TMSO_F16 && dtype != TMSO_BF16 && dtype != TMSO_F32))
+        return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < rows; ++r) {
+        float amax = 0.0f;
+        for (int t = 0; t < d; ++t) {
+            float v = (float)load_elem(x, dtype, r * d + t);
+            if (fabsf(v) > amax)
+                amax = fabsf(v);
+        }
+        float s = amax / 448.0f;
+        scales[r] = s;
+        for (int t = 0; t < d; ++t) {
+            if (s == 0.0f) {
+                codes[r * d + t] = 0;
+            } else {
+                float v = (float)load_elem(x, dtype, r * d + t) / s;
+                codes[r * d + t] = tmso_e4m3_encode(v);
+            }
+        }
+    }
+    return 0;
+}
 
 int tmso_max_threads(void)
 {

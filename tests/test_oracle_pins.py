@@ -379,3 +379,61 @@ def test_scaled_scores_match_explicit_dequantization():
     # and with unit scales it is the plain decode
     plain = oracle.dense_scores_scaled(Qd, None, Xd, None, off, lengths, cand)
     assert np.array_equal(plain, want)
+
+
+def _torch_fp8():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8")
+    return torch
+
+
+def test_e4m3_encode_matches_torch_cast_in_range():
+    """Round to nearest even agrees with torch's float32 -> float8_e4m3fn
+    cast on values below 464 (where torch does not overflow to NaN),
+    including exact ties, subnormals and signed zeros."""
+    torch = _torch_fp8()
+    g = np.random.default_rng(31)
+    mags = np.concatenate([g.uniform(0, 463.9, 3000), 2.0 ** g.uniform(-12, 8.85, 3000),
+                           g.uniform(0, 2.0 ** -6, 500)])
+    # every midpoint between adjacent finite codes is an exact tie
+    vals = np.array([oracle.e4m3_to_f64(c) for c in range(127)])
+    mids = (vals[:-1] + vals[1:]) / 2
+    v = np.concatenate([mags, mids, [0.0, 448.0, 463.0]]).astype(np.float32)
+    v = np.concatenate([v, -v])
+    want = torch.from_numpy(v).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    got = np.array([oracle.e4m3_encode(x) for x in v], np.uint8)
+    assert np.array_equal(got, want)
+
+
+def test_e4m3_encode_saturates():
+    for v, c in [(464.0, 0x7E), (480.0, 0x7E), (1e30, 0x7E), (-500.0, 0xFE), (448.5, 0x7E),
+                 (2.0 ** -10, 0x00), (2.0 ** -10 + 2.0 ** -20, 0x01), (-(2.0 ** -11), 0x80)]:
+        assert oracle.e4m3_encode(v) == c, v
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16", "f32"])
+def test_quantize_e4m3_rows(dt):
+    """Per-row scale = amax / 448 in fp32, codes = cast(x / scale) (torch
+    as the independent cast), the row maximum maps to +-448, a zero row has
+    scale 0 and zero codes, and decode(code) * scale is within the E4M3
+    rounding bound of x."""
+    torch = _torch_fp8()
+    from tests._common import oracle_view
+    x = np.random.default_rng(32).standard_normal((64, 96)) * 0.1
+    x[5] = 0
+    x_in = synth.cast(x, dt)
+    arr, code = oracle_view(x_in)
+    codes, scales = oracle.quantize_e4m3(arr, dtype=code)
+    xf = x_in.float()
+    s_want = (xf.abs().amax(dim=1) / 448.0).numpy()
+    assert np.array_equal(scales, s_want)
+    assert scales[5] == 0 and not codes[5].any()
+    nz = scales != 0
+    q = (xf[nz] / torch.from_numpy(scales[nz])[:, None]).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(codes[nz], q)
+    dec = np.vectorize(oracle.e4m3_to_f64)(codes).astype(np.float64) * scales[:, None]
+    xd = xf.double().numpy()
+    assert np.all(np.abs(np.abs(dec).max(axis=1)[nz] - np.abs(xd).max(axis=1)[nz]) <= 1e-6 * np.abs(xd).max())
+    bound = np.maximum(np.abs(xd) * 2.0 ** -4, scales[:, None].astype(np.float64) * 2.0 ** -10) * (1 + 1e-6)
+    assert np.all(np.abs(dec - xd) <= bound)
