@@ -9,10 +9,13 @@ each scoring its own random 100,000-document candidate subset.  One step
 = one tms_score_dense launch over all 16 x 100,000 candidates plus one
 tms_topk launch (top-10 per query).  Metric: documents scored per second.
 
-Also reported (N = 1 only): the same workload in bf16 and fp32, dimension
-tiling at d = 64/256/512/768 (200,000 docs, 32 queries over all of them,
-bf16, top-100) and fused PQ (1,000,000 docs, M = 16, K = 256, 64 queries
-over all of them).
+Also reported (N = 1 only): the same workload in bf16, fp32 and on the
+FP8 E4M3 store (per-token scales), dimension tiling at d = 64/256/512/768
+(200,000 docs, 32 queries over all of them, bf16, top-100; per-query and
+shared-candidate schedules), the FP8 store at 1,000,000 docs with 64
+queries over all of them (throughput, error and top-10 overlap against the
+fp16 scorer, with and without an fp16 re-score of the FP8 top-100) and
+fused PQ (1,000,000 docs, M = 16, K = 256, 64 queries over all of them).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tms|reference]
 
@@ -43,7 +46,7 @@ N_DOCS, LO, HI, D, NQ, N_QUERIES, N_CAND, TOPK = 500_000, 32, 180, 128, 32, 16, 
 METRIC = "docs scored/sec"
 WORKLOAD = ("dense MaxSim at scale: 500,000 docs, Nd~U[32,180], d=128, packed; "
             "16 queries Nq=32 x 100,000-doc random candidate subsets; top-10")
-KERNEL_SRC = os.path.join(ROOT, "paper_2606_26439_gb300", "csrc", "tms_dense.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2606_26439_gb300", "csrc", "tms_dense_tc.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dense_tc_kernel_500k_docs_fp16.txt")
 
 
@@ -341,6 +344,73 @@ def time_dense_e2e(w, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps, h2d, d2h
 
 
+def fp8_store_row(stream, hbm_peak):
+    """1,000,000 docs (Nd~U[32,180], d=128) quantized to the FP8 store; 64
+    fp16 queries, each over every document, in the shared schedule.
+    Throughput of the FP8 pass, and its quality against the fp16 tensor-core
+    scorer on the same documents (itself within 1e-3 of FP64 in the parity
+    tests): relative score error over all 64M scores, overlap of the top-10,
+    and the overlap after re-scoring the FP8 top-100 with the fp16 scorer."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    dev = torch.device("cuda")
+    n, nQ, k_short = 1_000_000, 64, 100
+    lens = synth.lengths_uniform(n, LO, HI, 4)
+    tok, off, ln = synth.device_dense_corpus(lens, D, "f16", 4, dev)
+    Q = synth.queries(nQ, NQ, D, "f16", 4).to(dev)
+    tc, tsc = tms.quantize_e4m3(tok)
+    qc, qsc = tms.quantize_e4m3(Q)
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    co = torch.arange(0, (nQ + 1) * n, n, dtype=torch.int64, device=dev)
+    s8 = torch.empty((nQ, n), dtype=torch.float32, device=dev)
+    s16 = torch.empty((nQ, n), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            tms.score_fp8_shared(qc, qsc, tc, tsc, off, ln, ids, out=s8, stream=stream)
+        tms.score_dense_shared(Q, tok, off, ln, ids, out=s16, stream=stream)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = 3
+    with torch.cuda.stream(stream):
+        e[0].record(stream)
+        for _ in range(reps):
+            tms.score_fp8_shared(qc, qsc, tc, tsc, off, ln, ids, out=s8, stream=stream)
+        e[1].record(stream)
+        for _ in range(reps):
+            tms.score_dense_shared(Q, tok, off, ln, ids, out=s16, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    ms8 = e[0].elapsed_time(e[1]) / reps
+    ms16 = e[1].elapsed_time(e[2]) / reps
+    tok_total = int(lens.astype(np.int64).sum())
+    # quality against the fp16 scorer
+    rel = ((s8 - s16).abs() / s16.abs().clamp_min(1e-6))
+    t8s, t8p = tms.topk(s8.view(-1), co, k_short)
+    t16s, t16p = tms.topk(s16.view(-1), co, TOPK)
+    torch.cuda.synchronize()
+    top10_8 = t8p[:, :TOPK].cpu().numpy()
+    top10_16 = t16p.cpu().numpy()
+    overlap = float(np.mean([len(set(a) & set(b)) / TOPK for a, b in zip(top10_8, top10_16)]))
+    # two-stage: re-score the FP8 top-100 (positions are document ids here) in fp16
+    short = t8p.reshape(-1).contiguous()
+    sco = torch.arange(0, (nQ + 1) * k_short, k_short, dtype=torch.int64, device=dev)
+    rs = tms.score_dense(Q, tok, off, ln, short, sco)
+    rts, rtp = tms.topk(rs, sco, TOPK)
+    torch.cuda.synchronize()
+    short_np = short.view(nQ, k_short).cpu().numpy()
+    top10_rs = np.take_along_axis(short_np, rtp.cpu().numpy().astype(np.int64), axis=1)
+    overlap_rs = float(np.mean([len(set(a) & set(b)) / TOPK for a, b in zip(top10_rs, top10_16)]))
+    fl = iomodel.dense_alg_flops(tok_total * nQ, NQ, D)
+    row = {"docs_per_s": nQ * n / (ms8 * 1e-3), "kernel_ms": ms8, "fp16_shared_kernel_ms": ms16,
+           "speedup_vs_fp16": ms16 / ms8, "tflops": fl / (ms8 * 1e-3) / 1e12,
+           "store_reads_gbs": tok_total * (D + 4) * (nQ // 8) / (ms8 * 1e-3) / 1e9,
+           "rel_err_vs_fp16_mean": float(rel.mean()), "rel_err_vs_fp16_max": float(rel.max()),
+           "top10_overlap_vs_fp16": overlap, "top10_overlap_rescored_top100": overlap_rs}
+    del tok, tc, tsc, s8, s16, rel
+    torch.cuda.empty_cache()
+    return row
+
+
 def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     """bf16/fp32 of the headline workload, dimension tiling, fused PQ."""
     import torch
@@ -357,6 +427,41 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
             "achieved_gbs": alg / (kms * 1e-3) / 1e9, "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak}
         del w
         torch.cuda.empty_cache()
+    # FP8 E4M3 store of the headline workload (quantized on the device)
+    w = dense_workload("f16", lengths, cands, dev)
+    n_tok = w["tok"].shape[0]
+    tc, tsc = tms.quantize_e4m3(w["tok"])
+    qc, qsc = tms.quantize_e4m3(w["q"])
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        e[0].record(stream)
+        tms.quantize_e4m3(w["tok"], tc, tsc, stream=stream)
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    quant_ms = e[0].elapsed_time(e[1])
+    del w["tok"]
+    torch.cuda.empty_cache()
+    out = torch.empty(len(w["flat"]), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            tms.score_fp8(qc, qsc, tc, tsc, w["off"], w["ln"], w["f"], w["c"], out=out, stream=stream)
+    torch.cuda.synchronize()
+    reps = 20
+    with torch.cuda.stream(stream):
+        e[0].record(stream)
+        for _ in range(reps):
+            tms.score_fp8(qc, qsc, tc, tsc, w["off"], w["ln"], w["f"], w["c"], out=out, stream=stream)
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    kms = e[0].elapsed_time(e[1]) / reps
+    alg = iomodel.fp8_alg_bytes(w["tokens"], len(w["flat"]), N_QUERIES, NQ, D)
+    qbytes = iomodel.quantize_alg_bytes(n_tok, D, 2)
+    rows["fp8_e4m3"] = {"docs_per_s": len(w["flat"]) / (kms * 1e-3), "kernel_ms": kms,
+                        "achieved_gbs": alg / (kms * 1e-3) / 1e9, "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak,
+                        "quantize_corpus_ms": quant_ms, "quantize_gbs": qbytes / (quant_ms * 1e-3) / 1e9}
+    del w, tc, tsc, qc, qsc, out
+    torch.cuda.empty_cache()
+    rows["fp8_e4m3_shared_1m"] = fp8_store_row(stream, hbm_peak)
     # dimension tiling: 200K docs, 32 queries over all docs, bf16, top-100
     n3 = 200_000
     len3 = synth.lengths_uniform(n3, LO, HI, 2)

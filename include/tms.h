@@ -113,6 +113,63 @@ tms_status tms_score_dense_shared(const void *queries, tms_dtype dtype, int n_qu
                                   cudaStream_t stream);
 
 /*
+ * FP8 E4M3 token store (an extension of the paper's fp16/bf16 scoring;
+ * E4M3 = 1 sign, 4 exponent (bias 7) and 3 fraction bits, max 448, no
+ * infinities).  A stored row of d codes with scale s stands for the vector
+ * s * decode(codes).
+ *
+ * Quantize `rows` rows of x [rows][d] (dtype fp16 / bf16 / fp32, finite
+ * values), one warp per row: amax = max |x[r][t]| and
+ * scales[r] = amax / 448, codes[r][t] = E4M3(x[r][t] / scales[r]) rounded
+ * to nearest even with saturation to +-448; both divisions are IEEE fp32.
+ * A row with scale 0 gets zero codes.  Used for document rows (the store)
+ * and query rows alike.
+ *
+ *   codes   [rows][d] uint8 (output), 16-byte aligned.
+ *   scales  [rows] fp32 (output), 4-byte aligned.
+ *
+ * Limits: 16 <= d <= 1024, d % 16 == 0; x 16-byte aligned.
+ */
+tms_status tms_quantize_e4m3(const void *x, tms_dtype dtype, int64_t rows, int d, uint8_t *codes, float *scales,
+                             cudaStream_t stream);
+
+/*
+ * Dense MaxSim (Eq. 1) on the FP8 store: with q_i = q_scales[q][i] *
+ * decode(q_codes[q][i]) and x_j = doc_scales[row] * decode(doc_codes[row]),
+ *   score = sum_i max_j q_i . x_j
+ *         = sum_i q_scales[q][i] * max_j (doc_scales[row_j] * (codes_i . codes_j))
+ * with the E4M3 x E4M3 products summed in fp32 on the tensor cores
+ * (tcgen05 kind::f8f6f4): the row scale is applied before the max.
+ *
+ *   q_codes     [n_queries][nq][d] uint8;  q_scales [n_queries][nq] fp32.
+ *   doc_codes   [n_tokens][d] uint8, packed like doc_tokens;
+ *   doc_scales  [n_tokens] fp32.
+ *   other arguments and the error behaviour as for tms_score_dense.
+ *
+ * Limits: 1 <= nq <= 128; 16 <= d <= 1024 with d % 16 == 0; codes and
+ * index arrays 16-byte aligned, scales 4-byte aligned; the query tile
+ * (nq rounded up to 32) x (d rounded up to 128) bytes must fit one CTA's
+ * shared memory next to two 16 KB stages (as for tms_score_dense, in
+ * bytes), else TMS_ERR_UNSUPPORTED.  Scales must be finite and >= 0.
+ */
+tms_status tms_score_fp8(const uint8_t *q_codes, const float *q_scales, int n_queries, int nq, int d,
+                         const uint8_t *doc_codes, const float *doc_scales, int64_t n_tokens,
+                         const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                         const int32_t *cand_ids, const int64_t *cand_offsets, int64_t n_cand,
+                         float *out_scores, cudaStream_t stream);
+
+/*
+ * tms_score_fp8 for queries that all score ONE candidate list, stacked in
+ * groups of up to 8 in the MMA N dimension (as tms_score_dense_shared):
+ * out_scores [n_queries][n_cand].  Limits as tms_score_fp8 with nq <= 32
+ * (nq > 32 returns TMS_ERR_UNSUPPORTED) and n_queries / group * n_cand < 2^31.
+ */
+tms_status tms_score_fp8_shared(const uint8_t *q_codes, const float *q_scales, int n_queries, int nq, int d,
+                                const uint8_t *doc_codes, const float *doc_scales, int64_t n_tokens,
+                                const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                                const int32_t *cand_ids, int64_t n_cand, float *out_scores, cudaStream_t stream);
+
+/*
  * PQ distance table (Section 4.2, Phase 1):
  *   lut[q][i][mm][kk] = sum_{t < d/m} queries[q][i][mm*(d/m) + t] * codebook[mm][kk][t]
  * computed in fp32 with fused multiply-adds in ascending t.

@@ -29,11 +29,12 @@ tms_status current_device(DeviceInfo* out);
 tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
                           uint64_t rows, uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows);
 
-// Encode the 3-D view {64 elements, rows, chunk} of a row-major
-// [rows][nchunks * 64] 2-byte array (chunk stride 128 bytes), box
-// {64, box_rows, 2}, 128-byte swizzle, zero fill outside.
+// Encode the 3-D view {chunk_elems elements, rows, chunk} of a row-major
+// [rows][nchunks * chunk_elems] array whose chunks are 128 bytes (chunk
+// stride 128 bytes), box {chunk_elems, box_rows, 2}, 128-byte swizzle,
+// zero fill outside.
 tms_status encode_tmap_rows_chunks(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int nchunks,
-                                   uint64_t rows, uint64_t row_bytes, uint32_t box_rows);
+                                   uint64_t rows, uint64_t row_bytes, uint32_t box_rows, uint32_t chunk_elems);
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

@@ -65,6 +65,20 @@ def dense_alg_bytes(total_tokens, n_cand, n_queries, nq, d, elem):
             + n_cand * (META_BYTES_PER_CAND + SCORE_BYTES))
 
 
+def fp8_alg_bytes(total_tokens, n_cand, n_queries, nq, d):
+    """Algorithmic HBM bytes of one pass over the FP8 E4M3 store: d one-byte
+    codes and one fp32 scale per candidate token, the same per query token,
+    metadata read and one fp32 score written per candidate."""
+    return (total_tokens * (d + 4) + n_queries * nq * (d + 4)
+            + n_cand * (META_BYTES_PER_CAND + SCORE_BYTES))
+
+
+def quantize_alg_bytes(rows, d, elem):
+    """HBM bytes of quantizing rows x d elements of `elem` bytes to E4M3:
+    read once, one-byte codes and one fp32 scale per row written."""
+    return rows * (d * elem + d + 4)
+
+
 def dense_alg_flops(total_tokens, nq, d):
     """Dot-product FLOPs of one dense pass: 2 Nq d per (query token, doc token)."""
     return 2 * total_tokens * nq * d

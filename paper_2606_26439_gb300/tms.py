@@ -29,8 +29,9 @@ TMS_DEVERR_TIMEOUT = 4
 TMS_DEVERR_BAD_CSR = 8
 
 #: every symbol include/tms.h declares
-EXPORTS = ("tms_score_dense", "tms_score_dense_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
-           "tms_get_device_error", "tms_status_string", "tms_version")
+EXPORTS = ("tms_score_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
+           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk", "tms_get_device_error",
+           "tms_status_string", "tms_version")
 
 _lib = None
 _lock = threading.Lock()
@@ -59,6 +60,9 @@ def lib(build_if_missing: bool = True):
             L = ctypes.CDLL(path)
             L.tms_score_dense.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
             L.tms_score_dense_shared.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p]
+            L.tms_quantize_e4m3.argtypes = [_p, _i32, _i64, _i32, _p, _p, _p]
+            L.tms_score_fp8.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_score_fp8_shared.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p]
             L.tms_build_pq_lut.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _p]
             L.tms_score_pq.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
             L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
@@ -66,7 +70,8 @@ def lib(build_if_missing: bool = True):
             L.tms_status_string.argtypes = [_i32]
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
-            for name in ("tms_score_dense", "tms_score_dense_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
+            for name in ("tms_score_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
+                         "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
                          "tms_get_device_error", "tms_version"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -94,6 +99,22 @@ def tms_score_dense_shared(queries, dtype, n_queries, nq, d, doc_tokens, n_token
                            n_docs, cand_ids, n_cand, out_scores, stream) -> int:
     return lib().tms_score_dense_shared(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets,
                                         doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream)
+
+
+def tms_quantize_e4m3(x, dtype, rows, d, codes, scales, stream) -> int:
+    return lib().tms_quantize_e4m3(x, dtype, rows, d, codes, scales, stream)
+
+
+def tms_score_fp8(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets, doc_lengths,
+                  n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream) -> int:
+    return lib().tms_score_fp8(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                               doc_lengths, n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream)
+
+
+def tms_score_fp8_shared(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                         doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream) -> int:
+    return lib().tms_score_fp8_shared(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens,
+                                      doc_offsets, doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream)
 
 
 def tms_build_pq_lut(queries, qdtype, n_queries, nq, d, codebook, m, k, lut, stream) -> int:
@@ -176,6 +197,54 @@ def score_dense_shared(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, 
         _dev(queries), _dtype_code(queries), nQ, nq, d, _dev(doc_tokens, queries.dtype), doc_tokens.shape[0],
         _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
         _dev(cand_ids, torch.int32), n_cand, _dev(out, torch.float32), _stream_ptr(stream)))
+    return out
+
+
+def quantize_e4m3(x, codes=None, scales=None, stream=None):
+    """Per-row E4M3 codes (uint8, x's shape) and fp32 scales (x.shape[:-1])
+    of a CUDA tensor x [..., d] (fp16 / bf16 / fp32)."""
+    torch = _torch()
+    d = x.shape[-1]
+    rows = x.numel() // d if d else 0
+    if codes is None:
+        codes = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    if scales is None:
+        scales = torch.empty(x.shape[:-1], dtype=torch.float32, device=x.device)
+    _check("tms_quantize_e4m3", tms_quantize_e4m3(_dev(x), _dtype_code(x), rows, d, _dev(codes, torch.uint8),
+                                                  _dev(scales, torch.float32), _stream_ptr(stream)))
+    return codes, scales
+
+
+def score_fp8(q_codes, q_scales, doc_codes, doc_scales, doc_offsets, doc_lengths, cand_ids, cand_offsets,
+              out=None, stream=None):
+    """MaxSim on the FP8 store.  q_codes [n_queries][nq][d] uint8, q_scales
+    [n_queries][nq]; doc_codes [n_tokens][d] uint8, doc_scales [n_tokens]."""
+    torch = _torch()
+    nQ, nq, d = q_codes.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty(n_cand, dtype=torch.float32, device=q_codes.device)
+    _check("tms_score_fp8", tms_score_fp8(
+        _dev(q_codes, torch.uint8), _dev(q_scales, torch.float32), nQ, nq, d, _dev(doc_codes, torch.uint8),
+        _dev(doc_scales, torch.float32), doc_codes.shape[0], _dev(doc_offsets, torch.int64),
+        _dev(doc_lengths, torch.int32), doc_offsets.shape[0], _dev(cand_ids, torch.int32),
+        _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32), _stream_ptr(stream)))
+    return out
+
+
+def score_fp8_shared(q_codes, q_scales, doc_codes, doc_scales, doc_offsets, doc_lengths, cand_ids, out=None,
+                     stream=None):
+    """score_fp8 of every query over ONE candidate list; out [n_queries][n_cand]."""
+    torch = _torch()
+    nQ, nq, d = q_codes.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty((nQ, n_cand), dtype=torch.float32, device=q_codes.device)
+    _check("tms_score_fp8_shared", tms_score_fp8_shared(
+        _dev(q_codes, torch.uint8), _dev(q_scales, torch.float32), nQ, nq, d, _dev(doc_codes, torch.uint8),
+        _dev(doc_scales, torch.float32), doc_codes.shape[0], _dev(doc_offsets, torch.int64),
+        _dev(doc_lengths, torch.int32), doc_offsets.shape[0], _dev(cand_ids, torch.int32), n_cand,
+        _dev(out, torch.float32), _stream_ptr(stream)))
     return out
 
 

@@ -98,6 +98,18 @@ def queries(n_queries: int, nq: int, d: int, dtype: str, seed: int):
     return cast(q, dtype)
 
 
+def e4m3_codes(n: int, d: int, seed: int, stream: int = 0) -> np.ndarray:
+    """n x d uniformly random finite E4M3 bit patterns (uint8; the two NaN
+    patterns 0x7F and 0xFF are never drawn)."""
+    c = rng(seed, 14, stream).integers(0, 254, size=(n, d))
+    return (c + (c >= 127)).astype(np.uint8)
+
+
+def row_scales(n: int, seed: int, stream: int = 0, lo: float = 0.5 / 448, hi: float = 2.0 / 448) -> np.ndarray:
+    """n fp32 row scales drawn uniformly from [lo, hi)."""
+    return rng(seed, 15, stream).uniform(lo, hi, n).astype(np.float32)
+
+
 def pq_corpus(lengths: np.ndarray, M: int, K: int, dsub: int, seed: int, noise: float = 0.05):
     """PQ corpus on the host: (codebook [M][K][dsub] f32, codes [n_tokens][M] u8,
     reconstructed-from-noise token values [n_tokens][M*dsub] f32, offsets, lengths)."""
@@ -157,6 +169,25 @@ def device_dense_corpus(lengths: np.ndarray, d: int, dtype: str, seed: int, devi
     n_tok = int(lengths.astype(np.int64).sum())
     tok = device_unit_rows(n_tok, d, dtype, seed, 1, device)
     return (tok, torch.from_numpy(off).to(device), torch.from_numpy(lengths).to(device))
+
+
+def device_e4m3_store(lengths: np.ndarray, d: int, seed: int, device="cuda", chunk_rows: int = 1 << 22):
+    """Packed random E4M3 store built on the device: (codes [n_tokens][d]
+    uint8, scales [n_tokens] fp32, offsets, lengths) as CUDA tensors; codes
+    uniform over the 254 finite patterns, scales uniform in [0.5, 2] / 448."""
+    lengths = np.asarray(lengths, np.int32)
+    off = offsets_of(lengths)
+    n_tok = int(lengths.astype(np.int64).sum())
+    g = _gen(device, seed, 16, 0)
+    codes = torch.empty((n_tok, d), dtype=torch.uint8, device=device)
+    for r0 in range(0, n_tok, chunk_rows):
+        r1 = min(n_tok, r0 + chunk_rows)
+        c = torch.randint(0, 254, (r1 - r0, d), generator=g, device=device, dtype=torch.int16)
+        c += (c >= 127).to(torch.int16)
+        codes[r0:r1].copy_(c)
+        del c
+    scales = torch.rand(n_tok, generator=g, device=device, dtype=torch.float32) * (1.5 / 448) + 0.5 / 448
+    return codes, scales, torch.from_numpy(off).to(device), torch.from_numpy(lengths).to(device)
 
 
 def device_candidates(n_docs: int, n_cand: int, seed: int, query_index: int, device="cuda"):
