@@ -146,8 +146,8 @@ tms_status tms_quantize_e4m3(const void *x, tms_dtype dtype, int64_t rows, int d
  *   doc_scales  [n_tokens] fp32.
  *   other arguments and the error behaviour as for tms_score_dense.
  *
- * Limits: 1 <= nq <= 128; 16 <= d <= 1024 with d % 16 == 0; codes and
- * index arrays 16-byte aligned, scales 4-byte aligned; the query tile
+ * Limits: 1 <= nq <= 128; 16 <= d <= 1024 with d % 16 == 0; codes,
+ * doc_scales and index arrays 16-byte aligned, q_scales 4-byte aligned; the query tile
  * (nq rounded up to 32) x (d rounded up to 128) bytes must fit one CTA's
  * shared memory next to two 16 KB stages (as for tms_score_dense, in
  * bytes), else TMS_ERR_UNSUPPORTED.  Scales must be finite and >= 0.

@@ -95,6 +95,17 @@ tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const voi
     return r == CUDA_SUCCESS ? TMS_OK : TMS_ERR_INVALID_ARG;
 }
 
+tms_status encode_tmap_1d_f32(CUtensorMap* map, const void* base, uint64_t n, uint32_t box_elems) {
+    if (!load_encoder()) return TMS_ERR_CUDA;
+    const cuuint64_t dims[1] = {n > 0 ? n : 1};
+    const cuuint32_t box[1] = {box_elems};
+    const cuuint32_t estr[1] = {1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<void*>(base), dims, nullptr, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? TMS_OK : TMS_ERR_INVALID_ARG;
+}
+
 }  // namespace tms
 
 extern "C" {

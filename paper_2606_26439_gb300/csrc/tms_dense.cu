@@ -162,13 +162,9 @@ extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int 
             static_cast<const float*>(queries), static_cast<const float*>(doc_tokens), a, d);
         return launch_status(cudaGetLastError());
     }
-    const int nb = (nq + 31) / 32;
-    switch (nb) {
-        case 1: return dense::launch_tc<1, false, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
-        case 2: return dense::launch_tc<2, false, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
-        case 3: return dense::launch_tc<3, false, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
-        default: return dense::launch_tc<4, false, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
-    }
+    a.bpc = (nq + 31) / 32;
+    a.qbox = 32 * a.bpc;
+    return dense::launch_tc<1, false, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
 }
 
 extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
@@ -211,11 +207,12 @@ extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtyp
         if (n_groups * n_cand >= (int64_t(1) << 31)) return TMS_ERR_UNSUPPORTED;
         a.n_flat = n_groups * n_cand;
         a.group = group;
-        switch (group) {
-            case 2: st = dense::launch_tc<2, true, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream); break;
-            case 4: st = dense::launch_tc<4, true, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream); break;
-            default: st = dense::launch_tc<8, true, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream); break;
-        }
+        a.bpc = group;
+        a.qbox = 32;
+        st = group == 8 ? dense::launch_tc<2, true, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                          stream)
+                        : dense::launch_tc<1, true, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                          stream);
         if (st != TMS_ERR_UNSUPPORTED) return st;
     }
     return TMS_ERR_UNSUPPORTED;

@@ -5,6 +5,16 @@
 // document and query rows stored as fp16 / bf16 or as FP8 E4M3 codes with
 // one fp32 scale per row (F8).
 //
+// Orientation: the MMA computes S^T = Q D^T, query tokens along M (tensor-
+// memory lanes, one per epilogue thread) and document rows along N
+// (tensor-memory columns).  The max over a document's tokens (Eq. 1's
+// inner max) is then a running max inside each thread's registers -- no
+// cross-lane reduction per tile.  M is always 128: the query tile's 32-row
+// blocks (token blocks of one query, or the queries of a shared group) are
+// replicated down the 128 rows when they are fewer, and each copy scores
+// its own slice of the tile's columns, so all four epilogue warps work on
+// every tile.
+//
 //   * Producer warp: reads candidate metadata (id -> offset, length), and
 //     streams each document's token rows from HBM into a ring of shared-
 //     memory stages with TMA box loads (128-byte swizzle).  A stage holds
@@ -12,21 +22,22 @@
 //     elements) of up to 128 rows of ONE document, loaded as one box whose
 //     height (8, 16, ..., 128) covers the tile's rows with at most 7 rows of
 //     over-fetch.  Each token is read from HBM once (Theorem 1 with
-//     BQ = Nq).
-//   * MMA warp: one elected thread issues tcgen05.mma (M = 128 document
-//     rows, N = Nq padded to 32, K = 32 bytes: 16 fp16/bf16 elements with
-//     kind::f16, 32 E4M3 elements with kind::f8f6f4) over every dimension
-//     chunk of a tile, accumulating the partial dot products in tensor
-//     memory before any max is taken -- the paper's dimension tiling
-//     (Section 3), with the K loop running through TMEM.
-//   * Four epilogue warps: thread = document row (TMEM lane).  Each reads
-//     its row's accumulators with tcgen05.ld, multiplies them by the row's
-//     scale (F8), and takes per-query-token column maxima with redux.sync
-//     over exactly the tile's valid rows.  At a document's end the four
-//     warps' maxima meet in shared memory, one warp sums them over the Nq
-//     query tokens (times each token's scale, F8) in a fixed order and
-//     writes the score once.  The Nq x Nd similarity matrix never reaches
-//     HBM and no atomics or memset are needed.
+//     BQ = Nq, or the whole group of queries in the shared schedule).  F8:
+//     the tile's row scales follow through a small ring of 1-D TMA loads.
+//   * MMA warp: one thread issues tcgen05.mma (M = 128 query rows,
+//     N = the tile's rows rounded up to 16, K = 32 bytes: 16 fp16/bf16
+//     elements with kind::f16, 32 E4M3 elements with kind::f8f6f4) over
+//     every dimension chunk of a tile, accumulating the partial dot
+//     products in tensor memory before any max is taken -- the paper's
+//     dimension tiling (Section 3), with the K loop running through TMEM.
+//   * Four epilogue warps: thread = query row (TMEM lane).  Each loads its
+//     slice of the tile's columns with tcgen05.ld, multiplies column j by
+//     document row j's scale (F8), drops columns past the tile's rows, and
+//     folds the rest into its running max.  At a document's end the copies'
+//     maxima meet in shared memory and one warp sums them over the query
+//     tokens (times each token's scale, F8) in a fixed order and writes the
+//     score once.  The Nq x Nd similarity matrix never reaches HBM and no
+//     atomics or memset are needed.
 //
 // Every wait is bounded (see tms_common.cuh); a timeout sets
 // TMS_DEVERR_TIMEOUT and the CTA drains its in-flight copies and MMAs,
@@ -42,20 +53,18 @@ namespace tms {
 
 namespace dense {
 
-constexpr int kRows = 128;                    // document rows per tile (MMA M)
+constexpr int kRows = 128;                    // document rows per tile (MMA N at most)
 constexpr int kChunkBytes = kRows * 128;      // 16 KB: 128 rows x one 128-byte dimension chunk
 // Elements per 128-byte dimension chunk (one 128-byte swizzle row).
 __host__ __device__ constexpr int chunk_elems(bool f8) { return f8 ? 128 : 64; }
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kInfoRing = 16;
-// One epilogue group of 4 warps per CTA.  (The kernel keeps the general
-// multi-group bookkeeping; two CTAs per SM -- each a full producer / MMA /
-// epilogue pipeline -- replace a second group: the tensor core accepts one
-// small MMA per ~84 cycles whatever its N, and the issuing thread blocks
-// meanwhile, so a second CTA's MMA thread fills the tensor pipe while the
-// first one waits or does its per-tile bookkeeping.)
-__host__ __device__ constexpr int epi_groups(int NT) { return 1; }
-__host__ __device__ constexpr int num_threads(int NT) { return 64 + 128 * epi_groups(NT); }
+constexpr int kScaleRing = 8;                 // F8: tiles whose row scales are in flight or held
+constexpr int kScaleBox = 136;                // floats per scale load: 128 rows + up to 3 of 16-byte alignment
+constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a multiple of 128 B)
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, four epilogue warps
+constexpr int kAcc = 2;                       // accumulator buffers (each H x 128 TMEM columns)
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
 
@@ -64,7 +73,7 @@ enum : int { kFirst = 1, kLast = 2, kEnd = 4 };
 struct TileInfo {
     int f;      // flat candidate index
     int r;      // valid rows in this tile (1..128)
-    int q;      // query index
+    int q;      // query index (shared mode: group index)
     int flags;  // kFirst / kLast / kEnd
     int row0;   // token row of the tile's first row
     int pad;
@@ -83,54 +92,44 @@ struct Args {
     int64_t n_tokens;
     int64_t n_cand;    // entries of cand_ids
     int64_t n_flat;    // work items: n_cand, or n_groups * n_cand in shared mode
-    int group;         // shared mode: queries per group (each a 32-column block); 0 otherwise
+    int group;         // shared mode: queries per group; 0 otherwise
     int n_queries;
     int nq;
     int nchunks;   // ceil(d / chunk_elems)
     int cps;       // dimension chunks per stage: 2 with the 3-D tensor view (d % chunk_elems == 0), else 1
     int stages;
     int qslots;
-    uint32_t idesc;
+    int bpc;         // 32-row query blocks per copy: ceil(nq / 32) token blocks, or the group's queries
+    int reps;        // copies stacked in M; copy c scores tile columns [c * 128 / reps, (c + 1) * 128 / reps)
+    int rows_alloc;  // query rows held per dimension chunk: 32 * bpc * reps
+    int qbox;        // rows of one query TMA box: 32 * bpc (per-query), 32 (shared)
+    uint32_t idesc;  // instruction descriptor, N field left 0 (set per tile)
 };
 
 struct Layout {
-    int stage_off, q_off, part_off, info_off, bar_off, misc_off, total;
+    int q_off, stage_off, part_off, sc_off, info_off, bar_off, misc_off, total;
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
-__host__ __device__ inline Layout make_layout(int stages, int cps, int qslots, int nchunks, int NT, int acc) {
+// The query region comes first: the MMA reads 128 (x H) rows from each
+// query chunk, and rows past rows_alloc fall on the following chunk or on
+// the stage ring -- always inside the allocation, and they only feed
+// accumulator rows that nothing reads.  1 KB after the stage ring likewise
+// absorbs the document operand's read of up to 8 rows past a chunk (N is
+// the tile's rows rounded up to 16, the box up to 8).
+__host__ __device__ inline Layout make_layout(int stages, int cps, int qslots, int nchunks, int rows_alloc, int H,
+                                              bool f8) {
     Layout L;
-    L.stage_off = 0;
-    L.q_off = stages * cps * kChunkBytes;
-    L.part_off = L.q_off + qslots * nchunks * NT * 128;
-    L.info_off = L.part_off + epi_groups(NT) * 2 * 4 * NT * 4;
+    L.q_off = 0;
+    L.stage_off = (qslots * nchunks * rows_alloc * 128 + 1023) & ~1023;
+    L.part_off = L.stage_off + stages * cps * kChunkBytes + 1024;
+    L.sc_off = L.part_off + 2 * 4 * H * 32 * 4;
+    L.info_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
     L.bar_off = L.info_off + kInfoRing * static_cast<int>(sizeof(TileInfo));
-    const int nbar = 2 * stages + 2 * acc + 2 * qslots + 2 * kInfoRing + epi_groups(NT) * 4 + 1;
+    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * kInfoRing + 4 + 2 * kScaleRing + 1;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
-}
-
-// A tile's K-steps are spread round-robin over `partials(NT)` accumulators
-// so that consecutive MMAs never depend on each other (a chain of tiny
-// M=128 x N=32 x K=16 MMAs into one accumulator is latency-bound); the
-// epilogue adds the partials before the max.
-//
-// Each epilogue group owns its own ring of acc_buffers(NT) accumulators,
-// used in the order of that group's tiles.  (With one shared ring a group
-// that skips the other group's tiles could wait on the second use of an
-// accumulator whose barrier has not finished its first phase -- and an
-// mbarrier parity wait cannot tell those apart.)
-__host__ __device__ constexpr int partials(int NT) { return NT <= 32 ? 4 : (NT <= 128 ? 2 : 1); }
-__host__ __device__ constexpr int acc_buffers(int NT) { return 2; }
-
-__host__ __device__ constexpr int acc_total(int NT) { return epi_groups(NT) * acc_buffers(NT); }
-
-__host__ __device__ constexpr int tmem_cols(int NT) {
-    return (acc_total(NT) * partials(NT) * NT <= 32) ? 32
-         : (acc_total(NT) * partials(NT) * NT <= 64) ? 64
-         : (acc_total(NT) * partials(NT) * NT <= 128) ? 128
-         : (acc_total(NT) * partials(NT) * NT <= 256) ? 256 : 512;
 }
 
 // Candidate metadata for the producer: lane l of the warp holds the raw
@@ -190,26 +189,25 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
 // {128 bytes of elements, rows, chunk} of the [n_tokens][d] array (chunk
 // stride 128 bytes): one box brings two chunks of r rows, landing as
 // [chunk][row][128 B] -- already the 128-byte-swizzle K-major layout.
+// scales (F8): the [n_tokens] fp32 row scales, boxes of kScaleBox.
 struct Maps {
     CUtensorMap q;
     CUtensorMap doc[kBoxKinds];
+    CUtensorMap scales;
 };
 
+// H: 128-row halves of the query tile (2 for a shared group of 8 queries).
 // SH (shared mode): the launch's queries all score one candidate list; a
-// "query" of the pipeline is then a group of up to NB queries stacked in
-// the MMA's N dimension (32 columns each), so each document tile is read
-// once per group, and the epilogue writes one score per query of the group.
+// "query" of the pipeline is then a group of up to 4 H queries stacked in
+// M, so each document tile is read once per group, and the epilogue
+// writes one score per query of the group.
 // F8: rows are E4M3 codes; similarities are scaled by the document row's
 // scale before the max and by the query token's scale before the sum.
-template <int NB, int CTAS, bool SH, bool F8>
-__global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
+template <int H, int CTAS, bool SH, bool F8>
+__global__ void __launch_bounds__(kThreads, CTAS)
     dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
-    constexpr int NT = NB * 32;
     constexpr int CE = chunk_elems(F8);
-    constexpr int kEpiGroups = epi_groups(NT);
-    constexpr int A = acc_buffers(NT);   // per epilogue group
-    constexpr int P = partials(NT);
-    constexpr uint32_t TCOLS = tmem_cols(NT);
+    constexpr uint32_t TCOLS = kAcc * H * 128;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -219,24 +217,28 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
     const int CPS = a.cps;
     const int stage_bytes = CPS * kChunkBytes;
     const int stages_per_tile = (NCH + CPS - 1) / CPS;
-    const Layout L = make_layout(S, CPS, QS, NCH, NT, acc_total(NT));
+    const int qslot_bytes = NCH * a.rows_alloc * 128;
+    const Layout L = make_layout(S, CPS, QS, NCH, a.rows_alloc, H, F8);
 
-    uint8_t* stage_base = smem + L.stage_off;
     uint8_t* q_base = smem + L.q_off;
-    float* part = reinterpret_cast<float*>(smem + L.part_off);  // [group][2][4][NT]
+    uint8_t* stage_base = smem + L.stage_off;
+    float* part = reinterpret_cast<float*>(smem + L.part_off);  // [2][4 H][32]
+    float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // [kScaleRing][kScalePitch]
     TileInfo* info = reinterpret_cast<TileInfo*>(smem + L.info_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;
     uint64_t* empty = full + S;
     uint64_t* tfull = empty + S;
-    uint64_t* tempty = tfull + acc_total(NT);
-    uint64_t* qfull = tempty + acc_total(NT);
+    uint64_t* tempty = tfull + kAcc;
+    uint64_t* qfull = tempty + kAcc;
     uint64_t* qempty = qfull + QS;
     uint64_t* ifull = qempty + QS;
     uint64_t* iempty = ifull + kInfoRing;
-    uint64_t* pfull = iempty + kInfoRing;       // [group][2]
-    uint64_t* pempty = pfull + 2 * kEpiGroups;  // [group][2]
-    uint64_t* mdone = pempty + 2 * kEpiGroups;
+    uint64_t* pfull = iempty + kInfoRing;  // [2]
+    uint64_t* pempty = pfull + 2;          // [2]
+    uint64_t* sfull = pempty + 2;          // [kScaleRing]
+    uint64_t* sempty = sfull + kScaleRing; // [kScaleRing]
+    uint64_t* mdone = sempty + kScaleRing;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
 
@@ -248,9 +250,9 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < acc_total(NT); ++i) {
+        for (int i = 0; i < kAcc; ++i) {
             mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], 4);
+            mbar_init(&tempty[i], kEpiWarps);
         }
         for (int i = 0; i < QS; ++i) {
             mbar_init(&qfull[i], 1);
@@ -258,18 +260,24 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
         }
         for (int i = 0; i < kInfoRing; ++i) {
             mbar_init(&ifull[i], 1);
-            mbar_init(&iempty[i], 1 + 4 * kEpiGroups);
+            mbar_init(&iempty[i], 1 + kEpiWarps);
         }
-        for (int i = 0; i < 2 * kEpiGroups; ++i) {
-            mbar_init(&pfull[i], 4);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&pfull[i], kEpiWarps);
             mbar_init(&pempty[i], 1);
+        }
+        for (int i = 0; i < kScaleRing; ++i) {
+            mbar_init(&sfull[i], 1);
+            mbar_init(&sempty[i], kEpiWarps);
         }
         mbar_init(mdone, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 0) {
-        if (lane <= kBoxKinds) prefetch_tensormap(lane == 0 ? &maps.q : &maps.doc[lane - 1]);
+        if (lane == 0) prefetch_tensormap(&maps.q);
+        if (lane >= 1 && lane <= kBoxKinds) prefetch_tensormap(&maps.doc[lane - 1]);
+        if (F8 && lane == kBoxKinds + 1) prefetch_tensormap(&maps.scales);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, TCOLS);
@@ -334,6 +342,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
             } else {
                 for (int r0 = 0; r0 < len; r0 += kRows) {
                     const int r = min(kRows, len - r0);
+                    const int y0 = static_cast<int>(off) + r0;
                     const int ii = t % kInfoRing;
                     if (!warp_wait(&iempty[ii], ((t / kInfoRing) & 1) ^ 1, abort_flag, a.err)) {
                         aborted = true;
@@ -345,10 +354,22 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                         ti.r = r;
                         ti.q = q;
                         ti.flags = (r0 == 0 ? kFirst : 0) | (r0 + kRows >= len ? kLast : 0);
-                        ti.row0 = static_cast<int>(off) + r0;
+                        ti.row0 = y0;
                         ti.pad = 0;
                         info[ii] = ti;
                         mbar_arrive(&ifull[ii]);
+                    }
+                    if (F8) {
+                        // the tile's row scales, from the 16-byte boundary at or below its first row
+                        const int j = t % kScaleRing;
+                        if (!warp_wait(&sempty[j], ((t / kScaleRing) & 1) ^ 1, abort_flag, a.err)) {
+                            aborted = true;
+                            break;
+                        }
+                        if (lane == 0) {
+                            mbar_arrive_expect_tx(&sfull[j], static_cast<uint32_t>(kScaleBox * 4));
+                            tma_load_1d(sc + j * kScalePitch, &maps.scales, y0 & ~3, &sfull[j], pol_stream);
+                        }
                     }
                     ++t;
                     // A new query's rows go to the next query slot.  The
@@ -361,16 +382,19 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                             break;
                         }
                         if (lane == 0) {
-                            mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(NCH * NT * 128));
-                            uint8_t* qdst = q_base + slot * NCH * NT * 128;
+                            mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(qslot_bytes));
+                            uint8_t* qdst = q_base + slot * qslot_bytes;
                             for (int kc = 0; kc < NCH; ++kc) {
-                                if (SH) {  // one 32-row box per query of the group
-                                    for (int g = 0; g < NB; ++g)
-                                        tma_load_2d(qdst + kc * NT * 128 + g * 32 * 128, &maps.q, kc * CE,
-                                                    (q * a.group + g) * a.nq, &qfull[slot], pol_keep);
-                                } else {
-                                    tma_load_2d(qdst + kc * NT * 128, &maps.q, kc * CE, q * a.nq,
-                                                &qfull[slot], pol_keep);
+                                uint8_t* cdst = qdst + kc * a.rows_alloc * 128;
+                                for (int rp = 0; rp < a.reps; ++rp) {
+                                    if (SH) {  // one 32-row box per query of the group
+                                        for (int g = 0; g < a.bpc; ++g)
+                                            tma_load_2d(cdst + (rp * a.bpc + g) * 32 * 128, &maps.q, kc * CE,
+                                                        (q * a.group + g) * a.nq, &qfull[slot], pol_keep);
+                                    } else {
+                                        tma_load_2d(cdst + rp * a.qbox * 128, &maps.q, kc * CE, q * a.nq,
+                                                    &qfull[slot], pol_keep);
+                                    }
                                 }
                             }
                         }
@@ -378,7 +402,6 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                         cur_q = q;
                     }
                     const int n8 = (r + 7) & ~7;
-                    const int y0 = static_cast<int>(off) + r0;
                     const CUtensorMap* dmap = &maps.doc[(n8 >> 3) - 1];
                     for (int st = 0; st < stages_per_tile; ++st) {
                         if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
@@ -437,6 +460,10 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                 }
                 drain_wait(&full[ss], pp);
             }
+            if (F8) {
+                const int ns = t < kScaleRing ? t : kScaleRing;
+                for (int i = 1; i <= ns; ++i) drain_wait(&sfull[(t - i) % kScaleRing], ((t - i) / kScaleRing) & 1);
+            }
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -448,9 +475,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
             int s = 0;
             uint32_t ph = 0;
             int qi = 0, cur_q = -1, qslot = 0;
-            int acc0 = 0, acc1 = 0;  // tiles issued for epilogue group 0 / 1
-            uint32_t doc_ord = 0;
-            int owner = 0;
+            int k = 0;  // tiles issued
             bool any = false;
             for (int t = 0;; ++t) {
                 const int ii = t % kInfoRing;
@@ -465,41 +490,43 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                     ++qi;
                     cur_q = ti.q;
                 }
-                if (ti.flags & kFirst) {
-                    owner = static_cast<int>(doc_ord % kEpiGroups);
-                    ++doc_ord;
-                }
-                const int k = owner == 0 ? acc0 : acc1;
-                const int ab = owner * A + k % A;
-                if (!mbar_wait(&tempty[ab], ((k / A) & 1) ^ 1, abort_flag, a.err)) break;
+                const int ab = k % kAcc;
+                if (!mbar_wait(&tempty[ab], ((k / kAcc) & 1) ^ 1, abort_flag, a.err)) break;
                 tc_fence_after();
                 bool ok = true;
-                const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * P * NT);
-                const uint64_t q_desc = desc_sw128(smem_u32(q_base + qslot * NCH * NT * 128));
+                const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * H * 128);
+                const uint64_t q_desc = desc_sw128(smem_u32(q_base + qslot * qslot_bytes));
                 const int n8 = (ti.r + 7) & ~7;
+                const int n16 = (ti.r + 15) & ~15;
+                const uint32_t idesc = a.idesc | (static_cast<uint32_t>(n16 >> 3) << 17);
                 for (int st = 0; st < stages_per_tile; ++st) {
                     if (!mbar_wait(&full[s], ph, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    // chunk c of the stage starts c * n8 rows in: its rows
-                    // past n8 (and the tile's rows past r) are masked later.
+                    // chunk c of the stage starts c * n8 rows in; the MMA
+                    // reads n16 rows from there and the columns past the
+                    // tile's r rows are dropped by the epilogue.
                     const uint64_t s_desc = desc_sw128(smem_u32(stage_base + s * stage_bytes));
                     for (int c = 0; c < CPS; ++c) {
                         const int kc = st * CPS + c;
                         if (kc >= NCH) break;
-                        const uint64_t a_desc = s_desc + static_cast<uint64_t>((c * n8 * 128) >> 4);
-                        const uint64_t b_desc = q_desc + static_cast<uint64_t>((kc * NT * 128) >> 4);
+                        const uint64_t b_desc = s_desc + static_cast<uint64_t>((c * n8 * 128) >> 4);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const int ks = kc * 4 + kk;  // K-step of the tile
-                            if (F8)
-                                mma_f8(d_tmem + static_cast<uint32_t>((ks % P) * NT), a_desc + 2 * kk,
-                                       b_desc + 2 * kk, a.idesc, ks >= P ? 1u : 0u);
-                            else
-                                mma_f16(d_tmem + static_cast<uint32_t>((ks % P) * NT), a_desc + 2 * kk,
-                                        b_desc + 2 * kk, a.idesc, ks >= P ? 1u : 0u);
+                        for (int h = 0; h < H; ++h) {
+                            const uint64_t a_desc =
+                                q_desc + static_cast<uint64_t>(((kc * a.rows_alloc + h * 128) * 128) >> 4);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint32_t accumulate = (kc > 0 || kk > 0) ? 1u : 0u;
+                                if (F8)
+                                    mma_f8(d_tmem + static_cast<uint32_t>(h * 128), a_desc + 2 * kk, b_desc + 2 * kk,
+                                           idesc, accumulate);
+                                else
+                                    mma_f16(d_tmem + static_cast<uint32_t>(h * 128), a_desc + 2 * kk,
+                                            b_desc + 2 * kk, idesc, accumulate);
+                            }
                         }
                     }
                     mma_commit(&empty[s]);
@@ -511,10 +538,7 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
                 }
                 if (!ok) break;
                 mma_commit(&tfull[ab]);
-                if (owner == 0)
-                    ++acc0;
-                else
-                    ++acc1;
+                ++k;
             }
             // Every MMA this thread issued must finish before TMEM is freed.
             if (any) {
@@ -525,29 +549,16 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
         __syncwarp();
     } else {
         // ----------------------------------------------------- epilogue
-        // Thread = document row (TMEM lane), register c = query token c.
-        // The column max over the tile's valid rows is one redux.sync.max
-        // per column whose member mask is exactly those rows, so rows past
-        // the document end never take part; the running maxima are held
-        // warp-uniform (lane 0 always participates when any row is valid).
-        // Group g (warps 2+4g .. 5+4g) takes the documents whose ordinal is
-        // g mod kEpiGroups; both groups read every tile's info.
-        const int qd = warp & 3;  // TMEM lane quadrant this warp may read
-        const int grp = (warp - 2) >> 2;
-        float* gpart = part + grp * 2 * 4 * NT;
-        uint64_t* gpfull = pfull + 2 * grp;
-        uint64_t* gpempty = pempty + 2 * grp;
-        uint32_t doc_ord = 0;  // ordinal of the current document (all groups count all documents)
-        bool mine = false;
-        constexpr int RB = SH ? 1 : NB;  // blocks of warp-uniform maxima (normal mode)
-        float rm[RB][32];
-        float rmd[NB];                    // per-lane maxima (shared mode)
+        // Thread = query row 128 h + 32 qd + lane of half h (TMEM lane
+        // 32 qd + lane).  Its 32-row block 4 h + qd is copy blk / bpc of
+        // block blk % bpc; copy c owns tile columns [c W, c W + W) with
+        // W = 128 / reps.  rmax[h] is the running max of that row over the
+        // document's columns seen so far.
+        const int qd = warp & 3;
+        const int W = 128 / a.reps;
+        float rmax[H];
 #pragma unroll
-        for (int b = 0; b < RB; ++b)
-#pragma unroll
-            for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) rmd[b] = -INFINITY;
+        for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
         int acc = 0;
         uint32_t docs = 0;  // documents finished; buffer = docs & 1, its use count = docs >> 1
         for (int t = 0;; ++t) {
@@ -558,119 +569,90 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
             if (lane == 0) mbar_arrive(&iempty[ii]);
             if (ti.flags & kEnd) break;
             if (ti.flags & kFirst) {
-                mine = (doc_ord % kEpiGroups) == static_cast<uint32_t>(grp);
-                ++doc_ord;
 #pragma unroll
-                for (int b = 0; b < RB; ++b)
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) rm[b][c] = -INFINITY;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) rmd[b] = -INFINITY;
+                for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
             }
-            if (!mine) continue;  // another group's tile
-            // F8: this thread's document row scale, fetched before the
-            // accumulator wait so the load overlaps it.
-            float srow = 1.f;
-            if (F8 && qd * 32 + lane < ti.r) srow = __ldg(a.t_scales + ti.row0 + qd * 32 + lane);
-            const int ab = grp * A + acc % A;
-            if (!warp_wait(&tfull[ab], (acc / A) & 1, abort_flag, a.err)) break;
+            const float* scl = nullptr;
+            const int j = t % kScaleRing;
+            if (F8) {
+                if (!warp_wait(&sfull[j], (t / kScaleRing) & 1, abort_flag, a.err)) break;
+                scl = sc + j * kScalePitch + (ti.row0 & 3);
+            }
+            const int ab = acc % kAcc;
+            if (!warp_wait(&tfull[ab], (acc / kAcc) & 1, abort_flag, a.err)) break;
             tc_fence_after();
-            const int rows_here = ti.r - qd * 32;
-            const int ksteps = NCH * 4;
-            if (rows_here > 0) {
-                const unsigned vmask = rows_here >= 32 ? 0xffffffffu : ((1u << rows_here) - 1u);
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    // sum the partial accumulators that received any K-step
-                    const uint32_t tl = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
-                                        static_cast<uint32_t>(ab * P * NT + b * 32);
-                    float v[32];
-                    tmem_ld32(tl, v);
+            for (int h = 0; h < H; ++h) {
+                const int blk = 4 * h + qd;
+                const int cp = blk / a.bpc;
+                if (cp < a.reps) {
+                    const int c_end = min(cp * W + W, ti.r);
+                    for (int c0 = cp * W; c0 < c_end; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(tbase + (static_cast<uint32_t>(qd * 32) << 16) +
+                                      static_cast<uint32_t>((ab * H + h) * 128 + c0),
+                                  v);
+                        if (F8) {
 #pragma unroll
-                    for (int pp = 1; pp < P; ++pp) {
-                        if (pp < ksteps) {
-                            float w[32];
-                            tmem_ld32(tl + static_cast<uint32_t>(pp * NT), w);
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) v[c] += w[c];
+                            for (int c = 0; c < 32; ++c) v[c] *= scl[c0 + c];
                         }
-                    }
-                    if (F8) {
+                        if (c0 + 32 > ti.r) {
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) v[c] *= srow;
-                    }
-                    if (SH) {
-                        // running max kept per lane: lane c owns column c of block b
-                        if (rows_here < 32 && lane >= rows_here) {
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) v[c] = -INFINITY;
+                            for (int c = 0; c < 32; ++c)
+                                if (c0 + c >= ti.r) v[c] = -INFINITY;
                         }
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            const float m = redux_max(v[c], 0xffffffffu);
-                            if (lane == c) rmd[b] = fmaxf(rmd[b], m);
-                        }
-                    } else if (lane < rows_here) {
+                        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) rm[b][c] = fmaxf(rm[b][c], redux_max(v[c], vmask));
+                            for (int c = 0; c < o; ++c) v[c] = fmaxf(v[c], v[c + o]);
+                        rmax[h] = fmaxf(rmax[h], v[0]);
                     }
-                    __syncwarp();
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[ab]);
+            if (lane == 0) {
+                mbar_arrive(&tempty[ab]);
+                if (F8) mbar_arrive(&sempty[j]);
+            }
             ++acc;
             if (ti.flags & kLast) {
                 const int pb = docs & 1;
                 const uint32_t use = docs >> 1;
-                if (!warp_wait(&gpempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
-                float* pp = gpart + pb * 4 * NT;
-                if (SH) {
+                if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
+                float* pp = part + pb * 4 * H * 32;
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) pp[qd * NT + b * 32 + lane] = rmd[b];
-                } else if (lane == 0) {
-#pragma unroll
-                    for (int b = 0; b < RB; ++b)
-#pragma unroll
-                        for (int c = 0; c < 32; c += 4)
-                            *reinterpret_cast<float4*>(pp + qd * NT + b * 32 + c) =
-                                make_float4(rm[b][c], rm[b][c + 1], rm[b][c + 2], rm[b][c + 3]);
-                }
+                for (int h = 0; h < H; ++h) pp[(4 * h + qd) * 32 + lane] = rmax[h];
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&gpfull[pb]);
+                if (lane == 0) mbar_arrive(&pfull[pb]);
                 if (qd == 0) {
-                    if (!warp_wait(&gpfull[pb], use & 1, abort_flag, a.err)) break;
+                    if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) break;
                     if (SH) {
                         const int64_t fc = static_cast<int64_t>(ti.f) % a.n_cand;
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            const int col = b * 32 + lane;
-                            const float m =
-                                fmaxf(fmaxf(pp[col], pp[NT + col]), fmaxf(pp[2 * NT + col], pp[3 * NT + col]));
+                        for (int b = 0; b < a.bpc; ++b) {
+                            float m = pp[b * 32 + lane];
+                            for (int rp = 1; rp < a.reps; ++rp) m = fmaxf(m, pp[(rp * a.bpc + b) * 32 + lane]);
                             const int qq = ti.q * a.group + b;
                             float sq = 1.f;
-                            if (F8 && lane < a.nq && b < a.group && qq < a.n_queries)
+                            if (F8 && lane < a.nq && qq < a.n_queries)
                                 sq = __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + lane);
                             const float sum = warp_sum(lane < a.nq ? (F8 ? m * sq : m) : 0.f);
-                            if (lane == 0 && b < a.group && qq < a.n_queries)
-                                a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
+                            if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
                         }
                     } else {
                         float sum = 0.f;
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            const int col = b * 32 + lane;
-                            const float m =
-                                fmaxf(fmaxf(pp[col], pp[NT + col]), fmaxf(pp[2 * NT + col], pp[3 * NT + col]));
-                            if (col < a.nq)
-                                sum += F8 ? m * __ldg(a.q_scales + static_cast<int64_t>(ti.q) * a.nq + col) : m;
+                        for (int b = 0; b < a.bpc; ++b) {
+                            float m = pp[b * 32 + lane];
+                            for (int rp = 1; rp < a.reps; ++rp) m = fmaxf(m, pp[(rp * a.bpc + b) * 32 + lane]);
+                            const int tok = b * 32 + lane;
+                            if (tok < a.nq)
+                                sum += F8 ? m * __ldg(a.q_scales + static_cast<int64_t>(ti.q) * a.nq + tok) : m;
                         }
                         sum = warp_sum(sum);
                         if (lane == 0) a.out[ti.f] = sum;
                     }
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&gpempty[pb]);
+                    if (lane == 0) mbar_arrive(&pempty[pb]);
                 }
                 ++docs;
             }
@@ -685,35 +667,36 @@ __global__ void __launch_bounds__(num_threads(NB * 32), CTAS)
     }
 }
 
-}  // namespace dense
-
-namespace dense {
-
 // Plan shared memory, encode the tensor maps and launch dense_tc_kernel.
-// F8 ignores `dtype` (rows are E4M3 codes); a.nchunks must be
-// ceil(d / chunk_elems(F8)).
-template <int NB, bool SH, bool F8>
+// F8 ignores `dtype` (rows are E4M3 codes; t_scales in `a`).  The caller
+// sets a.nchunks = ceil(d / chunk_elems(F8)), and a.bpc / a.qbox: per-query
+// ceil(nq / 32) and 32 bpc, shared mode the group size and 32.
+template <int H, bool SH, bool F8>
 tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
                      const void* doc_tokens, int64_t n_tokens, Args a, cudaStream_t stream) {
-    constexpr int NT = NB * 32;
-    constexpr int A = acc_total(NT);   // all epilogue groups
     constexpr int CE = chunk_elems(F8);
     const CUtensorMapDataType tdt = F8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                   : dtype == TMS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const uint64_t row_bytes = static_cast<uint64_t>(d) * (F8 ? 1 : 2);
+    // With no document rows nothing is ever loaded through the document
+    // maps; describe the query buffer so that they still encode.
+    const void* dbase = n_tokens > 0 ? doc_tokens : queries;
     Maps maps;
     tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
-                                   CE, SH ? 32 : NT);
+                                   CE, static_cast<uint32_t>(a.qbox));
     if (st != TMS_OK) return st;
-    // Shared-memory plan.  Prefer two CTAs per SM (NT <= 64) when each
-    // still gets a ring of at least 4 dimension chunks; within a plan take
-    // the query-slot count (2, else 1) that gives the most stage chunks.
+    // Shared-memory plan.  Prefer two CTAs per SM (H == 1: 256 TMEM columns
+    // each) when each still gets a ring of at least 4 dimension chunks, with
+    // as many copies of the query blocks as fit (fewer copies only narrow
+    // the epilogue's share of each tile); else one CTA per SM.  Within a
+    // plan take the query-slot count (2, else 1) that gives the most stage
+    // chunks.
     const bool can3d = d % CE == 0 && a.nchunks >= 2;
-    auto plan = [&](int per_cta_limit, int cps, int& stages, int& qslots) {
+    auto plan = [&](int per_cta_limit, int cps, int rows_alloc, int& stages, int& qslots) {
         int best = -1;
         for (int qs = 2; qs >= 1; --qs) {
-            const Layout L0 = make_layout(0, cps, qs, a.nchunks, NT, A);
+            const Layout L0 = make_layout(0, cps, qs, a.nchunks, rows_alloc, H, F8);
             const int sts = std::min(kMaxStages, (per_cta_limit - L0.total) / (cps * kChunkBytes + 16));
             if (sts * cps > best) {
                 best = sts * cps;
@@ -723,40 +706,60 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         }
         return best;
     };
-    int stages = 0, qslots = 1, ctas = 1;
+    const int max_reps = SH ? (a.bpc == 2 ? 2 : 1) : (a.bpc == 3 ? 1 : 4 / a.bpc);
     const int limit1 = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
     const int limit2 = dev.smem_per_sm / 2 - dev.smem_reserved - 1024;
-    a.cps = can3d ? 2 : 1;
-    if (NT <= 64 && plan(limit2, a.cps, stages, qslots) >= 4 && stages >= 2) {
-        ctas = 2;
-    } else if (NT <= 64 && can3d && plan(limit2, 1, stages, qslots) >= 4) {
-        ctas = 2;
-        a.cps = 1;
-    } else {
-        a.cps = can3d ? 2 : 1;
-        if (plan(limit1, a.cps, stages, qslots) < 2 || stages < 2) {
-            a.cps = 1;
-            if (plan(limit1, 1, stages, qslots) < 2) return TMS_ERR_UNSUPPORTED;
+    int stages = 0, qslots = 1, ctas = 0, reps = max_reps, cps = can3d ? 2 : 1;
+    if (H == 1) {
+        for (int rp = max_reps; rp >= 1 && ctas == 0; rp /= 2) {
+            const int ra = 32 * a.bpc * rp;
+            for (int c = can3d ? 2 : 1; c >= 1 && ctas == 0; --c) {
+                if (plan(limit2, c, ra, stages, qslots) >= 4 && stages >= 2) {
+                    ctas = 2;
+                    reps = rp;
+                    cps = c;
+                }
+            }
         }
     }
+    for (int rp = max_reps; rp >= 1 && ctas == 0; rp /= 2) {
+        const int ra = 32 * a.bpc * rp;
+        for (int c = can3d ? 2 : 1; c >= 1 && ctas == 0; --c) {
+            if (plan(limit1, c, ra, stages, qslots) >= 2 && stages >= 2) {
+                ctas = 1;
+                reps = rp;
+                cps = c;
+            }
+        }
+    }
+    if (ctas == 0) return TMS_ERR_UNSUPPORTED;
+    a.reps = reps;
+    a.rows_alloc = 32 * a.bpc * reps;
+    a.cps = cps;
     for (int h = 0; h < kBoxKinds; ++h) {
         const uint32_t rows = static_cast<uint32_t>(8 * (h + 1));
-        st = a.cps == 2
-                 ? encode_tmap_rows_chunks(&maps.doc[h], tdt, doc_tokens, a.nchunks, n_tokens, row_bytes, rows, CE)
-                 : encode_tmap_2d(&maps.doc[h], tdt, doc_tokens, d, n_tokens, row_bytes, CE, rows);
+        st = a.cps == 2 ? encode_tmap_rows_chunks(&maps.doc[h], tdt, dbase, a.nchunks, n_tokens, row_bytes, rows, CE)
+                        : encode_tmap_2d(&maps.doc[h], tdt, dbase, d, n_tokens, row_bytes, CE, rows);
         if (st != TMS_OK) return st;
     }
+    if (F8) {
+        st = encode_tmap_1d_f32(&maps.scales, n_tokens > 0 ? static_cast<const void*>(a.t_scales) : queries,
+                                static_cast<uint64_t>(n_tokens), kScaleBox);
+        if (st != TMS_OK) return st;
+    } else {
+        maps.scales = maps.q;  // never used
+    }
     // format code 0 is f16 under kind::f16 and E4M3 under kind::f8f6f4
-    a.idesc = make_idesc(kRows, NT, (!F8 && dtype == TMS_BF16) ? 1u : 0u);
+    a.idesc = make_idesc(128, 0, (!F8 && dtype == TMS_BF16) ? 1u : 0u);
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, a.cps, qslots, a.nchunks, NT, A);
+    const Layout L = make_layout(stages, a.cps, qslots, a.nchunks, a.rows_alloc, H, F8);
     const int smem = L.total + 1024;
-    auto kern = ctas == 2 ? dense_tc_kernel<NB, (NB <= 2 ? 2 : 1), SH, F8> : dense_tc_kernel<NB, 1, SH, F8>;
+    auto kern = ctas == 2 ? dense_tc_kernel<H, (H == 1 ? 2 : 1), SH, F8> : dense_tc_kernel<H, 1, SH, F8>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
-    kern<<<static_cast<unsigned>(grid), num_threads(NT), smem, stream>>>(maps, a);
+    kern<<<static_cast<unsigned>(grid), kThreads, smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
 }
 

@@ -95,7 +95,7 @@ tms_status prepare(const uint8_t* q_codes, const float* q_scales, int n_queries,
         return TMS_ERR_INVALID_ARG;
     if (n_docs > 0 && (!doc_offsets || !doc_lengths || !aligned16(doc_offsets) || !aligned16(doc_lengths)))
         return TMS_ERR_INVALID_ARG;
-    if (n_tokens > 0 && (!doc_codes || !doc_scales || !aligned16(doc_codes) || !aligned4(doc_scales)))
+    if (n_tokens > 0 && (!doc_codes || !doc_scales || !aligned16(doc_codes) || !aligned16(doc_scales)))
         return TMS_ERR_INVALID_ARG;
     tms_status st = current_device(dev);
     if (st != TMS_OK) return st;
@@ -157,12 +157,9 @@ extern "C" tms_status tms_score_fp8(const uint8_t* q_codes, const float* q_scale
     a.cand_offsets = cand_offsets;
     a.n_flat = n_cand;
     a.group = 0;
-    switch ((nq + 31) / 32) {
-        case 1: return dense::launch_tc<1, false, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
-        case 2: return dense::launch_tc<2, false, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
-        case 3: return dense::launch_tc<3, false, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
-        default: return dense::launch_tc<4, false, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
-    }
+    a.bpc = (nq + 31) / 32;
+    a.qbox = 32 * a.bpc;
+    return dense::launch_tc<1, false, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
 }
 
 extern "C" tms_status tms_score_fp8_shared(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq,
@@ -184,11 +181,12 @@ extern "C" tms_status tms_score_fp8_shared(const uint8_t* q_codes, const float* 
         if (n_groups * n_cand >= (int64_t(1) << 31)) return TMS_ERR_UNSUPPORTED;
         a.n_flat = n_groups * n_cand;
         a.group = group;
-        switch (group) {
-            case 2: st = dense::launch_tc<2, true, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream); break;
-            case 4: st = dense::launch_tc<4, true, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream); break;
-            default: st = dense::launch_tc<8, true, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream); break;
-        }
+        a.bpc = group;
+        a.qbox = 32;
+        st = group == 8 ? dense::launch_tc<2, true, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
+                                                         stream)
+                        : dense::launch_tc<1, true, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
+                                                         stream);
         if (st != TMS_ERR_UNSUPPORTED) return st;
     }
     return TMS_ERR_UNSUPPORTED;
