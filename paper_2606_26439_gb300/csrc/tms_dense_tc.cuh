@@ -23,7 +23,7 @@
 //     height (8, 16, ..., 128) covers the tile's rows with at most 7 rows of
 //     over-fetch.  Each token is read from HBM once (Theorem 1 with
 //     BQ = Nq, or the whole group of queries in the shared schedule).  F8:
-//     the tile's row scales follow through a small ring of 1-D TMA loads.
+//     the tile's row scales follow through a small ring of TMA loads.
 //   * MMA warp: one thread issues tcgen05.mma (M = 128 query rows,
 //     N = the tile's rows rounded up to 16, K = 32 bytes: 16 fp16/bf16
 //     elements with kind::f16, 32 E4M3 elements with kind::f8f6f4) over
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, CTAS)
                         }
                         if (lane == 0) {
                             mbar_arrive_expect_tx(&sfull[j], static_cast<uint32_t>(kScaleBox * 4));
-                            tma_load_1d(sc + j * kScalePitch, &maps.scales, y0 & ~3, &sfull[j], pol_stream);
+                            tma_load_2d(sc + j * kScalePitch, &maps.scales, y0 & ~3, 0, &sfull[j], pol_stream);
                         }
                     }
                     ++t;

@@ -36,8 +36,8 @@ tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const voi
 tms_status encode_tmap_rows_chunks(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int nchunks,
                                    uint64_t rows, uint64_t row_bytes, uint32_t box_rows, uint32_t chunk_elems);
 
-// Encode a 1-D tensor map over `n` 4-byte elements, box of box_elems, no
-// swizzle, zero fill outside.
+// Encode a tensor map over `n` consecutive fp32 elements (one row), box of
+// box_elems x 1, no swizzle, zero fill outside; load with tma_load_2d(x, 0).
 tms_status encode_tmap_1d_f32(CUtensorMap* map, const void* base, uint64_t n, uint32_t box_elems);
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
