@@ -75,10 +75,10 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
  * Limits: 1 <= nq <= 128; 8 <= d <= 1024 with d % 8 == 0 (16-byte rows);
  * 1 <= n_queries <= 4096; n_tokens < 2^31; queries, doc_tokens and every
  * index array 16-byte aligned.  For fp16/bf16 the whole query tile stays
- * in one CTA's shared memory next to at least two 16 KB stages: with nq
- * rounded up to a multiple of 32 and d to a multiple of 64, their product
- * must stay below 98,304 (nq 128 at d >= 768 and nq 96 at d 1024 return
- * TMS_ERR_UNSUPPORTED).  fp16/bf16 run on the tensor cores
+ * in one CTA's shared memory next to at least two 32 KB stages: with nq
+ * rounded up to a multiple of 32 and d to a multiple of 64, nq * d * 2
+ * bytes must not exceed 162,264 (nq > 96 at d > 576 and nq > 64 at d > 832
+ * return TMS_ERR_UNSUPPORTED).  fp16/bf16 run on the tensor cores
  * (tcgen05, fp32 accumulation in tensor memory); fp32 runs on an exact
  * fp32 path.  A candidate with a bad id or row range scores NaN and sets
  * TMS_DEVERR_BAD_ID / TMS_DEVERR_BAD_RANGE.
@@ -147,10 +147,9 @@ tms_status tms_quantize_e4m3(const void *x, tms_dtype dtype, int64_t rows, int d
  *   other arguments and the error behaviour as for tms_score_dense.
  *
  * Limits: 1 <= nq <= 128; 16 <= d <= 1024 with d % 16 == 0; codes,
- * doc_scales and index arrays 16-byte aligned, q_scales 4-byte aligned; the query tile
- * (nq rounded up to 32) x (d rounded up to 128) bytes must fit one CTA's
- * shared memory next to two 16 KB stages (as for tms_score_dense, in
- * bytes), else TMS_ERR_UNSUPPORTED.  Scales must be finite and >= 0.
+ * doc_scales and index arrays 16-byte aligned, q_scales 4-byte aligned
+ * (every supported nq and d fits shared memory).  Scales must be finite
+ * and >= 0.
  */
 tms_status tms_score_fp8(const uint8_t *q_codes, const float *q_scales, int n_queries, int nq, int d,
                          const uint8_t *doc_codes, const float *doc_scales, int64_t n_tokens,

@@ -67,19 +67,6 @@ bool load_encoder() {
 }
 }  // namespace
 
-tms_status encode_tmap_rows_chunks(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int nchunks,
-                                   uint64_t rows, uint64_t row_bytes, uint32_t box_rows, uint32_t chunk_elems) {
-    if (!load_encoder()) return TMS_ERR_CUDA;
-    const cuuint64_t dims[3] = {chunk_elems, rows > 0 ? rows : 1, static_cast<cuuint64_t>(nchunks)};
-    const cuuint64_t strides[2] = {row_bytes, 128};
-    const cuuint32_t box[3] = {chunk_elems, box_rows, 2};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = g_encode(map, dtype, 3, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? TMS_OK : TMS_ERR_INVALID_ARG;
-}
-
 tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
                           uint64_t rows, uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows) {
     if (!load_encoder()) return TMS_ERR_CUDA;

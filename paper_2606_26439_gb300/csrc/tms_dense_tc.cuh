@@ -9,35 +9,41 @@
 // memory lanes, one per epilogue thread) and document rows along N
 // (tensor-memory columns).  The max over a document's tokens (Eq. 1's
 // inner max) is then a running max inside each thread's registers -- no
-// cross-lane reduction per tile.  M is always 128: the query tile's 32-row
-// blocks (token blocks of one query, or the queries of a shared group) are
-// replicated down the 128 rows when they are fewer, and each copy scores
-// its own slice of the tile's columns, so all four epilogue warps work on
-// every tile.
+// cross-lane reduction.  M is always 128: the query tile's 32-row blocks
+// (token blocks of one query, or the queries of a shared group) are
+// replicated down the 128 rows when they are fewer.
 //
-//   * Producer warp: reads candidate metadata (id -> offset, length), and
-//     streams each document's token rows from HBM into a ring of shared-
-//     memory stages with TMA box loads (128-byte swizzle).  A stage holds
-//     one or two 128-byte-wide dimension chunks (64 fp16/bf16 or 128 E4M3
-//     elements) of up to 128 rows of ONE document, loaded as one box whose
-//     height (8, 16, ..., 128) covers the tile's rows with at most 7 rows of
-//     over-fetch.  Each token is read from HBM once (Theorem 1 with
-//     BQ = Nq, or the whole group of queries in the shared schedule).  F8:
-//     the tile's row scales follow through a small ring of TMA loads.
-//   * MMA warp: one thread issues tcgen05.mma (M = 128 query rows,
-//     N = the tile's rows rounded up to 16, K = 32 bytes: 16 fp16/bf16
-//     elements with kind::f16, 32 E4M3 elements with kind::f8f6f4) over
-//     every dimension chunk of a tile, accumulating the partial dot
-//     products in tensor memory before any max is taken -- the paper's
-//     dimension tiling (Section 3), with the K loop running through TMEM.
-//   * Four epilogue warps: thread = query row (TMEM lane).  Each loads its
-//     slice of the tile's columns with tcgen05.ld, multiplies column j by
-//     document row j's scale (F8), drops columns past the tile's rows, and
-//     folds the rest into its running max.  At a document's end the copies'
-//     maxima meet in shared memory and one warp sums them over the query
-//     tokens (times each token's scale, F8) in a fixed order and writes the
-//     score once.  The Nq x Nd similarity matrix never reaches HBM and no
-//     atomics or memset are needed.
+// Super-tiles: consecutive document tiles (up to 128 rows each, padded to
+// 8) are packed side by side into one super-tile of up to 256 rows (128
+// with two query halves), and one run of MMAs (N = the packed rows rounded
+// up to 16) scores them all.  The per-tile costs of the pipeline --
+// barrier round trips, commits, MMA issue -- are paid once per super-tile,
+// typically two to three documents.
+//
+//   * Producer warp: reads candidate metadata (id -> offset, length),
+//     packs tiles into super-tiles, and streams them from HBM into a ring
+//     of shared-memory chunk stages (256 rows x 128 bytes: 64 fp16/bf16 or
+//     128 E4M3 elements per row) with one TMA box per tile and chunk, lanes
+//     issuing the tiles of a super-tile in parallel (128-byte swizzle).
+//     Each token is read from HBM once (Theorem 1 with BQ = Nq, or the
+//     whole group of queries in the shared schedule).  F8: every tile's
+//     row scales follow through a ring of small TMA loads.
+//   * MMA warp: one thread issues tcgen05.mma (M = 128 query rows, K = 32
+//     bytes: 16 fp16/bf16 elements with kind::f16, 32 E4M3 elements with
+//     kind::f8f6f4) over every dimension chunk of a super-tile,
+//     accumulating the partial dot products in tensor memory before any
+//     max is taken -- the paper's dimension tiling (Section 3), with the K
+//     loop running through TMEM.
+//   * Four epilogue warps: thread = query row (TMEM lane).  Documents are
+//     dealt round-robin to the copies of the query tile; the warps of a
+//     copy load their document's columns with tcgen05.ld, multiply column
+//     j by document row j's scale (F8), drop columns of other documents,
+//     and fold the rest into a running max.  At the document's end each
+//     warp sums its 32 query tokens (times their scales, F8); with one
+//     token block per copy that sum is the score, else the copy's warps
+//     add their sums in block order.  Each score is written once; the
+//     Nq x Nd similarity matrix never reaches HBM and no atomics or memset
+//     are needed.
 //
 // Every wait is bounded (see tms_common.cuh); a timeout sets
 // TMS_DEVERR_TIMEOUT and the CTA drains its in-flight copies and MMAs,
@@ -53,29 +59,40 @@ namespace tms {
 
 namespace dense {
 
-constexpr int kRows = 128;                    // document rows per tile (MMA N at most)
-constexpr int kChunkBytes = kRows * 128;      // 16 KB: 128 rows x one 128-byte dimension chunk
+constexpr int kRows = 128;                    // document rows per tile
+__host__ __device__ constexpr int st_rows(int H) { return 256 / H; }  // rows per super-tile
 // Elements per 128-byte dimension chunk (one 128-byte swizzle row).
 __host__ __device__ constexpr int chunk_elems(bool f8) { return f8 ? 128 : 64; }
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
-constexpr int kInfoRing = 16;
-constexpr int kScaleRing = 8;                 // F8: tiles whose row scales are in flight or held
+constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per producer lane)
+constexpr int kSegRing = 64;                  // tile records in flight to the epilogue
+constexpr int kStRing = 8;                    // super-tile records in flight to the MMA thread
+constexpr int kScaleRing = 32;                // F8: tiles whose row scales are in flight or held
 constexpr int kScaleBox = 136;                // floats per scale load: 128 rows + up to 3 of 16-byte alignment
 constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a multiple of 128 B)
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, four epilogue warps
-constexpr int kAcc = 2;                       // accumulator buffers (each H x 128 TMEM columns)
+constexpr int kAcc = 2;                       // accumulator buffers (each H x st_rows(H) TMEM columns)
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
 
-enum : int { kFirst = 1, kLast = 2, kEnd = 4 };
+enum : int { kFirst = 1, kLast = 2, kEnd = 4, kStFirst = 8, kStLast = 16 };
 
-struct TileInfo {
+// One document tile inside a super-tile (producer -> epilogue).
+struct SegInfo {
     int f;      // flat candidate index
-    int r;      // valid rows in this tile (1..128)
+    int r;      // valid rows (1..128)
     int q;      // query index (shared mode: group index)
-    int flags;  // kFirst / kLast / kEnd
+    int flags;  // kFirst / kLast of the document, kStFirst / kStLast of the super-tile, kEnd
     int row0;   // token row of the tile's first row
+    int col;    // first column (row of the super-tile), a multiple of 8
+};
+
+// One super-tile (producer -> MMA thread).
+struct StInfo {
+    int q;      // query (group) whose tile it is scored against
+    int n;      // MMA N: packed rows rounded up to 16
+    int flags;  // kEnd
     int pad;
 };
 
@@ -95,38 +112,36 @@ struct Args {
     int group;         // shared mode: queries per group; 0 otherwise
     int n_queries;
     int nq;
-    int nchunks;   // ceil(d / chunk_elems)
-    int cps;       // dimension chunks per stage: 2 with the 3-D tensor view (d % chunk_elems == 0), else 1
-    int stages;
+    int nchunks;     // ceil(d / chunk_elems)
+    int stages;      // chunk stages in the ring
     int qslots;
     int bpc;         // 32-row query blocks per copy: ceil(nq / 32) token blocks, or the group's queries
-    int reps;        // copies stacked in M; copy c scores tile columns [c * 128 / reps, (c + 1) * 128 / reps)
+    int reps;        // copies of the blocks stacked in M; documents are dealt round-robin to the copies
     int rows_alloc;  // query rows held per dimension chunk: 32 * bpc * reps
     int qbox;        // rows of one query TMA box: 32 * bpc (per-query), 32 (shared)
-    uint32_t idesc;  // instruction descriptor, N field left 0 (set per tile)
+    uint32_t idesc;  // instruction descriptor, N field left 0 (set per super-tile)
 };
 
 struct Layout {
-    int q_off, stage_off, part_off, sc_off, info_off, bar_off, misc_off, total;
+    int q_off, stage_off, part_off, sc_off, seg_off, sti_off, bar_off, misc_off, total;
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
 // The query region comes first: the MMA reads 128 (x H) rows from each
 // query chunk, and rows past rows_alloc fall on the following chunk or on
 // the stage ring -- always inside the allocation, and they only feed
-// accumulator rows that nothing reads.  1 KB after the stage ring likewise
-// absorbs the document operand's read of up to 8 rows past a chunk (N is
-// the tile's rows rounded up to 16, the box up to 8).
-__host__ __device__ inline Layout make_layout(int stages, int cps, int qslots, int nchunks, int rows_alloc, int H,
-                                              bool f8) {
+// accumulator rows that nothing reads.  A stage holds the full st_rows(H)
+// rows, so the document operand (N <= st_rows) never reads past it.
+__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int H, bool f8) {
     Layout L;
     L.q_off = 0;
     L.stage_off = (qslots * nchunks * rows_alloc * 128 + 1023) & ~1023;
-    L.part_off = L.stage_off + stages * cps * kChunkBytes + 1024;
-    L.sc_off = L.part_off + 2 * 4 * H * 32 * 4;
-    L.info_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
-    L.bar_off = L.info_off + kInfoRing * static_cast<int>(sizeof(TileInfo));
-    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * kInfoRing + 4 + 2 * kScaleRing + 1;
+    L.part_off = L.stage_off + stages * st_rows(H) * 128;
+    L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
+    L.seg_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
+    L.sti_off = L.seg_off + kSegRing * static_cast<int>(sizeof(SegInfo));
+    L.bar_off = L.sti_off + kStRing * static_cast<int>(sizeof(StInfo));
+    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * kSegRing + 2 * kStRing + 8 + 2 * kScaleRing + 1;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
@@ -174,6 +189,14 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
+// Each lane waits on its own barrier (none when `bar` is null); the warp
+// agrees on the outcome.
+__device__ __forceinline__ bool lanes_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                           unsigned int* err) {
+    const bool ok = bar == nullptr || mbar_wait(bar, parity, abort_flag, err);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
 // Drain wait: bounded, but ignores the abort flag (used to let in-flight
 // asynchronous work land before the CTA exits).
 __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
@@ -184,12 +207,9 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Tensor maps of one launch.  doc[h] covers document rows with a box of
-// 8 (h + 1) rows, so a tile of r rows is always ONE box (at most 7 rows of
-// over-fetch).  With cps == 2 the document maps are the 3-D view
-// {128 bytes of elements, rows, chunk} of the [n_tokens][d] array (chunk
-// stride 128 bytes): one box brings two chunks of r rows, landing as
-// [chunk][row][128 B] -- already the 128-byte-swizzle K-major layout.
-// scales (F8): the [n_tokens] fp32 row scales, boxes of kScaleBox.
+// 8 (h + 1) rows x one 128-byte chunk, so a tile of r rows is always ONE
+// box per chunk (at most 7 rows of over-fetch).  scales (F8): the
+// [n_tokens] fp32 row scales, boxes of kScaleBox.
 struct Maps {
     CUtensorMap q;
     CUtensorMap doc[kBoxKinds];
@@ -203,28 +223,27 @@ struct Maps {
 // writes one score per query of the group.
 // F8: rows are E4M3 codes; similarities are scaled by the document row's
 // scale before the max and by the query token's scale before the sum.
-template <int H, int CTAS, bool SH, bool F8>
-__global__ void __launch_bounds__(kThreads, CTAS)
-    dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
+template <int H, bool SH, bool F8>
+__global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
     constexpr int CE = chunk_elems(F8);
-    constexpr uint32_t TCOLS = kAcc * H * 128;
+    constexpr int STR = st_rows(H);
+    constexpr int STAGE_BYTES = STR * 128;
+    constexpr uint32_t TCOLS = kAcc * H * STR;  // 512
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = a.stages;
     const int QS = a.qslots;
     const int NCH = a.nchunks;
-    const int CPS = a.cps;
-    const int stage_bytes = CPS * kChunkBytes;
-    const int stages_per_tile = (NCH + CPS - 1) / CPS;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    const Layout L = make_layout(S, CPS, QS, NCH, a.rows_alloc, H, F8);
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, H, F8);
 
     uint8_t* q_base = smem + L.q_off;
     uint8_t* stage_base = smem + L.stage_off;
-    float* part = reinterpret_cast<float*>(smem + L.part_off);  // [2][4 H][32]
+    float* part = reinterpret_cast<float*>(smem + L.part_off);  // [copy][parity][block]
     float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // [kScaleRing][kScalePitch]
-    TileInfo* info = reinterpret_cast<TileInfo*>(smem + L.info_off);
+    SegInfo* seg = reinterpret_cast<SegInfo*>(smem + L.seg_off);
+    StInfo* sti = reinterpret_cast<StInfo*>(smem + L.sti_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;
     uint64_t* empty = full + S;
@@ -232,18 +251,22 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     uint64_t* tempty = tfull + kAcc;
     uint64_t* qfull = tempty + kAcc;
     uint64_t* qempty = qfull + QS;
-    uint64_t* ifull = qempty + QS;
-    uint64_t* iempty = ifull + kInfoRing;
-    uint64_t* pfull = iempty + kInfoRing;  // [2]
-    uint64_t* pempty = pfull + 2;          // [2]
-    uint64_t* sfull = pempty + 2;          // [kScaleRing]
-    uint64_t* sempty = sfull + kScaleRing; // [kScaleRing]
+    uint64_t* gfull = qempty + QS;          // [kSegRing]
+    uint64_t* gempty = gfull + kSegRing;    // [kSegRing]
+    uint64_t* xfull = gempty + kSegRing;    // [kStRing]
+    uint64_t* xempty = xfull + kStRing;     // [kStRing]
+    uint64_t* pfull = xempty + kStRing;     // [copy][parity]
+    uint64_t* pempty = pfull + 4;           // [copy][parity]
+    uint64_t* sfull = pempty + 4;           // [kScaleRing]
+    uint64_t* sempty = sfull + kScaleRing;  // [kScaleRing]
     uint64_t* mdone = sempty + kScaleRing;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    // epilogue warps that read one tile (the warps of its copy)
+    const int owners = H == 2 ? 4 : a.bpc;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
@@ -258,17 +281,21 @@ __global__ void __launch_bounds__(kThreads, CTAS)
             mbar_init(&qfull[i], 1);
             mbar_init(&qempty[i], 1);
         }
-        for (int i = 0; i < kInfoRing; ++i) {
-            mbar_init(&ifull[i], 1);
-            mbar_init(&iempty[i], 1 + kEpiWarps);
+        for (int i = 0; i < kSegRing; ++i) {
+            mbar_init(&gfull[i], 1);
+            mbar_init(&gempty[i], kEpiWarps);
         }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&pfull[i], kEpiWarps);
+        for (int i = 0; i < kStRing; ++i) {
+            mbar_init(&xfull[i], 1);
+            mbar_init(&xempty[i], 1);
+        }
+        for (int i = 0; i < 4; ++i) {
+            mbar_init(&pfull[i], a.bpc);
             mbar_init(&pempty[i], 1);
         }
         for (int i = 0; i < kScaleRing; ++i) {
             mbar_init(&sfull[i], 1);
-            mbar_init(&sempty[i], kEpiWarps);
+            mbar_init(&sempty[i], owners);
         }
         mbar_init(mdone, 1);
         *abort_flag = 0;
@@ -295,11 +322,104 @@ __global__ void __launch_bounds__(kThreads, CTAS)
         int s = 0;
         uint32_t ph = 0;
         int64_t issued = 0;
-        int t = 0;
+        int tseg = 0;  // tile records published
+        int tst = 0;   // super-tiles published
         int qi = 0, cur_q = -1;
         int q = 0;
         int64_t q_end = 0;
         bool aborted = false;
+        // The open super-tile: its tile i lives in lane i's registers.
+        int nseg = 0, rows_used = 0, st_q = 0;
+        int my_f = 0, my_r = 0, my_flags = 0, my_row0 = 0, my_col = 0;
+
+        // Publish the open super-tile: tile records, F8 scale loads, the
+        // MMA record, the query tile if it changed, then every chunk.
+        auto close_st = [&]() -> bool {
+            const bool has = lane < nseg;
+            const int gs = (tseg + lane) % kSegRing;
+            if (!lanes_wait(has ? &gempty[gs] : nullptr, (((tseg + lane) / kSegRing) & 1) ^ 1, abort_flag, a.err))
+                return false;
+            if (has) {
+                SegInfo si;
+                si.f = my_f;
+                si.r = my_r;
+                si.q = st_q;
+                si.flags = my_flags | (lane == 0 ? kStFirst : 0) | (lane == nseg - 1 ? kStLast : 0);
+                si.row0 = my_row0;
+                si.col = my_col;
+                seg[gs] = si;
+                mbar_arrive(&gfull[gs]);
+            }
+            if (F8) {
+                // the tile's row scales, from the 16-byte boundary at or below its first row
+                const int ss = (tseg + lane) % kScaleRing;
+                if (!lanes_wait(has ? &sempty[ss] : nullptr, (((tseg + lane) / kScaleRing) & 1) ^ 1, abort_flag,
+                                a.err))
+                    return false;
+                if (has) {
+                    mbar_arrive_expect_tx(&sfull[ss], static_cast<uint32_t>(kScaleBox * 4));
+                    tma_load_2d(sc + ss * kScalePitch, &maps.scales, my_row0 & ~3, 0, &sfull[ss], pol_stream);
+                }
+            }
+            tseg += nseg;
+            const int xs = tst % kStRing;
+            if (!warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err)) return false;
+            if (lane == 0) {
+                StInfo x;
+                x.q = st_q;
+                x.n = (rows_used + 15) & ~15;
+                x.flags = 0;
+                x.pad = 0;
+                sti[xs] = x;
+                mbar_arrive(&xfull[xs]);
+            }
+            ++tst;
+            // A new query's rows go to the next query slot.  The super-tile
+            // record is published first: the MMA thread releases the old
+            // slot only once it sees the new query.
+            if (st_q != cur_q) {
+                const int slot = qi % QS;
+                if (!warp_wait(&qempty[slot], ((qi / QS) & 1) ^ 1, abort_flag, a.err)) return false;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(qslot_bytes));
+                    uint8_t* qdst = q_base + slot * qslot_bytes;
+                    for (int kc = 0; kc < NCH; ++kc) {
+                        uint8_t* cdst = qdst + kc * a.rows_alloc * 128;
+                        for (int rp = 0; rp < a.reps; ++rp) {
+                            if (SH) {  // one 32-row box per query of the group
+                                for (int g = 0; g < a.bpc; ++g)
+                                    tma_load_2d(cdst + (rp * a.bpc + g) * 32 * 128, &maps.q, kc * CE,
+                                                (st_q * a.group + g) * a.nq, &qfull[slot], pol_keep);
+                            } else {
+                                tma_load_2d(cdst + rp * a.qbox * 128, &maps.q, kc * CE, st_q * a.nq, &qfull[slot],
+                                            pol_keep);
+                            }
+                        }
+                    }
+                }
+                ++qi;
+                cur_q = st_q;
+            }
+            const int n8 = (my_r + 7) & ~7;
+            const CUtensorMap* dmap = &maps.doc[has ? (n8 >> 3) - 1 : 0];
+            for (int kc = 0; kc < NCH; ++kc) {
+                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) return false;
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(rows_used * 128));
+                __syncwarp();
+                if (has)
+                    tma_load_2d(stage_base + s * STAGE_BYTES + my_col * 128, dmap, kc * CE, my_row0, &full[s],
+                                pol_stream);
+                ++issued;
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            nseg = 0;
+            rows_used = 0;
+            return true;
+        };
+
         if (!SH) {
             const int64_t co_last = __ldg(a.cand_offsets + a.n_queries);
             if (co_last != a.n_cand && blockIdx.x == 0 && lane == 0) atomicOr(a.err, TMS_DEVERR_BAD_CSR);
@@ -342,87 +462,23 @@ __global__ void __launch_bounds__(kThreads, CTAS)
             } else {
                 for (int r0 = 0; r0 < len; r0 += kRows) {
                     const int r = min(kRows, len - r0);
-                    const int y0 = static_cast<int>(off) + r0;
-                    const int ii = t % kInfoRing;
-                    if (!warp_wait(&iempty[ii], ((t / kInfoRing) & 1) ^ 1, abort_flag, a.err)) {
-                        aborted = true;
-                        break;
-                    }
-                    if (lane == 0) {
-                        TileInfo ti;
-                        ti.f = static_cast<int>(f);
-                        ti.r = r;
-                        ti.q = q;
-                        ti.flags = (r0 == 0 ? kFirst : 0) | (r0 + kRows >= len ? kLast : 0);
-                        ti.row0 = y0;
-                        ti.pad = 0;
-                        info[ii] = ti;
-                        mbar_arrive(&ifull[ii]);
-                    }
-                    if (F8) {
-                        // the tile's row scales, from the 16-byte boundary at or below its first row
-                        const int j = t % kScaleRing;
-                        if (!warp_wait(&sempty[j], ((t / kScaleRing) & 1) ^ 1, abort_flag, a.err)) {
-                            aborted = true;
-                            break;
-                        }
-                        if (lane == 0) {
-                            mbar_arrive_expect_tx(&sfull[j], static_cast<uint32_t>(kScaleBox * 4));
-                            tma_load_2d(sc + j * kScalePitch, &maps.scales, y0 & ~3, 0, &sfull[j], pol_stream);
-                        }
-                    }
-                    ++t;
-                    // A new query's rows go to the next query slot.  The
-                    // tile info is published first: the MMA warp releases
-                    // the old slot only once it sees the new query.
-                    if (q != cur_q) {
-                        const int slot = qi % QS;
-                        if (!warp_wait(&qempty[slot], ((qi / QS) & 1) ^ 1, abort_flag, a.err)) {
-                            aborted = true;
-                            break;
-                        }
-                        if (lane == 0) {
-                            mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(qslot_bytes));
-                            uint8_t* qdst = q_base + slot * qslot_bytes;
-                            for (int kc = 0; kc < NCH; ++kc) {
-                                uint8_t* cdst = qdst + kc * a.rows_alloc * 128;
-                                for (int rp = 0; rp < a.reps; ++rp) {
-                                    if (SH) {  // one 32-row box per query of the group
-                                        for (int g = 0; g < a.bpc; ++g)
-                                            tma_load_2d(cdst + (rp * a.bpc + g) * 32 * 128, &maps.q, kc * CE,
-                                                        (q * a.group + g) * a.nq, &qfull[slot], pol_keep);
-                                    } else {
-                                        tma_load_2d(cdst + rp * a.qbox * 128, &maps.q, kc * CE, q * a.nq,
-                                                    &qfull[slot], pol_keep);
-                                    }
-                                }
-                            }
-                        }
-                        ++qi;
-                        cur_q = q;
-                    }
                     const int n8 = (r + 7) & ~7;
-                    const CUtensorMap* dmap = &maps.doc[(n8 >> 3) - 1];
-                    for (int st = 0; st < stages_per_tile; ++st) {
-                        if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == kMaxSeg)) {
+                        if (!close_st()) {
                             aborted = true;
                             break;
                         }
-                        if (lane == 0) {
-                            uint8_t* dst = stage_base + s * stage_bytes;
-                            mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(n8 * 128 * CPS));
-                            if (CPS == 2)
-                                tma_load_3d(dst, dmap, 0, y0, 2 * st, &full[s], pol_stream);
-                            else
-                                tma_load_2d(dst, dmap, st * CE, y0, &full[s], pol_stream);
-                        }
-                        ++issued;
-                        if (++s == S) {
-                            s = 0;
-                            ph ^= 1;
-                        }
                     }
-                    if (aborted) break;
+                    if (nseg == 0) st_q = q;
+                    if (lane == nseg) {
+                        my_f = static_cast<int>(f);
+                        my_r = r;
+                        my_flags = (r0 == 0 ? kFirst : 0) | (r0 + kRows >= len ? kLast : 0);
+                        my_row0 = static_cast<int>(off) + r0;
+                        my_col = rows_used;
+                    }
+                    rows_used += n8;
+                    ++nseg;
                 }
                 if (aborted) break;
             }
@@ -432,20 +488,29 @@ __global__ void __launch_bounds__(kThreads, CTAS)
                 id_next2 = load_id(a, k + 65 + lane);
             }
         }
+        if (!aborted && nseg > 0 && !close_st()) aborted = true;
         if (!aborted) {
-            const int ii = t % kInfoRing;
-            if (warp_wait(&iempty[ii], ((t / kInfoRing) & 1) ^ 1, abort_flag, a.err)) {
-                if (lane == 0) {
-                    TileInfo ti;
-                    ti.f = 0;
-                    ti.r = 0;
-                    ti.q = 0;
-                    ti.flags = kEnd;
-                    ti.row0 = 0;
-                    ti.pad = 0;
-                    info[ii] = ti;
-                    mbar_arrive(&ifull[ii]);
-                }
+            const int gs = tseg % kSegRing;
+            if (warp_wait(&gempty[gs], ((tseg / kSegRing) & 1) ^ 1, abort_flag, a.err) && lane == 0) {
+                SegInfo si;
+                si.f = 0;
+                si.r = 0;
+                si.q = 0;
+                si.flags = kEnd;
+                si.row0 = 0;
+                si.col = 0;
+                seg[gs] = si;
+                mbar_arrive(&gfull[gs]);
+            }
+            const int xs = tst % kStRing;
+            if (warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err) && lane == 0) {
+                StInfo x;
+                x.q = 0;
+                x.n = 0;
+                x.flags = kEnd;
+                x.pad = 0;
+                sti[xs] = x;
+                mbar_arrive(&xfull[xs]);
             }
         }
         // Let every copy still in flight land before the CTA can exit.
@@ -461,8 +526,9 @@ __global__ void __launch_bounds__(kThreads, CTAS)
                 drain_wait(&full[ss], pp);
             }
             if (F8) {
-                const int ns = t < kScaleRing ? t : kScaleRing;
-                for (int i = 1; i <= ns; ++i) drain_wait(&sfull[(t - i) % kScaleRing], ((t - i) / kScaleRing) & 1);
+                const int ns = tseg < kScaleRing ? tseg : kScaleRing;
+                for (int i = 1; i <= ns; ++i)
+                    drain_wait(&sfull[(tseg - i) % kScaleRing], ((tseg - i) / kScaleRing) & 1);
             }
         }
         __syncwarp();
@@ -475,58 +541,47 @@ __global__ void __launch_bounds__(kThreads, CTAS)
             int s = 0;
             uint32_t ph = 0;
             int qi = 0, cur_q = -1, qslot = 0;
-            int k = 0;  // tiles issued
             bool any = false;
             for (int t = 0;; ++t) {
-                const int ii = t % kInfoRing;
-                if (!mbar_wait(&ifull[ii], (t / kInfoRing) & 1, abort_flag, a.err)) break;
-                const TileInfo ti = info[ii];
-                mbar_arrive(&iempty[ii]);
-                if (ti.flags & kEnd) break;
-                if (ti.q != cur_q) {
+                const int xs = t % kStRing;
+                if (!mbar_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+                const StInfo x = sti[xs];
+                mbar_arrive(&xempty[xs]);
+                if (x.flags & kEnd) break;
+                if (x.q != cur_q) {
                     if (cur_q >= 0) mma_commit(&qempty[qslot]);
                     qslot = qi % QS;
                     if (!mbar_wait(&qfull[qslot], (qi / QS) & 1, abort_flag, a.err)) break;
                     ++qi;
-                    cur_q = ti.q;
+                    cur_q = x.q;
                 }
-                const int ab = k % kAcc;
-                if (!mbar_wait(&tempty[ab], ((k / kAcc) & 1) ^ 1, abort_flag, a.err)) break;
+                const int ab = t % kAcc;
+                if (!mbar_wait(&tempty[ab], ((t / kAcc) & 1) ^ 1, abort_flag, a.err)) break;
                 tc_fence_after();
                 bool ok = true;
-                const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * H * 128);
+                const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * H * STR);
                 const uint64_t q_desc = desc_sw128(smem_u32(q_base + qslot * qslot_bytes));
-                const int n8 = (ti.r + 7) & ~7;
-                const int n16 = (ti.r + 15) & ~15;
-                const uint32_t idesc = a.idesc | (static_cast<uint32_t>(n16 >> 3) << 17);
-                for (int st = 0; st < stages_per_tile; ++st) {
+                const uint32_t idesc = a.idesc | (static_cast<uint32_t>(x.n >> 3) << 17);
+                for (int kc = 0; kc < NCH; ++kc) {
                     if (!mbar_wait(&full[s], ph, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    // chunk c of the stage starts c * n8 rows in; the MMA
-                    // reads n16 rows from there and the columns past the
-                    // tile's r rows are dropped by the epilogue.
-                    const uint64_t s_desc = desc_sw128(smem_u32(stage_base + s * stage_bytes));
-                    for (int c = 0; c < CPS; ++c) {
-                        const int kc = st * CPS + c;
-                        if (kc >= NCH) break;
-                        const uint64_t b_desc = s_desc + static_cast<uint64_t>((c * n8 * 128) >> 4);
+                    const uint64_t b_desc = desc_sw128(smem_u32(stage_base + s * STAGE_BYTES));
 #pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            const uint64_t a_desc =
-                                q_desc + static_cast<uint64_t>(((kc * a.rows_alloc + h * 128) * 128) >> 4);
+                    for (int h = 0; h < H; ++h) {
+                        const uint64_t a_desc =
+                            q_desc + static_cast<uint64_t>(((kc * a.rows_alloc + h * 128) * 128) >> 4);
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint32_t accumulate = (kc > 0 || kk > 0) ? 1u : 0u;
-                                if (F8)
-                                    mma_f8(d_tmem + static_cast<uint32_t>(h * 128), a_desc + 2 * kk, b_desc + 2 * kk,
-                                           idesc, accumulate);
-                                else
-                                    mma_f16(d_tmem + static_cast<uint32_t>(h * 128), a_desc + 2 * kk,
-                                            b_desc + 2 * kk, idesc, accumulate);
-                            }
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t accumulate = (kc > 0 || kk > 0) ? 1u : 0u;
+                            if (F8)
+                                mma_f8(d_tmem + static_cast<uint32_t>(h * STR), a_desc + 2 * kk, b_desc + 2 * kk, idesc,
+                                       accumulate);
+                            else
+                                mma_f16(d_tmem + static_cast<uint32_t>(h * STR), a_desc + 2 * kk, b_desc + 2 * kk,
+                                        idesc, accumulate);
                         }
                     }
                     mma_commit(&empty[s]);
@@ -538,7 +593,6 @@ __global__ void __launch_bounds__(kThreads, CTAS)
                 }
                 if (!ok) break;
                 mma_commit(&tfull[ab]);
-                ++k;
             }
             // Every MMA this thread issued must finish before TMEM is freed.
             if (any) {
@@ -550,56 +604,63 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     } else {
         // ----------------------------------------------------- epilogue
         // Thread = query row 128 h + 32 qd + lane of half h (TMEM lane
-        // 32 qd + lane).  Its 32-row block 4 h + qd is copy blk / bpc of
-        // block blk % bpc; copy c owns tile columns [c W, c W + W) with
-        // W = 128 / reps.  rmax[h] is the running max of that row over the
-        // document's columns seen so far.
+        // 32 qd + lane).  Row block 4 h + qd is copy (4 h + qd) / bpc of
+        // block (4 h + qd) % bpc; the copy of this warp takes the documents
+        // whose ordinal is that copy mod reps, and rmax[h] is the running
+        // max of the row over the current document's columns.
         const int qd = warp & 3;
-        const int W = 128 / a.reps;
+        const int copy = qd / a.bpc;
+        const bool active = copy < a.reps;
         float rmax[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-        int acc = 0;
-        uint32_t docs = 0;  // documents finished; buffer = docs & 1, its use count = docs >> 1
+        int acc = 0;           // super-tiles finished
+        uint32_t ord = 0;      // documents seen (all copies)
+        uint32_t mydocs = 0;   // documents of this copy finished
+        bool mine = false;
         for (int t = 0;; ++t) {
-            const int ii = t % kInfoRing;
-            if (!warp_wait(&ifull[ii], (t / kInfoRing) & 1, abort_flag, a.err)) break;
-            const TileInfo ti = info[ii];
+            const int gs = t % kSegRing;
+            if (!warp_wait(&gfull[gs], (t / kSegRing) & 1, abort_flag, a.err)) break;
+            const SegInfo si = seg[gs];
             __syncwarp();
-            if (lane == 0) mbar_arrive(&iempty[ii]);
-            if (ti.flags & kEnd) break;
-            if (ti.flags & kFirst) {
+            if (lane == 0) mbar_arrive(&gempty[gs]);
+            if (si.flags & kEnd) break;
+            const int ab = acc % kAcc;
+            if (si.flags & kStFirst) {
+                if (!warp_wait(&tfull[ab], (acc / kAcc) & 1, abort_flag, a.err)) break;
+                tc_fence_after();
+            }
+            if (si.flags & kFirst) {
+                mine = active && (ord % static_cast<uint32_t>(a.reps)) == static_cast<uint32_t>(copy);
+                ++ord;
 #pragma unroll
                 for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
             }
-            const float* scl = nullptr;
-            const int j = t % kScaleRing;
-            if (F8) {
-                if (!warp_wait(&sfull[j], (t / kScaleRing) & 1, abort_flag, a.err)) break;
-                scl = sc + j * kScalePitch + (ti.row0 & 3);
-            }
-            const int ab = acc % kAcc;
-            if (!warp_wait(&tfull[ab], (acc / kAcc) & 1, abort_flag, a.err)) break;
-            tc_fence_after();
+            if (mine) {
+                const float* scl = nullptr;  // scl[c]: scale of column c's document row
+                const int ss = t % kScaleRing;
+                if (F8) {
+                    if (!warp_wait(&sfull[ss], (t / kScaleRing) & 1, abort_flag, a.err)) break;
+                    scl = sc + ss * kScalePitch + (si.row0 & 3) - si.col;
+                }
+                const int c_lo = si.col;
+                const int c_hi = si.col + si.r;
 #pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const int blk = 4 * h + qd;
-                const int cp = blk / a.bpc;
-                if (cp < a.reps) {
-                    const int c_end = min(cp * W + W, ti.r);
-                    for (int c0 = cp * W; c0 < c_end; c0 += 32) {
+                for (int h = 0; h < H; ++h) {
+                    for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
                         float v[32];
                         tmem_ld32(tbase + (static_cast<uint32_t>(qd * 32) << 16) +
-                                      static_cast<uint32_t>((ab * H + h) * 128 + c0),
+                                      static_cast<uint32_t>((ab * H + h) * STR + c0),
                                   v);
-                        if (F8) {
+                        if (c0 < c_lo || c0 + 32 > c_hi) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                const bool in = c0 + c >= c_lo && c0 + c < c_hi;
+                                v[c] = in ? (F8 ? v[c] * scl[c0 + c] : v[c]) : -INFINITY;
+                            }
+                        } else if (F8) {
 #pragma unroll
                             for (int c = 0; c < 32; ++c) v[c] *= scl[c0 + c];
-                        }
-                        if (c0 + 32 > ti.r) {
-#pragma unroll
-                            for (int c = 0; c < 32; ++c)
-                                if (c0 + c >= ti.r) v[c] = -INFINITY;
                         }
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1)
@@ -608,53 +669,60 @@ __global__ void __launch_bounds__(kThreads, CTAS)
                         rmax[h] = fmaxf(rmax[h], v[0]);
                     }
                 }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&tempty[ab]);
-                if (F8) mbar_arrive(&sempty[j]);
-            }
-            ++acc;
-            if (ti.flags & kLast) {
-                const int pb = docs & 1;
-                const uint32_t use = docs >> 1;
-                if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
-                float* pp = part + pb * 4 * H * 32;
-#pragma unroll
-                for (int h = 0; h < H; ++h) pp[(4 * h + qd) * 32 + lane] = rmax[h];
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&pfull[pb]);
-                if (qd == 0) {
-                    if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) break;
+                if (F8) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sempty[ss]);
+                }
+                if (si.flags & kLast) {
                     if (SH) {
-                        const int64_t fc = static_cast<int64_t>(ti.f) % a.n_cand;
-                        for (int b = 0; b < a.bpc; ++b) {
-                            float m = pp[b * 32 + lane];
-                            for (int rp = 1; rp < a.reps; ++rp) m = fmaxf(m, pp[(rp * a.bpc + b) * 32 + lane]);
-                            const int qq = ti.q * a.group + b;
+                        const int64_t fc = static_cast<int64_t>(si.f) % a.n_cand;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const int b = (4 * h + qd) % a.bpc;
+                            const int qq = si.q * a.group + b;
                             float sq = 1.f;
                             if (F8 && lane < a.nq && qq < a.n_queries)
                                 sq = __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + lane);
-                            const float sum = warp_sum(lane < a.nq ? (F8 ? m * sq : m) : 0.f);
+                            const float sum = warp_sum(lane < a.nq ? (F8 ? rmax[h] * sq : rmax[h]) : 0.f);
                             if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
                         }
                     } else {
-                        float sum = 0.f;
-                        for (int b = 0; b < a.bpc; ++b) {
-                            float m = pp[b * 32 + lane];
-                            for (int rp = 1; rp < a.reps; ++rp) m = fmaxf(m, pp[(rp * a.bpc + b) * 32 + lane]);
-                            const int tok = b * 32 + lane;
-                            if (tok < a.nq)
-                                sum += F8 ? m * __ldg(a.q_scales + static_cast<int64_t>(ti.q) * a.nq + tok) : m;
+                        const int b = qd % a.bpc;
+                        const int tok = b * 32 + lane;
+                        float v = 0.f;
+                        if (tok < a.nq)
+                            v = F8 ? rmax[0] * __ldg(a.q_scales + static_cast<int64_t>(si.q) * a.nq + tok) : rmax[0];
+                        const float sum = warp_sum(v);
+                        if (a.bpc == 1) {
+                            if (lane == 0) a.out[si.f] = sum;
+                        } else {
+                            // the copy's warps add their block sums in block order
+                            const int pb = copy * 2 + (mydocs & 1);
+                            const uint32_t use = mydocs >> 1;
+                            if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
+                            if (lane == 0) {
+                                part[pb * 4 + b] = sum;
+                                mbar_arrive(&pfull[pb]);
+                            }
+                            if (b == 0) {
+                                if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) break;
+                                if (lane == 0) {
+                                    float tot = part[pb * 4];
+                                    for (int bb = 1; bb < a.bpc; ++bb) tot += part[pb * 4 + bb];
+                                    a.out[si.f] = tot;
+                                    mbar_arrive(&pempty[pb]);
+                                }
+                            }
                         }
-                        sum = warp_sum(sum);
-                        if (lane == 0) a.out[ti.f] = sum;
                     }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&pempty[pb]);
+                    ++mydocs;
                 }
-                ++docs;
+            }
+            if (si.flags & kStLast) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[ab]);
+                ++acc;
             }
         }
     }
@@ -667,9 +735,10 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     }
 }
 
-// Plan shared memory, encode the tensor maps and launch dense_tc_kernel.
-// F8 ignores `dtype` (rows are E4M3 codes; t_scales in `a`).  The caller
-// sets a.nchunks = ceil(d / chunk_elems(F8)), and a.bpc / a.qbox: per-query
+// Plan shared memory, encode the tensor maps and launch dense_tc_kernel
+// (one CTA per SM: its two accumulators take all 512 TMEM columns).  F8
+// ignores `dtype` (rows are E4M3 codes; t_scales in `a`).  The caller sets
+// a.nchunks = ceil(d / chunk_elems(F8)), and a.bpc / a.qbox: per-query
 // ceil(nq / 32) and 32 bpc, shared mode the group size and 32.
 template <int H, bool SH, bool F8>
 tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
@@ -686,60 +755,34 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
                                    CE, static_cast<uint32_t>(a.qbox));
     if (st != TMS_OK) return st;
-    // Shared-memory plan.  Prefer two CTAs per SM (H == 1: 256 TMEM columns
-    // each) when each still gets a ring of at least 4 dimension chunks, with
-    // as many copies of the query blocks as fit (fewer copies only narrow
-    // the epilogue's share of each tile); else one CTA per SM.  Within a
-    // plan take the query-slot count (2, else 1) that gives the most stage
-    // chunks.
-    const bool can3d = d % CE == 0 && a.nchunks >= 2;
-    auto plan = [&](int per_cta_limit, int cps, int rows_alloc, int& stages, int& qslots) {
+    // Shared-memory plan: as many copies of the query blocks as fit with a
+    // ring of at least 4 chunk stages (fewer copies only deal documents to
+    // fewer warps), else at least 2; within a plan the query-slot count
+    // (2, else 1) that gives the most stages.
+    auto plan = [&](int rows_alloc, int& stages, int& qslots) {
+        const int limit = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
         int best = -1;
         for (int qs = 2; qs >= 1; --qs) {
-            const Layout L0 = make_layout(0, cps, qs, a.nchunks, rows_alloc, H, F8);
-            const int sts = std::min(kMaxStages, (per_cta_limit - L0.total) / (cps * kChunkBytes + 16));
-            if (sts * cps > best) {
-                best = sts * cps;
+            const Layout L0 = make_layout(0, qs, a.nchunks, rows_alloc, H, F8);
+            const int sts = std::min(kMaxStages, (limit - L0.total) / (st_rows(H) * 128 + 16));
+            if (sts > best) {
+                best = sts;
                 stages = sts;
                 qslots = qs;
             }
         }
         return best;
     };
-    const int max_reps = SH ? (a.bpc == 2 ? 2 : 1) : (a.bpc == 3 ? 1 : 4 / a.bpc);
-    const int limit1 = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
-    const int limit2 = dev.smem_per_sm / 2 - dev.smem_reserved - 1024;
-    int stages = 0, qslots = 1, ctas = 0, reps = max_reps, cps = can3d ? 2 : 1;
-    if (H == 1) {
-        for (int rp = max_reps; rp >= 1 && ctas == 0; rp /= 2) {
-            const int ra = 32 * a.bpc * rp;
-            for (int c = can3d ? 2 : 1; c >= 1 && ctas == 0; --c) {
-                if (plan(limit2, c, ra, stages, qslots) >= 4 && stages >= 2) {
-                    ctas = 2;
-                    reps = rp;
-                    cps = c;
-                }
-            }
-        }
-    }
-    for (int rp = max_reps; rp >= 1 && ctas == 0; rp /= 2) {
-        const int ra = 32 * a.bpc * rp;
-        for (int c = can3d ? 2 : 1; c >= 1 && ctas == 0; --c) {
-            if (plan(limit1, c, ra, stages, qslots) >= 2 && stages >= 2) {
-                ctas = 1;
-                reps = rp;
-                cps = c;
-            }
-        }
-    }
-    if (ctas == 0) return TMS_ERR_UNSUPPORTED;
+    const int max_reps = H == 2 ? 1 : (a.bpc == 3 ? 1 : 4 / a.bpc);
+    int stages = 0, qslots = 1, reps = 0;
+    for (int need = 4; need >= 2 && reps == 0; need -= 2)
+        for (int rp = max_reps; rp >= 1 && reps == 0; rp /= 2)
+            if (plan(32 * a.bpc * rp, stages, qslots) >= need) reps = rp;
+    if (reps == 0) return TMS_ERR_UNSUPPORTED;
     a.reps = reps;
     a.rows_alloc = 32 * a.bpc * reps;
-    a.cps = cps;
     for (int h = 0; h < kBoxKinds; ++h) {
-        const uint32_t rows = static_cast<uint32_t>(8 * (h + 1));
-        st = a.cps == 2 ? encode_tmap_rows_chunks(&maps.doc[h], tdt, dbase, a.nchunks, n_tokens, row_bytes, rows, CE)
-                        : encode_tmap_2d(&maps.doc[h], tdt, dbase, d, n_tokens, row_bytes, CE, rows);
+        st = encode_tmap_2d(&maps.doc[h], tdt, dbase, d, n_tokens, row_bytes, CE, static_cast<uint32_t>(8 * (h + 1)));
         if (st != TMS_OK) return st;
     }
     if (F8) {
@@ -753,12 +796,12 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.idesc = make_idesc(128, 0, (!F8 && dtype == TMS_BF16) ? 1u : 0u);
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, a.cps, qslots, a.nchunks, a.rows_alloc, H, F8);
+    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, H, F8);
     const int smem = L.total + 1024;
-    auto kern = ctas == 2 ? dense_tc_kernel<H, (H == 1 ? 2 : 1), SH, F8> : dense_tc_kernel<H, 1, SH, F8>;
+    auto kern = dense_tc_kernel<H, SH, F8>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
-    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count), a.n_flat);
     kern<<<static_cast<unsigned>(grid), kThreads, smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
 }

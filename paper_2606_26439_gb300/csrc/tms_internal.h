@@ -29,13 +29,6 @@ tms_status current_device(DeviceInfo* out);
 tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
                           uint64_t rows, uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows);
 
-// Encode the 3-D view {chunk_elems elements, rows, chunk} of a row-major
-// [rows][nchunks * chunk_elems] array whose chunks are 128 bytes (chunk
-// stride 128 bytes), box {chunk_elems, box_rows, 2}, 128-byte swizzle,
-// zero fill outside.
-tms_status encode_tmap_rows_chunks(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int nchunks,
-                                   uint64_t rows, uint64_t row_bytes, uint32_t box_rows, uint32_t chunk_elems);
-
 // Encode a tensor map over `n` consecutive fp32 elements (one row), box of
 // box_elems x 1, no swizzle, zero fill outside; load with tma_load_2d(x, 0).
 tms_status encode_tmap_1d_f32(CUtensorMap* map, const void* base, uint64_t n, uint32_t box_elems);
