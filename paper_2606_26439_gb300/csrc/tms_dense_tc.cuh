@@ -20,14 +20,18 @@
 // barrier round trips, commits, MMA issue -- are paid once per super-tile,
 // typically two to three documents.
 //
-//   * Producer warp: reads candidate metadata (id -> offset, length),
-//     packs tiles into super-tiles, and streams them from HBM into a ring
-//     of shared-memory chunk stages (256 rows x 128 bytes: 64 fp16/bf16 or
-//     128 E4M3 elements per row) with one TMA box per tile and chunk, lanes
-//     issuing the tiles of a super-tile in parallel (128-byte swizzle).
-//     Each token is read from HBM once (Theorem 1 with BQ = Nq, or the
-//     whole group of queries in the shared schedule).  F8: every tile's
-//     row scales follow through a ring of small TMA loads.
+//   * Planner warp: takes the candidates 32 at a time, one per lane
+//     (metadata, validity, query, -inf / NaN for empty / bad documents),
+//     packs their tiles into super-tiles and publishes each super-tile as
+//     one record -- header plus tile list -- with a single barrier
+//     arrival.  It also loads each query's tile (replicated, see above)
+//     and, F8, every tile's row scales through a ring of small TMA loads.
+//   * Loader warp: streams each super-tile from HBM into a ring of shared-
+//     memory chunk stages (st_rows x 128 bytes: 64 fp16/bf16 or 128 E4M3
+//     elements per row), one TMA box per tile and chunk, the tiles issued
+//     by parallel lanes (128-byte swizzle).  Each token is read from HBM
+//     once (Theorem 1 with BQ = Nq, or the whole group of queries in the
+//     shared schedule).
 //   * MMA warp: one thread issues tcgen05.mma (M = 128 query rows, K = 32
 //     bytes: 16 fp16/bf16 elements with kind::f16, 32 E4M3 elements with
 //     kind::f8f6f4) over every dimension chunk of a super-tile,
@@ -64,36 +68,43 @@ __host__ __device__ constexpr int st_rows(int H) { return 256 / H; }  // rows pe
 // Elements per 128-byte dimension chunk (one 128-byte swizzle row).
 __host__ __device__ constexpr int chunk_elems(bool f8) { return f8 ? 128 : 64; }
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
-constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per producer lane)
-constexpr int kSegRing = 64;                  // tile records in flight to the epilogue
-constexpr int kStRing = 8;                    // super-tile records in flight to the MMA thread
+constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per planner lane)
+constexpr int kStRing = 8;                    // super-tile records in flight
 constexpr int kScaleRing = 32;                // F8: tiles whose row scales are in flight or held
 constexpr int kScaleBox = 136;                // floats per scale load: 128 rows + up to 3 of 16-byte alignment
 constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a multiple of 128 B)
 constexpr int kEpiWarps = 4;
-constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, four epilogue warps
+constexpr int kLoaderWarp = 2 + kEpiWarps;
+constexpr int kThreads = 32 * (kLoaderWarp + 1);  // planner, MMA, four epilogue warps, loader
 constexpr int kAcc = 2;                       // accumulator buffers (each H x st_rows(H) TMEM columns)
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
 
 enum : int { kFirst = 1, kLast = 2, kEnd = 4, kStFirst = 8, kStLast = 16 };
 
-// One document tile inside a super-tile (producer -> epilogue).
+// One document tile inside a super-tile.
 struct SegInfo {
-    int f;      // flat candidate index
+    int f;      // flat candidate index (shared mode: position in the candidate list)
     int r;      // valid rows (1..128)
     int q;      // query index (shared mode: group index)
-    int flags;  // kFirst / kLast of the document, kStFirst / kStLast of the super-tile, kEnd
+    int flags;  // kFirst / kLast of the document
     int row0;   // token row of the tile's first row
     int col;    // first column (row of the super-tile), a multiple of 8
 };
 
-// One super-tile (producer -> MMA thread).
-struct StInfo {
+// One super-tile record (planner -> loader, MMA thread and epilogue).
+struct StHdr {
     int q;      // query (group) whose tile it is scored against
     int n;      // MMA N: packed rows rounded up to 16
+    int nseg;   // tiles
     int flags;  // kEnd
-    int pad;
+    int rows;   // packed rows (sum of the tiles' rows rounded up to 8)
+    int pad[3];
+};
+
+struct StSlot {
+    StHdr h;
+    SegInfo seg[kMaxSeg];
 };
 
 struct Args {
@@ -116,14 +127,14 @@ struct Args {
     int stages;      // chunk stages in the ring
     int qslots;
     int bpc;         // 32-row query blocks per copy: ceil(nq / 32) token blocks, or the group's queries
-    int reps;        // copies of the blocks stacked in M; documents are dealt round-robin to the copies
+    int reps;        // copies of the blocks stacked in M (1, 2 or 4); documents are dealt round-robin to them
     int rows_alloc;  // query rows held per dimension chunk: 32 * bpc * reps
     int qbox;        // rows of one query TMA box: 32 * bpc (per-query), 32 (shared)
     uint32_t idesc;  // instruction descriptor, N field left 0 (set per super-tile)
 };
 
 struct Layout {
-    int q_off, stage_off, part_off, sc_off, seg_off, sti_off, bar_off, misc_off, total;
+    int q_off, stage_off, part_off, sc_off, st_off, bar_off, misc_off, total;
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
@@ -138,19 +149,18 @@ __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunk
     L.stage_off = (qslots * nchunks * rows_alloc * 128 + 1023) & ~1023;
     L.part_off = L.stage_off + stages * st_rows(H) * 128;
     L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
-    L.seg_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
-    L.sti_off = L.seg_off + kSegRing * static_cast<int>(sizeof(SegInfo));
-    L.bar_off = L.sti_off + kStRing * static_cast<int>(sizeof(StInfo));
-    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * kSegRing + 2 * kStRing + 8 + 2 * kScaleRing + 1;
+    L.st_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
+    L.bar_off = L.st_off + kStRing * static_cast<int>(sizeof(StSlot));
+    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * kStRing + 8 + 2 * kScaleRing + 1;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
 }
 
-// Candidate metadata for the producer: lane l of the warp holds the raw
+// Candidate metadata for the planner: lane l of the warp holds the raw
 // entry of candidate window position l.  Loads are only issued here; they
 // are classified (meta_status) when the window becomes current, one window
-// later, so the producer never waits on them.
+// later, so the planner never waits on them.
 struct Meta {
     int64_t off;
     int len;
@@ -181,19 +191,24 @@ __device__ __forceinline__ int meta_status(const Args& a, int id, int64_t off, i
     return (len < 0 || off < 0 || off + len > a.n_tokens) ? 2 : 0;
 }
 
-// Every lane waits (and so acquires the barrier's phase itself); the warp
-// agrees on the outcome.  Returns false on timeout / abort.
+// Lane 0 polls the barrier and broadcasts the outcome; the warp barrier
+// orders the other lanes after lane 0's acquire.  For barriers guarding
+// data written by other threads or ordering tensor-core work.  Returns
+// false on timeout / abort.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           unsigned int* err) {
-    const bool ok = mbar_wait(bar, parity, abort_flag, err);
-    return __all_sync(0xffffffffu, ok) != 0;
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
 }
 
-// Each lane waits on its own barrier (none when `bar` is null); the warp
-// agrees on the outcome.
-__device__ __forceinline__ bool lanes_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                           unsigned int* err) {
-    const bool ok = bar == nullptr || mbar_wait(bar, parity, abort_flag, err);
+// Every lane waits (and so observes the phase itself): for barriers that
+// complete the TMA bytes the lanes then read.
+__device__ __forceinline__ bool warp_wait_all(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned int* err) {
+    const bool ok = mbar_wait(bar, parity, abort_flag, err);
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
@@ -242,8 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
     uint8_t* stage_base = smem + L.stage_off;
     float* part = reinterpret_cast<float*>(smem + L.part_off);  // [copy][parity][block]
     float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // [kScaleRing][kScalePitch]
-    SegInfo* seg = reinterpret_cast<SegInfo*>(smem + L.seg_off);
-    StInfo* sti = reinterpret_cast<StInfo*>(smem + L.sti_off);
+    StSlot* slots = reinterpret_cast<StSlot*>(smem + L.st_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;
     uint64_t* empty = full + S;
@@ -251,9 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
     uint64_t* tempty = tfull + kAcc;
     uint64_t* qfull = tempty + kAcc;
     uint64_t* qempty = qfull + QS;
-    uint64_t* gfull = qempty + QS;          // [kSegRing]
-    uint64_t* gempty = gfull + kSegRing;    // [kSegRing]
-    uint64_t* xfull = gempty + kSegRing;    // [kStRing]
+    uint64_t* xfull = qempty + QS;          // [kStRing]
     uint64_t* xempty = xfull + kStRing;     // [kStRing]
     uint64_t* pfull = xempty + kStRing;     // [copy][parity]
     uint64_t* pempty = pfull + 4;           // [copy][parity]
@@ -265,8 +277,6 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    // epilogue warps that read one tile (the warps of its copy)
-    const int owners = H == 2 ? 4 : a.bpc;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
@@ -281,13 +291,9 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
             mbar_init(&qfull[i], 1);
             mbar_init(&qempty[i], 1);
         }
-        for (int i = 0; i < kSegRing; ++i) {
-            mbar_init(&gfull[i], 1);
-            mbar_init(&gempty[i], kEpiWarps);
-        }
         for (int i = 0; i < kStRing; ++i) {
             mbar_init(&xfull[i], 1);
-            mbar_init(&xempty[i], 1);
+            mbar_init(&xempty[i], 2 + kEpiWarps);  // loader, MMA thread, epilogue warps
         }
         for (int i = 0; i < 4; ++i) {
             mbar_init(&pfull[i], a.bpc);
@@ -295,16 +301,18 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
         }
         for (int i = 0; i < kScaleRing; ++i) {
             mbar_init(&sfull[i], 1);
-            mbar_init(&sempty[i], owners);
+            mbar_init(&sempty[i], kEpiWarps);
         }
         mbar_init(mdone, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
+    if (warp == kLoaderWarp) {
+        if (lane < kBoxKinds) prefetch_tensormap(&maps.doc[lane]);
+    }
     if (warp == 0) {
         if (lane == 0) prefetch_tensormap(&maps.q);
-        if (lane >= 1 && lane <= kBoxKinds) prefetch_tensormap(&maps.doc[lane - 1]);
-        if (F8 && lane == kBoxKinds + 1) prefetch_tensormap(&maps.scales);
+        if (F8 && lane == 1) prefetch_tensormap(&maps.scales);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, TCOLS);
@@ -316,67 +324,64 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
     const uint32_t tbase = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------------ producer
+        // ------------------------------------------------------- planner
         const uint64_t pol_stream = policy_evict_first();
         const uint64_t pol_keep = policy_evict_last();
-        int s = 0;
-        uint32_t ph = 0;
-        int64_t issued = 0;
-        int tseg = 0;  // tile records published
+        int tseg = 0;  // tiles published
         int tst = 0;   // super-tiles published
         int qi = 0, cur_q = -1;
-        int q = 0;
-        int64_t q_end = 0;
         bool aborted = false;
         // The open super-tile: its tile i lives in lane i's registers.
         int nseg = 0, rows_used = 0, st_q = 0;
         int my_f = 0, my_r = 0, my_flags = 0, my_row0 = 0, my_col = 0;
 
-        // Publish the open super-tile: tile records, F8 scale loads, the
-        // MMA record, the query tile if it changed, then every chunk.
+        // Publish the open super-tile: F8 row-scale loads, the record, and
+        // the query tile if the query changed.
         auto close_st = [&]() -> bool {
             const bool has = lane < nseg;
-            const int gs = (tseg + lane) % kSegRing;
-            if (!lanes_wait(has ? &gempty[gs] : nullptr, (((tseg + lane) / kSegRing) & 1) ^ 1, abort_flag, a.err))
-                return false;
+            const int xs = tst % kStRing;
+            if (!warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err)) return false;
+            if (F8) {
+                // Every epilogue warp passes every tile's scale slot in
+                // order, so the slot of the last tile being free means all
+                // of this super-tile's slots are.
+                const int u = tseg + nseg - 1;
+                if (!warp_wait(&sempty[u % kScaleRing], ((u / kScaleRing) & 1) ^ 1, abort_flag, a.err)) return false;
+                if (has) {
+                    // the tile's row scales, from the 16-byte boundary at or below its first row
+                    const int ss = (tseg + lane) % kScaleRing;
+                    mbar_arrive_expect_tx(&sfull[ss], static_cast<uint32_t>(kScaleBox * 4));
+                    tma_load_2d(sc + ss * kScalePitch, &maps.scales, my_row0 & ~3, 0, &sfull[ss], pol_stream);
+                }
+            }
+            StSlot* x = &slots[xs];
             if (has) {
                 SegInfo si;
                 si.f = my_f;
                 si.r = my_r;
                 si.q = st_q;
-                si.flags = my_flags | (lane == 0 ? kStFirst : 0) | (lane == nseg - 1 ? kStLast : 0);
+                si.flags = my_flags;
                 si.row0 = my_row0;
                 si.col = my_col;
-                seg[gs] = si;
-                mbar_arrive(&gfull[gs]);
+                x->seg[lane] = si;
             }
-            if (F8) {
-                // the tile's row scales, from the 16-byte boundary at or below its first row
-                const int ss = (tseg + lane) % kScaleRing;
-                if (!lanes_wait(has ? &sempty[ss] : nullptr, (((tseg + lane) / kScaleRing) & 1) ^ 1, abort_flag,
-                                a.err))
-                    return false;
-                if (has) {
-                    mbar_arrive_expect_tx(&sfull[ss], static_cast<uint32_t>(kScaleBox * 4));
-                    tma_load_2d(sc + ss * kScalePitch, &maps.scales, my_row0 & ~3, 0, &sfull[ss], pol_stream);
-                }
-            }
-            tseg += nseg;
-            const int xs = tst % kStRing;
-            if (!warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err)) return false;
             if (lane == 0) {
-                StInfo x;
-                x.q = st_q;
-                x.n = (rows_used + 15) & ~15;
-                x.flags = 0;
-                x.pad = 0;
-                sti[xs] = x;
-                mbar_arrive(&xfull[xs]);
+                StHdr h;
+                h.q = st_q;
+                h.n = (rows_used + 15) & ~15;
+                h.nseg = nseg;
+                h.flags = 0;
+                h.rows = rows_used;
+                h.pad[0] = h.pad[1] = h.pad[2] = 0;
+                x->h = h;
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xfull[xs]);
             ++tst;
-            // A new query's rows go to the next query slot.  The super-tile
-            // record is published first: the MMA thread releases the old
-            // slot only once it sees the new query.
+            tseg += nseg;
+            // A new query's rows go to the next query slot.  The record is
+            // published first: the MMA thread releases the old slot only
+            // once it sees the new query.
             if (st_q != cur_q) {
                 const int slot = qi % QS;
                 if (!warp_wait(&qempty[slot], ((qi / QS) & 1) ^ 1, abort_flag, a.err)) return false;
@@ -400,30 +405,17 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                 ++qi;
                 cur_q = st_q;
             }
-            const int n8 = (my_r + 7) & ~7;
-            const CUtensorMap* dmap = &maps.doc[has ? (n8 >> 3) - 1 : 0];
-            for (int kc = 0; kc < NCH; ++kc) {
-                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) return false;
-                if (lane == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(rows_used * 128));
-                __syncwarp();
-                if (has)
-                    tma_load_2d(stage_base + s * STAGE_BYTES + my_col * 128, dmap, kc * CE, my_row0, &full[s],
-                                pol_stream);
-                ++issued;
-                if (++s == S) {
-                    s = 0;
-                    ph ^= 1;
-                }
-            }
             nseg = 0;
             rows_used = 0;
             return true;
         };
 
+        int qw = 0;            // query of the window's first candidate (per-query mode)
+        int64_t qw_end = 0;    // its end in the flat list
         if (!SH) {
             const int64_t co_last = __ldg(a.cand_offsets + a.n_queries);
             if (co_last != a.n_cand && blockIdx.x == 0 && lane == 0) atomicOr(a.err, TMS_DEVERR_BAD_CSR);
-            q_end = __ldg(a.cand_offsets + 1);
+            qw_end = __ldg(a.cand_offsets + 1);
         }
         // three-window metadata pipeline: ids two windows ahead, offsets
         // and lengths one window ahead, the current window in registers.
@@ -432,34 +424,52 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
         Meta nxt = load_meta(a, id_next);
         int id_next2 = load_id(a, 64 + lane);
 
-        for (int64_t k = 0;; ++k) {
-            const int kl = static_cast<int>(k & 31);
-            const int64_t f = static_cast<int64_t>(blockIdx.x) + k * gridDim.x;
-            if (f >= a.n_flat) break;
-            const int cid = __shfl_sync(0xffffffffu, cur.id, kl);
-            const int64_t off = __shfl_sync(0xffffffffu, cur.off, kl);
-            const int len = __shfl_sync(0xffffffffu, cur.len, kl);
-            const int status = meta_status(a, cid, off, len);
+        for (int64_t k0 = 0;; k0 += 32) {
+            if (static_cast<int64_t>(blockIdx.x) + k0 * gridDim.x >= a.n_flat) break;
+            // lane = one candidate of the window
+            const int64_t f = static_cast<int64_t>(blockIdx.x) + (k0 + lane) * gridDim.x;
+            const bool valid = f < a.n_flat;
+            const int status = valid ? meta_status(a, cur.id, cur.off, cur.len) : 3;
+            int ql = 0;
+            int64_t pos = f;  // shared mode: position in the candidate list
             if (SH) {
-                q = static_cast<int>(f / a.n_cand);
-            } else {
-                while (f >= q_end && q < a.n_queries - 1) {
-                    ++q;
-                    q_end = __ldg(a.cand_offsets + q + 1);
+                if (valid) {
+                    ql = static_cast<int>(f / a.n_cand);
+                    pos = f - static_cast<int64_t>(ql) * a.n_cand;
                 }
+            } else {
+                ql = qw;
+                int64_t qe = qw_end;
+                if (valid) {
+                    while (f >= qe && ql < a.n_queries - 1) {
+                        ++ql;
+                        qe = __ldg(a.cand_offsets + ql + 1);
+                    }
+                }
+                const int last = __popc(__ballot_sync(0xffffffffu, valid)) - 1;
+                qw = __shfl_sync(0xffffffffu, ql, last);
+                qw_end = __shfl_sync(0xffffffffu, qe, last);
             }
-            if (status != 0 || len == 0) {
+            if (valid && (status != 0 || cur.len == 0)) {
                 const float v = status != 0 ? __int_as_float(0x7fc00000) : -INFINITY;
                 if (SH) {
-                    const int64_t fc = f % a.n_cand;
-                    if (lane < a.group && q * a.group + lane < a.n_queries)
-                        a.out[static_cast<int64_t>(q * a.group + lane) * a.n_cand + fc] = v;
-                } else if (lane == 0) {
+                    for (int g = 0; g < a.group; ++g)
+                        if (ql * a.group + g < a.n_queries)
+                            a.out[static_cast<int64_t>(ql * a.group + g) * a.n_cand + pos] = v;
+                } else {
                     a.out[f] = v;
                 }
-                if (status != 0 && lane == 0)
-                    atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
-            } else {
+                if (status != 0) atomicOr(a.err, status == 1 ? TMS_DEVERR_BAD_ID : TMS_DEVERR_BAD_RANGE);
+            }
+            // pack the window's documents, in order, into super-tiles
+            unsigned docs = __ballot_sync(0xffffffffu, valid && status == 0 && cur.len > 0);
+            while (docs != 0u) {
+                const int i = __ffs(docs) - 1;
+                docs &= docs - 1u;
+                const int len = __shfl_sync(0xffffffffu, cur.len, i);
+                const int off = static_cast<int>(__shfl_sync(0xffffffffu, cur.off, i));
+                const int q = __shfl_sync(0xffffffffu, ql, i);
+                const int fi = static_cast<int>(__shfl_sync(0xffffffffu, SH ? pos : f, i));
                 for (int r0 = 0; r0 < len; r0 += kRows) {
                     const int r = min(kRows, len - r0);
                     const int n8 = (r + 7) & ~7;
@@ -471,10 +481,10 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                     }
                     if (nseg == 0) st_q = q;
                     if (lane == nseg) {
-                        my_f = static_cast<int>(f);
+                        my_f = fi;
                         my_r = r;
                         my_flags = (r0 == 0 ? kFirst : 0) | (r0 + kRows >= len ? kLast : 0);
-                        my_row0 = static_cast<int>(off) + r0;
+                        my_row0 = off + r0;
                         my_col = rows_used;
                     }
                     rows_used += n8;
@@ -482,36 +492,74 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                 }
                 if (aborted) break;
             }
-            if (kl == 31) {
-                cur = nxt;
-                nxt = load_meta(a, id_next2);
-                id_next2 = load_id(a, k + 65 + lane);
-            }
+            if (aborted) break;
+            cur = nxt;
+            nxt = load_meta(a, id_next2);
+            id_next2 = load_id(a, k0 + 96 + lane);
         }
         if (!aborted && nseg > 0 && !close_st()) aborted = true;
         if (!aborted) {
-            const int gs = tseg % kSegRing;
-            if (warp_wait(&gempty[gs], ((tseg / kSegRing) & 1) ^ 1, abort_flag, a.err) && lane == 0) {
-                SegInfo si;
-                si.f = 0;
-                si.r = 0;
-                si.q = 0;
-                si.flags = kEnd;
-                si.row0 = 0;
-                si.col = 0;
-                seg[gs] = si;
-                mbar_arrive(&gfull[gs]);
-            }
             const int xs = tst % kStRing;
             if (warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err) && lane == 0) {
-                StInfo x;
-                x.q = 0;
-                x.n = 0;
-                x.flags = kEnd;
-                x.pad = 0;
-                sti[xs] = x;
+                StHdr h;
+                h.q = 0;
+                h.n = 0;
+                h.nseg = 0;
+                h.flags = kEnd;
+                h.rows = 0;
+                h.pad[0] = h.pad[1] = h.pad[2] = 0;
+                slots[xs].h = h;
                 mbar_arrive(&xfull[xs]);
             }
+        }
+        // Let every copy this warp issued land before the CTA can exit.
+        if (lane == 0) {
+            if (F8) {
+                const int ns = tseg < kScaleRing ? tseg : kScaleRing;
+                for (int i = 1; i <= ns; ++i)
+                    drain_wait(&sfull[(tseg - i) % kScaleRing], ((tseg - i) / kScaleRing) & 1);
+            }
+            if (qi > 0) drain_wait(&qfull[(qi - 1) % QS], ((qi - 1) / QS) & 1);
+        }
+        __syncwarp();
+    } else if (warp == kLoaderWarp) {
+        // -------------------------------------------------------- loader
+        const uint64_t pol_stream = policy_evict_first();
+        int s = 0;
+        uint32_t ph = 0;
+        int64_t issued = 0;
+        for (int t = 0;; ++t) {
+            const int xs = t % kStRing;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            const StHdr h = slots[xs].h;
+            if (h.flags & kEnd) break;
+            const bool has = lane < h.nseg;
+            int n8 = 8, row0 = 0, col = 0;
+            if (has) {
+                const SegInfo si = slots[xs].seg[lane];
+                n8 = (si.r + 7) & ~7;
+                row0 = si.row0;
+                col = si.col;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xempty[xs]);
+            const CUtensorMap* dmap = &maps.doc[(n8 >> 3) - 1];
+            bool ok = true;
+            for (int kc = 0; kc < NCH; ++kc) {
+                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(h.rows * 128));
+                __syncwarp();
+                if (has) tma_load_2d(stage_base + s * STAGE_BYTES + col * 128, dmap, kc * CE, row0, &full[s], pol_stream);
+                ++issued;
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            if (!ok) break;
         }
         // Let every copy still in flight land before the CTA can exit.
         if (lane == 0) {
@@ -524,11 +572,6 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                     pp ^= 1;
                 }
                 drain_wait(&full[ss], pp);
-            }
-            if (F8) {
-                const int ns = tseg < kScaleRing ? tseg : kScaleRing;
-                for (int i = 1; i <= ns; ++i)
-                    drain_wait(&sfull[(tseg - i) % kScaleRing], ((tseg - i) / kScaleRing) & 1);
             }
         }
         __syncwarp();
@@ -545,9 +588,9 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
             for (int t = 0;; ++t) {
                 const int xs = t % kStRing;
                 if (!mbar_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
-                const StInfo x = sti[xs];
-                mbar_arrive(&xempty[xs]);
+                const StHdr x = slots[xs].h;
                 if (x.flags & kEnd) break;
+                mbar_arrive(&xempty[xs]);
                 if (x.q != cur_q) {
                     if (cur_q >= 0) mma_commit(&qempty[qslot]);
                     qslot = qi % QS;
@@ -614,33 +657,38 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
         float rmax[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-        int acc = 0;           // super-tiles finished
+        int tseg = 0;          // tiles seen (all copies)
         uint32_t ord = 0;      // documents seen (all copies)
         uint32_t mydocs = 0;   // documents of this copy finished
         bool mine = false;
-        for (int t = 0;; ++t) {
-            const int gs = t % kSegRing;
-            if (!warp_wait(&gfull[gs], (t / kSegRing) & 1, abort_flag, a.err)) break;
-            const SegInfo si = seg[gs];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&gempty[gs]);
-            if (si.flags & kEnd) break;
-            const int ab = acc % kAcc;
-            if (si.flags & kStFirst) {
-                if (!warp_wait(&tfull[ab], (acc / kAcc) & 1, abort_flag, a.err)) break;
-                tc_fence_after();
-            }
-            if (si.flags & kFirst) {
-                mine = active && (ord % static_cast<uint32_t>(a.reps)) == static_cast<uint32_t>(copy);
-                ++ord;
+        bool aborted = false;
+        for (int t = 0; !aborted; ++t) {
+            const int xs = t % kStRing;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            const StHdr xh = slots[xs].h;
+            if (xh.flags & kEnd) break;
+            const int ab = t % kAcc;
+            if (!warp_wait(&tfull[ab], (t / kAcc) & 1, abort_flag, a.err)) break;
+            tc_fence_after();
+            for (int i = 0; i < xh.nseg; ++i, ++tseg) {
+                const SegInfo si = slots[xs].seg[i];
+                if (si.flags & kFirst) {
+                    mine = active && (ord & static_cast<uint32_t>(a.reps - 1)) == static_cast<uint32_t>(copy);
+                    ++ord;
 #pragma unroll
-                for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-            }
-            if (mine) {
+                    for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
+                }
+                const int ss = tseg % kScaleRing;
+                if (!mine) {
+                    if (F8 && lane == 0) mbar_arrive(&sempty[ss]);
+                    continue;
+                }
                 const float* scl = nullptr;  // scl[c]: scale of column c's document row
-                const int ss = t % kScaleRing;
                 if (F8) {
-                    if (!warp_wait(&sfull[ss], (t / kScaleRing) & 1, abort_flag, a.err)) break;
+                    if (!warp_wait_all(&sfull[ss], (tseg / kScaleRing) & 1, abort_flag, a.err)) {
+                        aborted = true;
+                        break;
+                    }
                     scl = sc + ss * kScalePitch + (si.row0 & 3) - si.col;
                 }
                 const int c_lo = si.col;
@@ -675,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                 }
                 if (si.flags & kLast) {
                     if (SH) {
-                        const int64_t fc = static_cast<int64_t>(si.f) % a.n_cand;
+                        const int64_t fc = si.f;  // shared mode: position in the candidate list
 #pragma unroll
                         for (int h = 0; h < H; ++h) {
                             const int b = (4 * h + qd) % a.bpc;
@@ -699,13 +747,19 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                             // the copy's warps add their block sums in block order
                             const int pb = copy * 2 + (mydocs & 1);
                             const uint32_t use = mydocs >> 1;
-                            if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) break;
+                            if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) {
+                                aborted = true;
+                                break;
+                            }
                             if (lane == 0) {
                                 part[pb * 4 + b] = sum;
                                 mbar_arrive(&pfull[pb]);
                             }
                             if (b == 0) {
-                                if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) break;
+                                if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) {
+                                    aborted = true;
+                                    break;
+                                }
                                 if (lane == 0) {
                                     float tot = part[pb * 4];
                                     for (int bb = 1; bb < a.bpc; ++bb) tot += part[pb * 4 + bb];
@@ -718,11 +772,12 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                     ++mydocs;
                 }
             }
-            if (si.flags & kStLast) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[ab]);
-                ++acc;
+            if (aborted) break;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&tempty[ab]);
+                mbar_arrive(&xempty[xs]);
             }
         }
     }
