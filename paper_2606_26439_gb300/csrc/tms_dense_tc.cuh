@@ -27,7 +27,7 @@
 //     arrival.  It also loads each query's tile (replicated, see above)
 //     and, F8, every tile's row scales through a ring of small TMA loads.
 //   * Loader warp: streams each super-tile from HBM into a ring of shared-
-//     memory chunk stages (st_rows x 128 bytes: 64 fp16/bf16 or 128 E4M3
+//     memory chunk stages (STR rows x 128 bytes: 64 fp16/bf16 or 128 E4M3
 //     elements per row), one TMA box per tile and chunk, the tiles issued
 //     by parallel lanes (128-byte swizzle).  Each token is read from HBM
 //     once (Theorem 1 with BQ = Nq, or the whole group of queries in the
@@ -64,19 +64,18 @@ namespace tms {
 namespace dense {
 
 constexpr int kRows = 128;                    // document rows per tile
-__host__ __device__ constexpr int st_rows(int H) { return 256 / H; }  // rows per super-tile
 // Elements per 128-byte dimension chunk (one 128-byte swizzle row).
 __host__ __device__ constexpr int chunk_elems(bool f8) { return f8 ? 128 : 64; }
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per planner lane)
-constexpr int kStRing = 8;                    // super-tile records in flight
+constexpr int kStRing = 4;                    // super-tile records in flight
 constexpr int kScaleRing = 32;                // F8: tiles whose row scales are in flight or held
 constexpr int kScaleBox = 136;                // floats per scale load: 128 rows + up to 3 of 16-byte alignment
 constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a multiple of 128 B)
 constexpr int kEpiWarps = 4;
 constexpr int kLoaderWarp = 2 + kEpiWarps;
 constexpr int kThreads = 32 * (kLoaderWarp + 1);  // planner, MMA, four epilogue warps, loader
-constexpr int kAcc = 2;                       // accumulator buffers (each H x st_rows(H) TMEM columns)
+constexpr int kAcc = 2;                       // accumulator buffers (each H x STR TMEM columns)
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
 
@@ -141,13 +140,13 @@ struct Layout {
 // The query region comes first: the MMA reads 128 (x H) rows from each
 // query chunk, and rows past rows_alloc fall on the following chunk or on
 // the stage ring -- always inside the allocation, and they only feed
-// accumulator rows that nothing reads.  A stage holds the full st_rows(H)
-// rows, so the document operand (N <= st_rows) never reads past it.
-__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int H, bool f8) {
+// accumulator rows that nothing reads.  A stage holds the full super-tile
+// of str rows, so the document operand (N <= str) never reads past it.
+__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, bool f8) {
     Layout L;
     L.q_off = 0;
     L.stage_off = (qslots * nchunks * rows_alloc * 128 + 1023) & ~1023;
-    L.part_off = L.stage_off + stages * st_rows(H) * 128;
+    L.part_off = L.stage_off + stages * str * 128;
     L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
     L.st_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
     L.bar_off = L.st_off + kStRing * static_cast<int>(sizeof(StSlot));
@@ -232,18 +231,20 @@ struct Maps {
 };
 
 // H: 128-row halves of the query tile (2 for a shared group of 8 queries).
+// STR: rows per super-tile (MMA N at most): 256 with one CTA per SM, 128
+// with two (each CTA then holds kAcc x H x STR = 256 TMEM columns).
 // SH (shared mode): the launch's queries all score one candidate list; a
 // "query" of the pipeline is then a group of up to 4 H queries stacked in
 // M, so each document tile is read once per group, and the epilogue
 // writes one score per query of the group.
 // F8: rows are E4M3 codes; similarities are scaled by the document row's
 // scale before the max and by the query token's scale before the sum.
-template <int H, bool SH, bool F8>
-__global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
+template <int H, int STR, int CTAS, bool SH, bool F8>
+__global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
     constexpr int CE = chunk_elems(F8);
-    constexpr int STR = st_rows(H);
     constexpr int STAGE_BYTES = STR * 128;
-    constexpr uint32_t TCOLS = kAcc * H * STR;  // 512
+    constexpr uint32_t TCOLS = kAcc * H * STR;
+    static_assert(TCOLS * CTAS <= 512, "tensor memory of one SM");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
     const int QS = a.qslots;
     const int NCH = a.nchunks;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, H, F8);
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, F8);
 
     uint8_t* q_base = smem + L.q_off;
     uint8_t* stage_base = smem + L.stage_off;
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
                 for (int r0 = 0; r0 < len; r0 += kRows) {
                     const int r = min(kRows, len - r0);
                     const int n8 = (r + 7) & ~7;
-                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == kMaxSeg)) {
+                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == STR / 8)) {
                         if (!close_st()) {
                             aborted = true;
                             break;
@@ -790,11 +791,14 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
     }
 }
 
-// Plan shared memory, encode the tensor maps and launch dense_tc_kernel
-// (one CTA per SM: its two accumulators take all 512 TMEM columns).  F8
-// ignores `dtype` (rows are E4M3 codes; t_scales in `a`).  The caller sets
-// a.nchunks = ceil(d / chunk_elems(F8)), and a.bpc / a.qbox: per-query
-// ceil(nq / 32) and 32 bpc, shared mode the group size and 32.
+// Plan shared memory, encode the tensor maps and launch dense_tc_kernel.
+// Per-query mode prefers two CTAs per SM with 128-row super-tiles (two of
+// every pipeline role per SM); the shared schedule prefers one CTA with
+// 256-row super-tiles (more documents per MMA); a group of 8 (H = 2) takes
+// one CTA with 128-row super-tiles.  F8 ignores `dtype` (rows are E4M3
+// codes; t_scales in `a`).  The caller sets a.nchunks =
+// ceil(d / chunk_elems(F8)), and a.bpc / a.qbox: per-query ceil(nq / 32)
+// and 32 bpc, shared mode the group size and 32.
 template <int H, bool SH, bool F8>
 tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
                      const void* doc_tokens, int64_t n_tokens, Args a, cudaStream_t stream) {
@@ -810,30 +814,44 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
                                    CE, static_cast<uint32_t>(a.qbox));
     if (st != TMS_OK) return st;
-    // Shared-memory plan: as many copies of the query blocks as fit with a
-    // ring of at least 4 chunk stages (fewer copies only deal documents to
-    // fewer warps), else at least 2; within a plan the query-slot count
-    // (2, else 1) that gives the most stages.
-    auto plan = [&](int rows_alloc, int& stages, int& qslots) {
-        const int limit = std::min(kSmemLimit, dev.max_smem_optin) - 1024;
-        int best = -1;
-        for (int qs = 2; qs >= 1; --qs) {
-            const Layout L0 = make_layout(0, qs, a.nchunks, rows_alloc, H, F8);
-            const int sts = std::min(kMaxStages, (limit - L0.total) / (st_rows(H) * 128 + 16));
-            if (sts > best) {
-                best = sts;
-                stages = sts;
-                qslots = qs;
+    // Shared-memory plan for a configuration (rows per super-tile, CTAs per
+    // SM): as many copies of the query blocks as fit with a ring of at
+    // least 4 chunk stages (fewer copies only deal documents to fewer
+    // warps), else -- one CTA per SM only -- at least 2; within a plan the
+    // query-slot count (2, else 1) that gives the most stages.
+    auto plan = [&](int str, int ctas, int& stages, int& qslots, int& reps) {
+        const int limit = ctas == 2 ? dev.smem_per_sm / 2 - dev.smem_reserved - 1024
+                                    : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
+        const int max_reps = H == 2 ? 1 : (a.bpc == 3 ? 1 : 4 / a.bpc);
+        for (int need = 4; need >= (ctas == 2 ? 4 : 2); need -= 2)
+            for (int rp = max_reps; rp >= 1; rp /= 2) {
+                int best = -1;
+                for (int qs = 2; qs >= 1; --qs) {
+                    const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, F8);
+                    const int sts = std::min(kMaxStages, (limit - L0.total) / (str * 128 + 16));
+                    if (sts > best) {
+                        best = sts;
+                        stages = sts;
+                        qslots = qs;
+                    }
+                }
+                if (best >= need) {
+                    reps = rp;
+                    return true;
+                }
             }
-        }
-        return best;
+        return false;
     };
-    const int max_reps = H == 2 ? 1 : (a.bpc == 3 ? 1 : 4 / a.bpc);
-    int stages = 0, qslots = 1, reps = 0;
-    for (int need = 4; need >= 2 && reps == 0; need -= 2)
-        for (int rp = max_reps; rp >= 1 && reps == 0; rp /= 2)
-            if (plan(32 * a.bpc * rp, stages, qslots) >= need) reps = rp;
-    if (reps == 0) return TMS_ERR_UNSUPPORTED;
+    int stages = 0, qslots = 1, reps = 0, str = 0, ctas = 0;
+    if (H == 2) {
+        if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
+    } else if (!SH) {
+        if (plan(128, 2, stages, qslots, reps)) str = 128, ctas = 2;
+        else if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+    } else {
+        if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+    }
+    if (ctas == 0) return TMS_ERR_UNSUPPORTED;
     a.reps = reps;
     a.rows_alloc = 32 * a.bpc * reps;
     for (int h = 0; h < kBoxKinds; ++h) {
@@ -851,12 +869,19 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.idesc = make_idesc(128, 0, (!F8 && dtype == TMS_BF16) ? 1u : 0u);
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, H, F8);
+    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, F8);
     const int smem = L.total + 1024;
-    auto kern = dense_tc_kernel<H, SH, F8>;
+    void (*kern)(const Maps, const Args);
+    if constexpr (H == 2) {
+        kern = dense_tc_kernel<2, 128, 1, SH, F8>;
+    } else if constexpr (SH) {
+        kern = dense_tc_kernel<1, 256, 1, true, F8>;
+    } else {
+        kern = str == 128 ? dense_tc_kernel<1, 128, 2, false, F8> : dense_tc_kernel<1, 256, 1, false, F8>;
+    }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
-    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count), a.n_flat);
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
     kern<<<static_cast<unsigned>(grid), kThreads, smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
 }

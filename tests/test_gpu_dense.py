@@ -17,7 +17,7 @@ from tests._common import assert_scores_close, assert_topk_consistent, oracle_vi
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(32, 128), (1, 64), (7, 72), (33, 200), (64, 384), (128, 128), (32, 768), (16, 8), (96, 256), (96, 576),
-          (64, 512), (128, 576), (96, 768), (64, 1024)]
+          (64, 512), (128, 576), (96, 832), (64, 1024)]
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16", "f32"])
@@ -40,10 +40,10 @@ def test_dense_edge_grid(cuda_lib, dtype, nq, d):
     assert not flags & tms.TMS_DEVERR_BAD_CSR
 
 
-@pytest.mark.parametrize("nq,d", [(128, 768), (128, 640), (96, 832)])
+@pytest.mark.parametrize("nq,d", [(128, 768), (128, 640), (96, 896)])
 def test_dense_query_tile_too_large_is_unsupported(cuda_lib, nq, d):
     """The whole fp16 query tile must fit one CTA's shared memory beside two
-    32 KB stages: nq * d * 2 bytes (nq rounded to 32, d to 64) above 157,696
+    32 KB stages: nq * d * 2 bytes (nq rounded to 32, d to 64) above 161,792
     is refused with TMS_ERR_UNSUPPORTED."""
     from paper_2606_26439_gb300 import tms
     tok, off, ln = synth.dense_corpus(4, np.array([3, 4, 5, 6], np.int32), d, "f16", 9)
