@@ -663,6 +663,11 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
         uint32_t mydocs = 0;   // documents of this copy finished
         bool mine = false;
         bool aborted = false;
+        // F8: this thread's query-token scale(s), reloaded when the query changes
+        float qsc[H];
+        int qsc_q = -1;
+#pragma unroll
+        for (int h = 0; h < H; ++h) qsc[h] = 1.f;
         for (int t = 0; !aborted; ++t) {
             const int xs = t % kStRing;
             if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
@@ -678,6 +683,18 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                     ++ord;
 #pragma unroll
                     for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
+                    if (F8 && mine && si.q != qsc_q) {
+                        qsc_q = si.q;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const int b = (4 * h + qd) % a.bpc;
+                            const int qq = SH ? si.q * a.group + b : si.q;
+                            const int tok = SH ? lane : b * 32 + lane;
+                            qsc[h] = (tok < a.nq && qq < a.n_queries)
+                                         ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
+                                         : 0.f;
+                        }
+                    }
                 }
                 const int ss = tseg % kScaleRing;
                 if (!mine) {
@@ -696,11 +713,34 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                 const int c_hi = si.col + si.r;
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
-                    for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
+                    const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
+                                          static_cast<uint32_t>((ab * H + h) * STR);
+                    int c0 = c_lo & ~31;
+                    // 64 columns per load while both halves are needed and
+                    // inside this accumulator, else 32
+                    while (c0 + 32 < c_hi && c0 + 64 <= STR) {
+                        float v[64];
+                        tmem_ld64(tcol + static_cast<uint32_t>(c0), v);
+                        if (c0 < c_lo || c0 + 64 > c_hi) {
+#pragma unroll
+                            for (int c = 0; c < 64; ++c) {
+                                const bool in = c0 + c >= c_lo && c0 + c < c_hi;
+                                v[c] = in ? (F8 ? v[c] * scl[c0 + c] : v[c]) : -INFINITY;
+                            }
+                        } else if (F8) {
+#pragma unroll
+                            for (int c = 0; c < 64; ++c) v[c] *= scl[c0 + c];
+                        }
+#pragma unroll
+                        for (int o = 32; o > 0; o >>= 1)
+#pragma unroll
+                            for (int c = 0; c < o; ++c) v[c] = fmaxf(v[c], v[c + o]);
+                        rmax[h] = fmaxf(rmax[h], v[0]);
+                        c0 += 64;
+                    }
+                    if (c0 < c_hi) {
                         float v[32];
-                        tmem_ld32(tbase + (static_cast<uint32_t>(qd * 32) << 16) +
-                                      static_cast<uint32_t>((ab * H + h) * STR + c0),
-                                  v);
+                        tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
                         if (c0 < c_lo || c0 + 32 > c_hi) {
 #pragma unroll
                             for (int c = 0; c < 32; ++c) {
@@ -729,18 +769,14 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                         for (int h = 0; h < H; ++h) {
                             const int b = (4 * h + qd) % a.bpc;
                             const int qq = si.q * a.group + b;
-                            float sq = 1.f;
-                            if (F8 && lane < a.nq && qq < a.n_queries)
-                                sq = __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + lane);
-                            const float sum = warp_sum(lane < a.nq ? (F8 ? rmax[h] * sq : rmax[h]) : 0.f);
+                            const float sum = warp_sum(lane < a.nq ? (F8 ? rmax[h] * qsc[h] : rmax[h]) : 0.f);
                             if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
                         }
                     } else {
                         const int b = qd % a.bpc;
                         const int tok = b * 32 + lane;
                         float v = 0.f;
-                        if (tok < a.nq)
-                            v = F8 ? rmax[0] * __ldg(a.q_scales + static_cast<int64_t>(si.q) * a.nq + tok) : rmax[0];
+                        if (tok < a.nq) v = F8 ? rmax[0] * qsc[0] : rmax[0];
                         const float sum = warp_sum(v);
                         if (a.bpc == 1) {
                             if (lane == 0) a.out[si.f] = sum;
