@@ -77,7 +77,7 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
  * index array 16-byte aligned.  For fp16/bf16 the whole query tile stays
  * in one CTA's shared memory next to at least two 32 KB stages: with nq
  * rounded up to a multiple of 32 and d to a multiple of 64, nq * d * 2
- * bytes must not exceed 161,792 (nq > 96 at d > 576 and nq > 64 at d > 832
+ * bytes must not exceed 160,256 (nq > 96 at d > 576 and nq > 64 at d > 832
  * return TMS_ERR_UNSUPPORTED).  fp16/bf16 run on the tensor cores
  * (tcgen05, fp32 accumulation in tensor memory); fp32 runs on an exact
  * fp32 path.  A candidate with a bad id or row range scores NaN and sets

@@ -68,7 +68,9 @@ constexpr int kRows = 128;                    // document rows per tile
 __host__ __device__ constexpr int chunk_elems(bool f8) { return f8 ? 128 : 64; }
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per planner lane)
-constexpr int kStRing = 4;                    // super-tile records in flight
+// Super-tile records in flight: 8 with 256-row super-tiles (one CTA per
+// SM), 4 with 128-row ones (two CTAs per SM share the shared memory).
+__host__ __device__ constexpr int st_ring(int str) { return str == 256 ? 8 : 4; }
 constexpr int kScaleRing = 32;                // F8: tiles whose row scales are in flight or held
 constexpr int kScaleBox = 136;                // floats per scale load: 128 rows + up to 3 of 16-byte alignment
 constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a multiple of 128 B)
@@ -81,14 +83,13 @@ constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
 
 enum : int { kFirst = 1, kLast = 2, kEnd = 4, kStFirst = 8, kStLast = 16 };
 
-// One document tile inside a super-tile.
+// One document tile inside a super-tile (16 bytes).
 struct SegInfo {
-    int f;      // flat candidate index (shared mode: position in the candidate list)
-    int r;      // valid rows (1..128)
-    int q;      // query index (shared mode: group index)
-    int flags;  // kFirst / kLast of the document
-    int row0;   // token row of the tile's first row
-    int col;    // first column (row of the super-tile), a multiple of 8
+    int f;        // flat candidate index (shared mode: position in the candidate list)
+    int row0;     // token row of the tile's first row
+    short r;      // valid rows (1..128)
+    short col;    // first column (row of the super-tile), a multiple of 8
+    int flags;    // kFirst / kLast of the document
 };
 
 // One super-tile record (planner -> loader, MMA thread and epilogue).
@@ -149,8 +150,8 @@ __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunk
     L.part_off = L.stage_off + stages * str * 128;
     L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
     L.st_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
-    L.bar_off = L.st_off + kStRing * static_cast<int>(sizeof(StSlot));
-    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * kStRing + 8 + 2 * kScaleRing + 1;
+    L.bar_off = L.st_off + st_ring(str) * static_cast<int>(sizeof(StSlot));
+    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * st_ring(str) + 8 + 2 * kScaleRing + 1;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
     constexpr int CE = chunk_elems(F8);
     constexpr int STAGE_BYTES = STR * 128;
     constexpr uint32_t TCOLS = kAcc * H * STR;
+    constexpr int kStRing = st_ring(STR);
     static_assert(TCOLS * CTAS <= 512, "tensor memory of one SM");
 
     extern __shared__ uint8_t smem_raw[];
@@ -359,11 +361,10 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
             if (has) {
                 SegInfo si;
                 si.f = my_f;
-                si.r = my_r;
-                si.q = st_q;
-                si.flags = my_flags;
                 si.row0 = my_row0;
-                si.col = my_col;
+                si.r = static_cast<short>(my_r);
+                si.col = static_cast<short>(my_col);
+                si.flags = my_flags;
                 x->seg[lane] = si;
             }
             if (lane == 0) {
@@ -683,12 +684,12 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                     ++ord;
 #pragma unroll
                     for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-                    if (F8 && mine && si.q != qsc_q) {
-                        qsc_q = si.q;
+                    if (F8 && mine && xh.q != qsc_q) {
+                        qsc_q = xh.q;
 #pragma unroll
                         for (int h = 0; h < H; ++h) {
                             const int b = (4 * h + qd) % a.bpc;
-                            const int qq = SH ? si.q * a.group + b : si.q;
+                            const int qq = SH ? xh.q * a.group + b : xh.q;
                             const int tok = SH ? lane : b * 32 + lane;
                             qsc[h] = (tok < a.nq && qq < a.n_queries)
                                          ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
@@ -715,30 +716,7 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                 for (int h = 0; h < H; ++h) {
                     const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
                                           static_cast<uint32_t>((ab * H + h) * STR);
-                    int c0 = c_lo & ~31;
-                    // 64 columns per load while both halves are needed and
-                    // inside this accumulator, else 32
-                    while (c0 + 32 < c_hi && c0 + 64 <= STR) {
-                        float v[64];
-                        tmem_ld64(tcol + static_cast<uint32_t>(c0), v);
-                        if (c0 < c_lo || c0 + 64 > c_hi) {
-#pragma unroll
-                            for (int c = 0; c < 64; ++c) {
-                                const bool in = c0 + c >= c_lo && c0 + c < c_hi;
-                                v[c] = in ? (F8 ? v[c] * scl[c0 + c] : v[c]) : -INFINITY;
-                            }
-                        } else if (F8) {
-#pragma unroll
-                            for (int c = 0; c < 64; ++c) v[c] *= scl[c0 + c];
-                        }
-#pragma unroll
-                        for (int o = 32; o > 0; o >>= 1)
-#pragma unroll
-                            for (int c = 0; c < o; ++c) v[c] = fmaxf(v[c], v[c + o]);
-                        rmax[h] = fmaxf(rmax[h], v[0]);
-                        c0 += 64;
-                    }
-                    if (c0 < c_hi) {
+                    for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
                         float v[32];
                         tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
                         if (c0 < c_lo || c0 + 32 > c_hi) {
@@ -768,7 +746,7 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
 #pragma unroll
                         for (int h = 0; h < H; ++h) {
                             const int b = (4 * h + qd) % a.bpc;
-                            const int qq = si.q * a.group + b;
+                            const int qq = xh.q * a.group + b;
                             const float sum = warp_sum(lane < a.nq ? (F8 ? rmax[h] * qsc[h] : rmax[h]) : 0.f);
                             if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
                         }
@@ -828,10 +806,11 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
 }
 
 // Plan shared memory, encode the tensor maps and launch dense_tc_kernel.
-// Per-query mode prefers two CTAs per SM with 128-row super-tiles (two of
-// every pipeline role per SM); the shared schedule prefers one CTA with
-// 256-row super-tiles (more documents per MMA); a group of 8 (H = 2) takes
-// one CTA with 128-row super-tiles.  F8 ignores `dtype` (rows are E4M3
+// One CTA per SM with 256-row super-tiles (about two documents per MMA run)
+// by default; per-query lists on the FP8 store prefer two CTAs per SM with
+// 128-row super-tiles (two of every pipeline role per SM; measured faster
+// for its 128-byte rows, slower for fp16/bf16); a shared group of 8
+// (H = 2) takes one CTA with 128-row super-tiles.  F8 ignores `dtype` (rows are E4M3
 // codes; t_scales in `a`).  The caller sets a.nchunks =
 // ceil(d / chunk_elems(F8)), and a.bpc / a.qbox: per-query ceil(nq / 32)
 // and 32 bpc, shared mode the group size and 32.
@@ -881,7 +860,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     int stages = 0, qslots = 1, reps = 0, str = 0, ctas = 0;
     if (H == 2) {
         if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
-    } else if (!SH) {
+    } else if (!SH && F8) {
         if (plan(128, 2, stages, qslots, reps)) str = 128, ctas = 2;
         else if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
     } else {
@@ -910,10 +889,10 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {
         kern = dense_tc_kernel<2, 128, 1, SH, F8>;
-    } else if constexpr (SH) {
-        kern = dense_tc_kernel<1, 256, 1, true, F8>;
+    } else if constexpr (SH || !F8) {
+        kern = dense_tc_kernel<1, 256, 1, SH, F8>;
     } else {
-        kern = str == 128 ? dense_tc_kernel<1, 128, 2, false, F8> : dense_tc_kernel<1, 256, 1, false, F8>;
+        kern = str == 128 ? dense_tc_kernel<1, 128, 2, false, true> : dense_tc_kernel<1, 256, 1, false, true>;
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);

@@ -43,7 +43,7 @@ def test_dense_edge_grid(cuda_lib, dtype, nq, d):
 @pytest.mark.parametrize("nq,d", [(128, 768), (128, 640), (96, 896)])
 def test_dense_query_tile_too_large_is_unsupported(cuda_lib, nq, d):
     """The whole fp16 query tile must fit one CTA's shared memory beside two
-    32 KB stages: nq * d * 2 bytes (nq rounded to 32, d to 64) above 161,792
+    32 KB stages: nq * d * 2 bytes (nq rounded to 32, d to 64) above 160,256
     is refused with TMS_ERR_UNSUPPORTED."""
     from paper_2606_26439_gb300 import tms
     tok, off, ln = synth.dense_corpus(4, np.array([3, 4, 5, 6], np.int32), d, "f16", 9)
