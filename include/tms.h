@@ -6,10 +6,10 @@
  *     computed without materialising the Nq x Nd similarity matrix
  *     (Section 3, Algorithm 3 "V2-MQ"), with the embedding dimension
  *     tiled into chunks whose partial dot products are summed before the
- *     max (Section 3, dimension tiling; Section 6.6, Table dim_scaling);
+ *     max (Section 3, dimension tiling; Section 6.8, Table dim_scaling);
  *   - the PQ distance table (Section 4.2, Phase 1) and fused PQ scoring
  *     through it without decompression (Section 4.2, Phase 2);
- *   - top-k selection after scoring (Section 6.6, end-to-end retrieval).
+ *   - top-k selection after scoring (Section 6.8, end-to-end retrieval latency).
  *
  * Conventions shared by every entry point:
  *   - All array arguments are DEVICE pointers on the current CUDA device,
@@ -92,7 +92,7 @@ tms_status tms_score_dense(const void *queries, tms_dtype dtype, int n_queries, 
 /*
  * Dense MaxSim of n_queries queries that all score ONE candidate list
  * (e.g. every query over the whole corpus, the dimension-scaling workload
- * of Section 6.6).  Same arithmetic as tms_score_dense, but queries are
+ * of Section 6.8).  Same arithmetic as tms_score_dense, but queries are
  * processed in groups of up to 8 stacked in the tensor-core N dimension,
  * so each document tile is read from HBM once per group instead of once
  * per query (Theorem 1 with BQ = 32 x group).
@@ -204,7 +204,7 @@ tms_status tms_score_pq(const float *lut, int n_queries, int nq, int m, int k,
                         float *out_scores, cudaStream_t stream);
 
 /*
- * Top-k per query over scores laid out like out_scores above (Section 6.6).
+ * Top-k per query over scores laid out like out_scores above (Section 6.8).
  *
  *   scores        [n_cand] fp32, query q's list at cand_offsets[q]..[q+1].
  *   out_scores    [n_queries][topk] fp32;  out_pos [n_queries][topk] int32:

@@ -11,7 +11,7 @@ arrays into it.  Each function names the definition it follows:
 * :func:`pq_decompress_scores` -- Section 4.1, decompress then Eq. 1.
 * :func:`pq_lut`             -- Section 4.2, the distance table T.
 * :func:`pq_lut_scores`      -- Section 4.2 Phase 2, sum of table entries.
-* :func:`topk`               -- Section 6.6, top-k after scoring.
+* :func:`topk`               -- Section 6.8, top-k after scoring.
 
 Element types are passed as the stored bits: fp16 and bf16 arrays are
 given as ``uint16`` bit patterns with an explicit dtype code, fp32 as ``float32``, and

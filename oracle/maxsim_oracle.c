@@ -22,10 +22,10 @@
  *   - PQ distance table (Section 4.2):
  *         T[i][m][k] = q_i[m*dsub : (m+1)*dsub] . C[m][k]
  *     and the approximate similarity  q_i . d^_j = sum_m T[i][m][code_{j,m}].
- *   - Top-k after scoring (Section 6.6, end-to-end retrieval): the k largest
+ *   - Top-k after scoring (Section 6.8, end-to-end retrieval latency): the k largest
  *     scores of a query's candidate list.
- *   - A per-token scaled FP8 store (an extension of Section 6.6's precision
- *     discussion; the paper itself scores fp16/bf16): each stored row is
+ *   - A per-token scaled FP8 store (not part of the paper, which scores
+ *     fp16 inputs with fp32 accumulation, Section 6.1): each stored row is
  *     E4M3 codes with one fp32 scale, the vector it stands for is
  *     scale * decode(codes), and MaxSim is Eq. 1 on those vectors -- the
  *     row scale multiplies each similarity before the max.

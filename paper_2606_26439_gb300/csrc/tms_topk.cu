@@ -1,4 +1,4 @@
-// tms_topk.cu -- per-query top-k after scoring (Section 6.6).
+// tms_topk.cu -- per-query top-k after scoring (Section 6.8, end-to-end retrieval latency).
 //
 // One 1024-thread CTA per query:
 //   1. scores map to order-preserving 32-bit keys (NaN lowest, -0 == +0);

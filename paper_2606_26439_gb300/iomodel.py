@@ -5,7 +5,7 @@ measured time into achieved GB/s and TFLOP/s:
 
 * :func:`flops_paper` -- Section 2.3, Eq. "flops": B Nq Nd (2d + 1).
 * :func:`flops_dot`   -- the 2 B Nq Nd d dot-product FLOPs the paper's
-  profiling table (Section 6.5) divides by time.
+  profiling table (Section 6.7) divides by time.
 * :func:`io_naive`    -- Section 2.3, Eq. "io_naive": Q, D and a written and
   re-read fp32 similarity matrix.
 * :func:`io_fused`    -- Section 2.3, Eq. "io_flash" (output counted as
