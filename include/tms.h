@@ -52,7 +52,8 @@ typedef enum {
     TMS_ERR_UNSUPPORTED = -2, /* valid, but outside this build's limits     */
     TMS_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed        */
     TMS_ERR_DEVICE_FLAG = -5, /* tms_get_device_error found flags set       */
-    TMS_ERR_TIMEOUT = -6      /* a bounded device-side wait ran out         */
+    TMS_ERR_TIMEOUT = -6,     /* a bounded wait ran out                      */
+    TMS_ERR_BUSY = -7         /* admission refused: too many pending requests */
 } tms_status;
 
 typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
@@ -217,6 +218,93 @@ tms_status tms_score_pq(const float *lut, int n_queries, int nq, int m, int k,
  */
 tms_status tms_topk(const float *scores, const int64_t *cand_offsets, int n_queries, int topk,
                     float *out_scores, int32_t *out_pos, cudaStream_t stream);
+
+/*
+ * Serving loop: a device-resident corpus (a dense store and optionally a PQ
+ * store) and a worker thread that scores requests -- one query of nq tokens
+ * against its own candidate list, top-k back to the host -- with continuous
+ * batching: every launch takes all pending requests that fit the batch
+ * buffers, requests arriving meanwhile go into the next launch, and the
+ * host side of one batch (staging, completion) overlaps the GPU work of the
+ * next.  Scores come from tms_score_dense / tms_score_pq and tms_topk, whose
+ * results do not depend on the batch they run in: a request's result is
+ * bitwise the same alone and in any mix.
+ *
+ * The config's device pointers are owned by the caller and must stay valid
+ * until tms_server_destroy; the server owns its own batch buffers (device
+ * and pinned host memory, allocated in tms_server_create).  Host pointers
+ * passed to submit are copied before it returns.
+ */
+typedef struct tms_server tms_server;
+
+typedef enum { TMS_STORE_DENSE = 0, TMS_STORE_PQ = 1 } tms_store;
+
+typedef struct {
+    /* dense store (required), as for tms_score_dense */
+    const void *doc_tokens;
+    tms_dtype dtype;            /* TMS_F16 or TMS_BF16 */
+    int d;
+    int64_t n_tokens;
+    const int64_t *doc_offsets;
+    const int32_t *doc_lengths;
+    int64_t n_docs;
+    /* PQ store (optional: pq_codes == NULL for none), as for tms_score_pq;
+     * queries of PQ requests have the dense store's dtype and d */
+    const uint8_t *pq_codes;
+    const float *pq_codebook;   /* [pq_m][pq_k][d / pq_m] fp32 */
+    int pq_m;
+    int pq_k;
+    int64_t pq_n_tokens;
+    const int64_t *pq_offsets;
+    const int32_t *pq_lengths;
+    int64_t pq_n_docs;
+    /* requests */
+    int nq;                        /* query tokens per request, 1..128 */
+    int topk;                      /* results per request, 1..1024 */
+    int max_batch_requests;        /* requests per launch, 1..4096 (1 = no batching) */
+    int64_t max_batch_candidates;  /* candidates per launch (all requests), >= 1 */
+    int max_pending;               /* admitted but unfinished requests, >= 1 */
+    int inject_error_batch;        /* test hook: > 0 fails that batch (1-based) on the host, 0 = off */
+} tms_server_config;
+
+typedef struct {
+    uint64_t requests;     /* completed */
+    uint64_t batches;      /* launches */
+    uint64_t candidates;   /* scored */
+    uint64_t rejected;     /* refused by admission */
+} tms_server_stats;
+
+/* Create the server and start its worker on the current device.  Returns
+ * TMS_ERR_INVALID_ARG for a bad config, TMS_ERR_CUDA if the buffers cannot
+ * be allocated. */
+tms_status tms_server_create(const tms_server_config *cfg, tms_server **out);
+
+/*
+ * Submit one request (HOST pointers, copied): query [nq][d] of the dense
+ * store's dtype, cand_ids [n_cand] document ids of `store`.  *ticket
+ * receives its handle.  Returns TMS_ERR_BUSY when max_pending requests are
+ * unfinished, TMS_ERR_UNSUPPORTED when n_cand exceeds max_batch_candidates
+ * or the PQ store is absent.
+ */
+tms_status tms_server_submit(tms_server *s, tms_store store, const void *query, const int32_t *cand_ids,
+                             int64_t n_cand, uint64_t *ticket);
+
+/*
+ * Wait (at most timeout_s seconds) for a request and take its result (HOST
+ * pointers): out_scores [topk] fp32 and out_ids [topk] int32 document ids,
+ * ordered as tms_topk orders them (ids -1 past the list's end);
+ * *latency_s (may be NULL) receives submit-to-completion time.  Returns the
+ * request's status (TMS_ERR_CUDA if its batch failed), TMS_ERR_TIMEOUT if
+ * it is not done in time (it stays waitable), TMS_ERR_INVALID_ARG for an
+ * unknown ticket.
+ */
+tms_status tms_server_wait(tms_server *s, uint64_t ticket, double timeout_s, float *out_scores, int32_t *out_ids,
+                           double *latency_s);
+
+tms_status tms_server_get_stats(tms_server *s, tms_server_stats *out);
+
+/* Finish every admitted request, stop the worker and free the server. */
+tms_status tms_server_destroy(tms_server *s);
 
 /*
  * Read and clear the current device's error word after `stream` drains.

@@ -128,7 +128,8 @@ const char* tms_status_string(tms_status s) {
         case TMS_ERR_UNSUPPORTED: return "unsupported shape for this build";
         case TMS_ERR_CUDA: return "CUDA runtime or launch error";
         case TMS_ERR_DEVICE_FLAG: return "device-side data error flagged";
-        case TMS_ERR_TIMEOUT: return "device-side wait timed out";
+        case TMS_ERR_TIMEOUT: return "bounded wait timed out";
+        case TMS_ERR_BUSY: return "admission refused: too many pending requests";
     }
     return "unknown status";
 }

@@ -1,0 +1,387 @@
+// tms_server.cu -- the serving loop: continuous batching of MaxSim requests
+// over a device-resident corpus (a dense store and optionally a PQ store).
+//
+// One worker thread per server.  Each turn it takes every pending request
+// that fits the batch buffers (FIFO), stages their queries and candidate
+// lists in pinned memory, and enqueues on its own stream: the host-to-
+// device copies, tms_score_dense (dense requests) or tms_build_pq_lut +
+// tms_score_pq (PQ requests), tms_topk, and the device-to-host copy of the
+// top-k.  Two buffer slots alternate, so while the GPU runs one batch the
+// worker completes the previous one and stages the next: requests that
+// arrive during a launch go into the following one (continuous batching).
+// Batch composition never changes a result: every score has one owner and
+// a fixed summation order, and the top-k of a request reads only its own
+// scores.
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tms_internal.h"
+
+namespace tms {
+
+namespace server {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    int store = 0;
+    std::vector<uint8_t> query;
+    std::vector<int32_t> cands;
+    std::vector<float> scores;
+    std::vector<int32_t> ids;
+    tms_status status = TMS_OK;
+    bool done = false;
+    Clock::time_point t_submit, t_done;
+};
+
+using RequestPtr = std::shared_ptr<Request>;
+
+// Buffers of one batch in flight, per store (0 dense, 1 PQ).
+struct Slot {
+    void* h_q[2] = {nullptr, nullptr};
+    int32_t* h_c[2] = {nullptr, nullptr};
+    int64_t* h_co[2] = {nullptr, nullptr};
+    float* h_ts[2] = {nullptr, nullptr};
+    int32_t* h_tp[2] = {nullptr, nullptr};
+    void* d_q[2] = {nullptr, nullptr};
+    int32_t* d_c[2] = {nullptr, nullptr};
+    int64_t* d_co[2] = {nullptr, nullptr};
+    float* d_sc[2] = {nullptr, nullptr};
+    float* d_ts[2] = {nullptr, nullptr};
+    int32_t* d_tp[2] = {nullptr, nullptr};
+    float* d_lut = nullptr;
+    cudaEvent_t done = nullptr;
+    std::vector<RequestPtr> reqs[2];
+    tms_status status = TMS_OK;
+};
+
+}  // namespace server
+
+}  // namespace tms
+
+struct tms_server {
+    tms_server_config cfg;
+    int device = 0;
+    size_t qbytes = 0;  // bytes of one query
+    cudaStream_t stream = nullptr;
+    tms::server::Slot slots[2];
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<tms::server::RequestPtr> pending;
+    std::unordered_map<uint64_t, tms::server::RequestPtr> live;  // admitted, result not yet taken
+    uint64_t next_ticket = 1;
+    int unfinished = 0;
+    bool stop = false;
+    uint64_t batch_ordinal = 0;
+    tms_server_stats stats{};
+    std::thread worker;
+};
+
+namespace tms {
+
+namespace server {
+
+inline bool cuda_ok(cudaError_t e) {
+    if (e == cudaSuccess) return true;
+    (void)cudaGetLastError();
+    return false;
+}
+
+bool alloc_slot(tms_server* s, Slot& sl) {
+    const tms_server_config& c = s->cfg;
+    const size_t nb = static_cast<size_t>(c.max_batch_requests);
+    const size_t nc = static_cast<size_t>(c.max_batch_candidates);
+    const int stores = c.pq_codes ? 2 : 1;
+    for (int st = 0; st < stores; ++st) {
+        if (!cuda_ok(cudaMallocHost(&sl.h_q[st], nb * s->qbytes)) ||
+            !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_c[st]), nc * 4)) ||
+            !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_co[st]), (nb + 1) * 8)) ||
+            !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_ts[st]), nb * c.topk * 4)) ||
+            !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_tp[st]), nb * c.topk * 4)) ||
+            !cuda_ok(cudaMalloc(&sl.d_q[st], nb * s->qbytes)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_c[st]), nc * 4)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_co[st]), (nb + 1) * 8)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_sc[st]), nc * 4)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_ts[st]), nb * c.topk * 4)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_tp[st]), nb * c.topk * 4)))
+            return false;
+    }
+    if (c.pq_codes &&
+        !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_lut),
+                            nb * static_cast<size_t>(c.nq) * c.pq_m * c.pq_k * 4)))
+        return false;
+    return cuda_ok(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+}
+
+void free_slot(Slot& sl) {
+    for (int st = 0; st < 2; ++st) {
+        cudaFreeHost(sl.h_q[st]);
+        cudaFreeHost(sl.h_c[st]);
+        cudaFreeHost(sl.h_co[st]);
+        cudaFreeHost(sl.h_ts[st]);
+        cudaFreeHost(sl.h_tp[st]);
+        cudaFree(sl.d_q[st]);
+        cudaFree(sl.d_c[st]);
+        cudaFree(sl.d_co[st]);
+        cudaFree(sl.d_sc[st]);
+        cudaFree(sl.d_ts[st]);
+        cudaFree(sl.d_tp[st]);
+    }
+    cudaFree(sl.d_lut);
+    if (sl.done) cudaEventDestroy(sl.done);
+    (void)cudaGetLastError();
+}
+
+// Stage a batch into `sl` and enqueue its work; the result lands in the
+// slot's pinned buffers when sl.done completes.
+void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
+    const tms_server_config& c = s->cfg;
+    sl.reqs[0].clear();
+    sl.reqs[1].clear();
+    for (auto& r : batch) sl.reqs[r->store].push_back(r);
+    sl.status = TMS_OK;
+    const bool inject = c.inject_error_batch > 0 && s->batch_ordinal == static_cast<uint64_t>(c.inject_error_batch);
+    for (int st = 0; st < 2 && !inject; ++st) {
+        const int nb = static_cast<int>(sl.reqs[st].size());
+        if (nb == 0) continue;
+        int64_t total = 0;
+        sl.h_co[st][0] = 0;
+        for (int i = 0; i < nb; ++i) {
+            const Request& r = *sl.reqs[st][i];
+            std::memcpy(static_cast<uint8_t*>(sl.h_q[st]) + i * s->qbytes, r.query.data(), s->qbytes);
+            if (!r.cands.empty()) std::memcpy(sl.h_c[st] + total, r.cands.data(), r.cands.size() * 4);
+            total += static_cast<int64_t>(r.cands.size());
+            sl.h_co[st][i + 1] = total;
+        }
+        tms_status rc = TMS_OK;
+        if (!cuda_ok(cudaMemcpyAsync(sl.d_q[st], sl.h_q[st], nb * s->qbytes, cudaMemcpyHostToDevice, s->stream)) ||
+            !cuda_ok(cudaMemcpyAsync(sl.d_c[st], sl.h_c[st], total * 4, cudaMemcpyHostToDevice, s->stream)) ||
+            !cuda_ok(cudaMemcpyAsync(sl.d_co[st], sl.h_co[st], (nb + 1) * 8, cudaMemcpyHostToDevice, s->stream)))
+            rc = TMS_ERR_CUDA;
+        if (rc == TMS_OK && st == 0)
+            rc = tms_score_dense(sl.d_q[st], c.dtype, nb, c.nq, c.d, c.doc_tokens, c.n_tokens, c.doc_offsets,
+                                 c.doc_lengths, c.n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st], s->stream);
+        if (rc == TMS_OK && st == 1) {
+            rc = tms_build_pq_lut(sl.d_q[st], c.dtype, nb, c.nq, c.d, c.pq_codebook, c.pq_m, c.pq_k, sl.d_lut,
+                                  s->stream);
+            if (rc == TMS_OK)
+                rc = tms_score_pq(sl.d_lut, nb, c.nq, c.pq_m, c.pq_k, c.pq_codes, c.pq_n_tokens, c.pq_offsets,
+                                  c.pq_lengths, c.pq_n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st], s->stream);
+        }
+        if (rc == TMS_OK) rc = tms_topk(sl.d_sc[st], sl.d_co[st], nb, c.topk, sl.d_ts[st], sl.d_tp[st], s->stream);
+        if (rc == TMS_OK &&
+            (!cuda_ok(cudaMemcpyAsync(sl.h_ts[st], sl.d_ts[st], static_cast<size_t>(nb) * c.topk * 4,
+                                      cudaMemcpyDeviceToHost, s->stream)) ||
+             !cuda_ok(cudaMemcpyAsync(sl.h_tp[st], sl.d_tp[st], static_cast<size_t>(nb) * c.topk * 4,
+                                      cudaMemcpyDeviceToHost, s->stream))))
+            rc = TMS_ERR_CUDA;
+        if (rc != TMS_OK) sl.status = rc;
+    }
+    if (inject) sl.status = TMS_ERR_CUDA;
+    if (!cuda_ok(cudaEventRecord(sl.done, s->stream))) sl.status = TMS_ERR_CUDA;
+}
+
+// Wait for a slot's batch and hand each request its result.
+void complete(tms_server* s, Slot& sl) {
+    const tms_server_config& c = s->cfg;
+    if (!cuda_ok(cudaEventSynchronize(sl.done)) && sl.status == TMS_OK) sl.status = TMS_ERR_CUDA;
+    const Clock::time_point now = Clock::now();
+    uint64_t n = 0, cands = 0;
+    for (int st = 0; st < 2; ++st) {
+        for (size_t i = 0; i < sl.reqs[st].size(); ++i) {
+            Request& r = *sl.reqs[st][i];
+            r.status = sl.status;
+            r.scores.assign(c.topk, -INFINITY);
+            r.ids.assign(c.topk, -1);
+            if (sl.status == TMS_OK) {
+                const float* ts = sl.h_ts[st] + i * c.topk;
+                const int32_t* tp = sl.h_tp[st] + i * c.topk;
+                for (int j = 0; j < c.topk; ++j) {
+                    r.scores[j] = ts[j];
+                    r.ids[j] = (tp[j] >= 0 && static_cast<size_t>(tp[j]) < r.cands.size()) ? r.cands[tp[j]] : -1;
+                }
+            }
+            r.t_done = now;
+            cands += r.cands.size();
+            ++n;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int st = 0; st < 2; ++st)
+            for (auto& r : sl.reqs[st]) r->done = true;
+        s->unfinished -= static_cast<int>(n);
+        s->stats.requests += n;
+        s->stats.candidates += cands;
+    }
+    sl.reqs[0].clear();
+    sl.reqs[1].clear();
+    s->cv_done.notify_all();
+}
+
+void worker_main(tms_server* s) {
+    cudaSetDevice(s->device);
+    bool inflight[2] = {false, false};
+    int cur = 0;
+    for (;;) {
+        std::vector<RequestPtr> batch;
+        bool quit = false;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            const bool busy = inflight[cur ^ 1];
+            if (!busy) s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
+            int64_t cands = 0;
+            while (!s->pending.empty() && static_cast<int>(batch.size()) < s->cfg.max_batch_requests) {
+                const RequestPtr& r = s->pending.front();
+                const int64_t n = static_cast<int64_t>(r->cands.size());
+                if (!batch.empty() && cands + n > s->cfg.max_batch_candidates) break;
+                cands += n;
+                batch.push_back(r);
+                s->pending.pop_front();
+            }
+            if (!batch.empty()) {
+                ++s->batch_ordinal;
+                ++s->stats.batches;
+            }
+            quit = batch.empty() && !busy && s->stop;
+        }
+        if (quit) break;
+        if (!batch.empty()) launch(s, s->slots[cur], batch);
+        if (inflight[cur ^ 1]) {
+            complete(s, s->slots[cur ^ 1]);
+            inflight[cur ^ 1] = false;
+        }
+        if (!batch.empty()) {
+            inflight[cur] = true;
+            cur ^= 1;
+        }
+    }
+}
+
+bool config_ok(const tms_server_config& c) {
+    if (c.dtype != TMS_F16 && c.dtype != TMS_BF16) return false;
+    if (!c.doc_tokens || !c.doc_offsets || !c.doc_lengths || c.n_docs < 1 || c.n_tokens < 1) return false;
+    if (c.d < 8 || c.d > 1024 || c.d % 8 != 0) return false;
+    if (c.nq < 1 || c.nq > 128 || c.topk < 1 || c.topk > 1024) return false;
+    if (c.max_batch_requests < 1 || c.max_batch_requests > 4096 || c.max_batch_candidates < 1 ||
+        c.max_batch_candidates >= (int64_t(1) << 31) || c.max_pending < 1 || c.inject_error_batch < 0)
+        return false;
+    if (c.pq_codes) {
+        if (!c.pq_codebook || !c.pq_offsets || !c.pq_lengths || c.pq_n_docs < 1 || c.pq_n_tokens < 1) return false;
+        if (c.pq_m != 4 && c.pq_m != 8 && c.pq_m != 16 && c.pq_m != 32) return false;
+        if (c.pq_k < 1 || c.pq_k > 256 || c.pq_m * c.pq_k > 4096 || c.d % c.pq_m != 0) return false;
+    }
+    return true;
+}
+
+void destroy(tms_server* s) {
+    for (auto& sl : s->slots) free_slot(sl);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    (void)cudaGetLastError();
+    delete s;
+}
+
+}  // namespace server
+
+}  // namespace tms
+
+extern "C" tms_status tms_server_create(const tms_server_config* cfg, tms_server** out) {
+    using namespace tms::server;
+    if (!cfg || !out || !config_ok(*cfg)) return TMS_ERR_INVALID_ARG;
+    tms_server* s = new (std::nothrow) tms_server();
+    if (!s) return TMS_ERR_CUDA;
+    s->cfg = *cfg;
+    s->qbytes = static_cast<size_t>(cfg->nq) * cfg->d * 2;
+    if (!cuda_ok(cudaGetDevice(&s->device)) || !cuda_ok(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) ||
+        !alloc_slot(s, s->slots[0]) || !alloc_slot(s, s->slots[1])) {
+        destroy(s);
+        return TMS_ERR_CUDA;
+    }
+    try {
+        s->worker = std::thread(worker_main, s);
+    } catch (...) {
+        destroy(s);
+        return TMS_ERR_CUDA;
+    }
+    *out = s;
+    return TMS_OK;
+}
+
+extern "C" tms_status tms_server_submit(tms_server* s, tms_store store, const void* query, const int32_t* cand_ids,
+                                        int64_t n_cand, uint64_t* ticket) {
+    using namespace tms::server;
+    if (!s || !query || !ticket || n_cand < 0 || (n_cand > 0 && !cand_ids)) return TMS_ERR_INVALID_ARG;
+    if (store != TMS_STORE_DENSE && store != TMS_STORE_PQ) return TMS_ERR_INVALID_ARG;
+    if (store == TMS_STORE_PQ && !s->cfg.pq_codes) return TMS_ERR_UNSUPPORTED;
+    if (n_cand > s->cfg.max_batch_candidates) return TMS_ERR_UNSUPPORTED;
+    auto r = std::make_shared<Request>();
+    r->store = store;
+    r->query.assign(static_cast<const uint8_t*>(query), static_cast<const uint8_t*>(query) + s->qbytes);
+    r->cands.assign(cand_ids, cand_ids + n_cand);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return TMS_ERR_INVALID_ARG;
+        if (s->unfinished >= s->cfg.max_pending) {
+            ++s->stats.rejected;
+            return TMS_ERR_BUSY;
+        }
+        r->ticket = s->next_ticket++;
+        s->pending.push_back(r);
+        s->live.emplace(r->ticket, r);
+        ++s->unfinished;
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_one();
+    return TMS_OK;
+}
+
+extern "C" tms_status tms_server_wait(tms_server* s, uint64_t ticket, double timeout_s, float* out_scores,
+                                      int32_t* out_ids, double* latency_s) {
+    using namespace tms::server;
+    if (!s || !out_scores || !out_ids || !(timeout_s >= 0.0)) return TMS_ERR_INVALID_ARG;
+    RequestPtr r;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->live.find(ticket);
+        if (it == s->live.end()) return TMS_ERR_INVALID_ARG;
+        r = it->second;
+        const auto limit = std::chrono::duration<double>(timeout_s > 1e6 ? 1e6 : timeout_s);
+        if (!s->cv_done.wait_for(lk, limit, [&] { return r->done; })) return TMS_ERR_TIMEOUT;
+        s->live.erase(it);
+    }
+    std::memcpy(out_scores, r->scores.data(), r->scores.size() * 4);
+    std::memcpy(out_ids, r->ids.data(), r->ids.size() * 4);
+    if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    return r->status;
+}
+
+extern "C" tms_status tms_server_get_stats(tms_server* s, tms_server_stats* out) {
+    if (!s || !out) return TMS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    return TMS_OK;
+}
+
+extern "C" tms_status tms_server_destroy(tms_server* s) {
+    using namespace tms::server;
+    if (!s) return TMS_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    destroy(s);
+    return TMS_OK;
+}

@@ -20,6 +20,7 @@ TMS_ERR_UNSUPPORTED = -2
 TMS_ERR_CUDA = -3
 TMS_ERR_DEVICE_FLAG = -5
 TMS_ERR_TIMEOUT = -6
+TMS_ERR_BUSY = -7
 
 TMS_F16, TMS_BF16, TMS_F32 = 0, 1, 2
 
@@ -30,8 +31,31 @@ TMS_DEVERR_BAD_CSR = 8
 
 #: every symbol include/tms.h declares
 EXPORTS = ("tms_score_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
-           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk", "tms_get_device_error",
-           "tms_status_string", "tms_version")
+           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk", "tms_server_create",
+           "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy",
+           "tms_get_device_error", "tms_status_string", "tms_version")
+
+TMS_STORE_DENSE, TMS_STORE_PQ = 0, 1
+
+
+class ServerConfig(ctypes.Structure):
+    """Mirror of tms_server_config (include/tms.h)."""
+    _fields_ = [
+        ("doc_tokens", ctypes.c_void_p), ("dtype", ctypes.c_int), ("d", ctypes.c_int),
+        ("n_tokens", ctypes.c_int64), ("doc_offsets", ctypes.c_void_p), ("doc_lengths", ctypes.c_void_p),
+        ("n_docs", ctypes.c_int64),
+        ("pq_codes", ctypes.c_void_p), ("pq_codebook", ctypes.c_void_p), ("pq_m", ctypes.c_int),
+        ("pq_k", ctypes.c_int), ("pq_n_tokens", ctypes.c_int64), ("pq_offsets", ctypes.c_void_p),
+        ("pq_lengths", ctypes.c_void_p), ("pq_n_docs", ctypes.c_int64),
+        ("nq", ctypes.c_int), ("topk", ctypes.c_int), ("max_batch_requests", ctypes.c_int),
+        ("max_batch_candidates", ctypes.c_int64), ("max_pending", ctypes.c_int),
+        ("inject_error_batch", ctypes.c_int),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64)]
 
 _lib = None
 _lock = threading.Lock()
@@ -66,13 +90,20 @@ def lib(build_if_missing: bool = True):
             L.tms_build_pq_lut.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _p]
             L.tms_score_pq.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
             L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
+            L.tms_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
+            L.tms_server_submit.argtypes = [_p, _i32, _p, _p, _i64, ctypes.POINTER(ctypes.c_uint64)]
+            L.tms_server_wait.argtypes = [_p, ctypes.c_uint64, ctypes.c_double, _p, _p,
+                                          ctypes.POINTER(ctypes.c_double)]
+            L.tms_server_get_stats.argtypes = [_p, ctypes.POINTER(ServerStats)]
+            L.tms_server_destroy.argtypes = [_p]
             L.tms_get_device_error.argtypes = [_p, ctypes.POINTER(ctypes.c_int)]
             L.tms_status_string.argtypes = [_i32]
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
             for name in ("tms_score_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
                          "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
-                         "tms_get_device_error", "tms_version"):
+                         "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
+                         "tms_server_destroy", "tms_get_device_error", "tms_version"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -296,3 +327,82 @@ def device_error(stream=None) -> int:
     if st not in (TMS_OK, TMS_ERR_DEVICE_FLAG):
         raise TmsError("tms_get_device_error", st)
     return flags
+
+
+# --------------------------------------------------------------- serving
+
+class Server:
+    """Serving loop over a device-resident dense store (and optional PQ
+    store): submit requests from the host, wait for their top-k.  The
+    config's device tensors must outlive the server."""
+
+    def __init__(self, doc_tokens, doc_offsets, doc_lengths, nq, topk, max_batch_requests,
+                 max_batch_candidates, max_pending, pq=None, inject_error_batch=0):
+        torch = _torch()
+        cfg = ServerConfig()
+        cfg.doc_tokens = _dev(doc_tokens)
+        cfg.dtype = _dtype_code(doc_tokens)
+        cfg.d = doc_tokens.shape[1]
+        cfg.n_tokens = doc_tokens.shape[0]
+        cfg.doc_offsets = _dev(doc_offsets, torch.int64)
+        cfg.doc_lengths = _dev(doc_lengths, torch.int32)
+        cfg.n_docs = doc_offsets.shape[0]
+        if pq is not None:
+            codes, codebook, offsets, lengths = pq
+            cfg.pq_codes = _dev(codes, torch.uint8)
+            cfg.pq_codebook = _dev(codebook, torch.float32)
+            cfg.pq_m, cfg.pq_k = codebook.shape[0], codebook.shape[1]
+            cfg.pq_n_tokens = codes.shape[0]
+            cfg.pq_offsets = _dev(offsets, torch.int64)
+            cfg.pq_lengths = _dev(lengths, torch.int32)
+            cfg.pq_n_docs = offsets.shape[0]
+        cfg.nq, cfg.topk = nq, topk
+        cfg.max_batch_requests = max_batch_requests
+        cfg.max_batch_candidates = max_batch_candidates
+        cfg.max_pending = max_pending
+        cfg.inject_error_batch = inject_error_batch
+        self.topk = topk
+        self.qshape = (nq, cfg.d)
+        self.qdtype = doc_tokens.dtype
+        h = ctypes.c_void_p()
+        _check("tms_server_create", lib().tms_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, query, cand_ids, store=TMS_STORE_DENSE):
+        """query: host tensor [nq][d] of the store dtype; cand_ids: int32 numpy array."""
+        import numpy as np
+        q = query.contiguous()
+        if tuple(q.shape) != self.qshape or q.dtype != self.qdtype or q.is_cuda:
+            raise ValueError("query must be a host tensor of the store's dtype and shape [nq][d]")
+        c = np.ascontiguousarray(cand_ids, dtype=np.int32)
+        t = ctypes.c_uint64()
+        _check("tms_server_submit", lib().tms_server_submit(self._h, store, q.data_ptr(), c.ctypes.data,
+                                                            c.shape[0], ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket, timeout_s=60.0):
+        """(scores [topk] fp32, ids [topk] int32, latency seconds); raises TmsError on failure."""
+        import numpy as np
+        sc = np.empty(self.topk, np.float32)
+        ids = np.empty(self.topk, np.int32)
+        lat = ctypes.c_double()
+        _check("tms_server_wait", lib().tms_server_wait(self._h, ticket, timeout_s, sc.ctypes.data, ids.ctypes.data,
+                                                        ctypes.byref(lat)))
+        return sc, ids, lat.value
+
+    def stats(self):
+        st = ServerStats()
+        _check("tms_server_get_stats", lib().tms_server_get_stats(self._h, ctypes.byref(st)))
+        return {"requests": st.requests, "batches": st.batches, "candidates": st.candidates,
+                "rejected": st.rejected}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check("tms_server_destroy", lib().tms_server_destroy(self._h))
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

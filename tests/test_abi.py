@@ -91,3 +91,25 @@ def test_topk_rejects_bad_k(lib, k):
 
 def test_get_device_error_rejects_null(lib):
     assert lib.tms_get_device_error(None, ctypes.POINTER(ctypes.c_int)()) == tms.TMS_ERR_INVALID_ARG
+
+
+def test_server_rejects_bad_config(lib):
+    """Config checks happen before any device call (runs without a GPU)."""
+    cfg = tms.ServerConfig()
+    h = ctypes.c_void_p()
+    assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG
+    cfg.doc_tokens, cfg.doc_offsets, cfg.doc_lengths = DUMMY, DUMMY, DUMMY
+    cfg.dtype, cfg.d, cfg.n_tokens, cfg.n_docs = tms.TMS_F16, 128, 100, 10
+    cfg.nq, cfg.topk, cfg.max_batch_requests, cfg.max_batch_candidates, cfg.max_pending = 32, 10, 8, 1000, 16
+    for field, bad in (("nq", 0), ("topk", 1025), ("max_batch_requests", 0), ("max_pending", 0), ("d", 12),
+                       ("dtype", tms.TMS_F32), ("inject_error_batch", -1)):
+        good = getattr(cfg, field)
+        setattr(cfg, field, bad)
+        assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG, field
+        setattr(cfg, field, good)
+    cfg.pq_codes, cfg.pq_codebook, cfg.pq_offsets, cfg.pq_lengths = DUMMY, DUMMY, DUMMY, DUMMY
+    cfg.pq_n_tokens, cfg.pq_n_docs, cfg.pq_k = 100, 10, 256
+    cfg.pq_m = 12  # unsupported subspace count
+    assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG
+    assert lib.tms_server_destroy(None) == tms.TMS_ERR_INVALID_ARG
+    assert "admission" in tms.status_string(tms.TMS_ERR_BUSY)

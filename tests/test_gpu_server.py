@@ -1,0 +1,156 @@
+"""Serving loop (tms_server_*): continuous batching of requests over a
+device-resident dense store and PQ store.
+
+* parity: every request's top-k against the FP64 oracle's scores of its
+  own candidates (dense: Eq. 1; PQ: decompress-then-dot), within the 1e-3
+  tolerance, positions a valid top-k up to tolerance ties;
+* a request's result is bitwise the same alone (batches of one) and mixed
+  with others in large batches;
+* admission by pending budget, a host-injected batch failure, bounded
+  waits and unknown tickets.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import gpu_cases as gc
+from tests._common import assert_topk_consistent, oracle_view
+
+pytestmark = pytest.mark.gpu
+
+NQ, D, TOPK, M, K, DSUB = 32, 128, 10, 16, 256, 8
+
+
+@pytest.fixture(scope="module")
+def stores(cuda_lib):
+    import torch
+    lengths = synth.lengths_uniform(600, 1, 200, 70)
+    tok, off, ln = synth.dense_corpus(600, lengths, D, "f16", 70)
+    plen = synth.lengths_uniform(500, 1, 180, 71)
+    cb, codes, _, poff, pln = synth.pq_corpus(plen, M, K, DSUB, 71)
+    dev = gc.to_dev(tok, off, ln, codes, cb, poff, pln)
+    torch.cuda.synchronize()
+    return dict(tok=tok, off=off, ln=ln, cb=cb, codes=codes, poff=poff, pln=pln, dev=dev)
+
+
+def _server(stores, **kw):
+    from paper_2606_26439_gb300 import tms
+    tok_d, off_d, ln_d, codes_d, cb_d, poff_d, pln_d = stores["dev"]
+    args = dict(nq=NQ, topk=TOPK, max_batch_requests=64, max_batch_candidates=200_000, max_pending=256)
+    args.update(kw)
+    return tms.Server(tok_d, off_d, ln_d, pq=(codes_d, cb_d, poff_d, pln_d), **args)
+
+
+def _requests(n, seed):
+    g = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        store = int(g.integers(0, 2))
+        n_docs = 600 if store == 0 else 500
+        size = int(g.choice([0, 1, 7, 10, 33, 250, n_docs]))
+        cands = g.choice(n_docs, size, replace=False).astype(np.int32)
+        if size > 20 and i % 5 == 0:
+            cands[3] = n_docs + 5       # a bad id: scores NaN, sorts last
+        q = synth.queries(1, NQ, D, "f16", seed * 1000 + i)[0]
+        reqs.append((store, q, cands))
+    return reqs
+
+
+def _oracle_scores(stores, store, q, cands):
+    qa, qdt = oracle_view(q)
+    if store == 0:
+        ta, tdt = oracle_view(stores["tok"])
+        return oracle.dense_scores(qa, ta, stores["off"], stores["ln"], cands, qdtype=qdt, tdtype=tdt)
+    return oracle.pq_decompress_scores(qa, stores["cb"], stores["codes"], stores["poff"], stores["pln"], cands,
+                                       qdtype=qdt)
+
+
+def test_server_parity_with_oracle(stores):
+    reqs = _requests(40, 1)
+    with _server(stores) as srv:
+        tickets = [srv.submit(q, c, store) for store, q, c in reqs]
+        results = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert st["requests"] == len(reqs) and st["rejected"] == 0
+    for (store, q, cands), (sc, ids, lat) in zip(reqs, results):
+        want = _oracle_scores(stores, store, q, cands)
+        n_valid = min(TOPK, len(cands))
+        assert np.all(ids[n_valid:] == -1) and np.all(np.isneginf(sc[n_valid:]))
+        if len(cands) == 0:
+            continue
+        # map the returned ids back to positions of the list (first occurrence)
+        pos = np.array([int(np.nonzero(cands == i)[0][0]) for i in ids[:n_valid]])
+        tol = 2e-3 * max(1.0, np.nanmax(np.abs(want)))
+        assert_topk_consistent(sc[:n_valid], pos, want, TOPK, tol)
+        fin = np.isfinite(want[pos])
+        assert np.all(np.abs(sc[:n_valid][fin] - want[pos][fin]) <= 1e-3 * np.maximum(np.abs(want[pos][fin]),
+                                                                                       NQ * 1e-3))
+        assert lat > 0
+
+
+def test_alone_equals_mixed(stores):
+    reqs = _requests(48, 2)
+    with _server(stores, max_batch_requests=1) as srv:   # every request alone
+        alone = [srv.wait(srv.submit(q, c, s))[:2] for s, q, c in reqs]
+    with _server(stores, max_batch_requests=64) as srv:  # all submitted at once, batched
+        tickets = [srv.submit(q, c, s) for s, q, c in reqs]
+        mixed = [srv.wait(t)[:2] for t in tickets]
+        assert srv.stats()["batches"] < len(reqs)
+    for (sa, ia), (sm, im) in zip(alone, mixed):
+        assert np.array_equal(sa.view(np.uint32), sm.view(np.uint32))
+        assert np.array_equal(ia, im)
+
+
+def test_admission_budget(stores):
+    from paper_2606_26439_gb300 import tms
+    reqs = _requests(30, 3)
+    with _server(stores, max_pending=2, max_batch_requests=1) as srv:
+        tickets, busy = [], 0
+        for s, q, c in reqs:
+            try:
+                tickets.append(srv.submit(q, c, s))
+            except tms.TmsError as e:
+                assert e.status == tms.TMS_ERR_BUSY
+                busy += 1
+        for t in tickets:
+            srv.wait(t)
+        st = srv.stats()
+    assert st["rejected"] == busy and st["requests"] == len(tickets)
+    assert len(tickets) >= 2
+
+
+def test_injected_batch_failure_is_reported(stores):
+    from paper_2606_26439_gb300 import tms
+    reqs = _requests(6, 4)
+    with _server(stores, max_batch_requests=1, inject_error_batch=2) as srv:
+        statuses = []
+        for s, q, c in reqs:
+            try:
+                srv.wait(srv.submit(q, c, s))
+                statuses.append(tms.TMS_OK)
+            except tms.TmsError as e:
+                statuses.append(e.status)
+    assert statuses[1] == tms.TMS_ERR_CUDA
+    assert all(st == tms.TMS_OK for i, st in enumerate(statuses) if i != 1)
+
+
+def test_bounded_wait_unknown_ticket_and_oversize(stores):
+    from paper_2606_26439_gb300 import tms
+    big = np.random.default_rng(5).integers(0, 600, 150_000).astype(np.int32)
+    q = synth.queries(1, NQ, D, "f16", 5)[0]
+    with _server(stores) as srv:
+        with pytest.raises(tms.TmsError) as e:
+            srv.wait(12345)
+        assert e.value.status == tms.TMS_ERR_INVALID_ARG
+        with pytest.raises(tms.TmsError) as e:
+            srv.submit(q, np.zeros(200_001, np.int32))
+        assert e.value.status == tms.TMS_ERR_UNSUPPORTED
+        tickets = [srv.submit(q, big) for _ in range(8)]
+        with pytest.raises(tms.TmsError) as e:
+            srv.wait(tickets[-1], timeout_s=0.0)
+        assert e.value.status == tms.TMS_ERR_TIMEOUT
+        for t in tickets:                 # still waitable after a timeout
+            srv.wait(t)
