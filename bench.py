@@ -14,8 +14,10 @@ FP8 E4M3 store (per-token scales), dimension tiling at d = 64/256/512/768
 (200,000 docs, 32 queries over all of them, bf16, top-100; per-query and
 shared-candidate schedules), the FP8 store at 1,000,000 docs with 64
 queries over all of them (throughput, error and top-10 overlap against the
-fp16 scorer, with and without an fp16 re-score of the FP8 top-100) and
-fused PQ (1,000,000 docs, M = 16, K = 256, 64 queries over all of them).
+fp16 scorer, with and without an fp16 re-score of the FP8 top-100),
+fused PQ (1,000,000 docs, M = 16, K = 256, 64 queries over all of them)
+and the serving loop on a mixed dense + PQ request stream (p50 / p99
+latency and docs/s, batched against one request per launch).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tms|reference]
 
@@ -426,6 +428,77 @@ def fp8_store_row(stream, hbm_peak):
     return row
 
 
+def serving_row():
+    """Serving loop on a mix like config 5: 1,000,000 fp16 documents and
+    1,000,000 PQ documents (M=16, K=256) resident; requests of 32 query
+    tokens, each on one store (even odds), candidate lists log-uniform in
+    [1,000, 100,000] (ids drawn uniformly), top-10, Poisson arrivals.  For
+    each arrival rate: p50 / p99 latency (submit to result) and docs/s with
+    continuous batching, and with one request per launch (the plain
+    per-request baseline, same kernels)."""
+    import threading
+    import torch
+    from paper_2606_26439_gb300 import tms
+    dev = torch.device("cuda")
+    n_docs = 1_000_000
+    tok, off, ln = synth.device_dense_corpus(synth.lengths_uniform(n_docs, LO, HI, 5), D, "f16", 5, dev)
+    cb, codes, poff, pln = synth.device_pq_corpus(synth.lengths_uniform(n_docs, LO, HI, 6), 16, 256, 8, 6,
+                                                  device=dev)
+    g = np.random.default_rng(7)
+    pool = []
+    for i in range(512):
+        n = int(np.exp(g.uniform(np.log(1_000), np.log(100_000))))
+        pool.append((int(g.integers(0, 2)), synth.queries(1, NQ, D, "f16", 100 + i)[0],
+                     g.integers(0, n_docs, n).astype(np.int32)))
+    mean_cands = float(np.mean([len(p[2]) for p in pool]))
+
+    def run(rate, batched, duration=3.0):
+        srv = tms.Server(tok, off, ln, nq=NQ, topk=TOPK, max_batch_requests=256 if batched else 1,
+                         max_batch_candidates=4_000_000, max_pending=1 << 20, pq=(codes, cb, poff, pln))
+        n_req = int(rate * duration)
+        gaps = np.random.default_rng(11).exponential(1.0 / rate, n_req)
+        tickets = [None] * n_req
+        ready = threading.Semaphore(0)
+
+        def submitter():
+            t0 = time.perf_counter()
+            due = 0.0
+            for i in range(n_req):
+                due += gaps[i]
+                delay = t0 + due - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                store, q, c = pool[i % len(pool)]
+                tickets[i] = (srv.submit(q, c, store), len(c))
+                ready.release()
+
+        th = threading.Thread(target=submitter)
+        t_start = time.perf_counter()
+        th.start()
+        lat, docs = [], 0
+        for i in range(n_req):
+            ready.acquire()
+            t, n = tickets[i]
+            _, _, l = srv.wait(t, timeout_s=600.0)
+            lat.append(l)
+            docs += n
+        wall = time.perf_counter() - t_start
+        th.join()
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat) * 1e3
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "docs_per_s": docs / wall, "requests": n_req, "batches": st["batches"]}
+
+    out = {"mean_candidates": mean_cands}
+    for rate in (1000, 4000):
+        out[f"{rate}_qps"] = {"demand_docs_per_s": rate * mean_cands, "batched": run(rate, True),
+                              "one_per_launch": run(rate, False)}
+    del tok, codes
+    torch.cuda.empty_cache()
+    return out
+
+
 def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     """bf16/fp32 of the headline workload, dimension tiling, fused PQ."""
     import torch
@@ -477,6 +550,7 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     del w, tc, tsc, qc, qsc, out
     torch.cuda.empty_cache()
     rows["fp8_e4m3_shared_1m"] = fp8_store_row(stream, hbm_peak)
+    rows["serving_mix_1m_dense_1m_pq"] = serving_row()
     # dimension tiling: 200K docs, 32 queries over all docs, bf16, top-100
     n3 = 200_000
     len3 = synth.lengths_uniform(n3, LO, HI, 2)
