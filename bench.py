@@ -61,6 +61,8 @@ def parse_args():
     p.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     p.add_argument("--workload", choices=["headline", "small"], default="headline",
                    help="small: 100,000 docs, 1 query x 100,000 candidates (sized for ncu captures)")
+    p.add_argument("--profile-case", choices=["fp8_small", "pq_small", "shared_small"], default=None,
+                   help="run only one small secondary kernel (sized for ncu captures) and print its timing")
     args = p.parse_args()
     if args.workload == "small":
         global N_DOCS, N_QUERIES, WORKLOAD
@@ -715,8 +717,58 @@ def run_tms(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """One secondary kernel on a small case (100,000 documents, a few GB):
+    fp8_small -- FP8 store, 1 query x 100,000 candidates; pq_small -- PQ
+    M=16 K=256, 8 queries over all documents; shared_small -- bf16 d=256,
+    8 queries over all documents in the shared schedule."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    dev = torch.device("cuda")
+    n = 100_000
+    lens = synth.lengths_uniform(n, LO, HI, 9)
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    if args.profile_case == "fp8_small":
+        tok, off, ln = synth.device_dense_corpus(lens, D, "f16", 9, dev)
+        tc, ts = tms.quantize_e4m3(tok)
+        del tok
+        qc, qs = tms.quantize_e4m3(synth.queries(1, NQ, D, "f16", 9).to(dev))
+        co = torch.tensor([0, n], dtype=torch.int64, device=dev)
+        run = lambda: tms.score_fp8(qc, qs, tc, ts, off, ln, ids, co)  # noqa: E731
+        units = n
+    elif args.profile_case == "pq_small":
+        cb, codes, off, ln = synth.device_pq_corpus(lens, 16, 256, 8, 9, device=dev)
+        q = synth.queries(8, NQ, 128, "f16", 9).to(dev)
+        lut = tms.build_pq_lut(q, cb)
+        f = ids.repeat(8)
+        co = torch.arange(0, 9 * n, n, dtype=torch.int64, device=dev)
+        run = lambda: tms.score_pq(lut, codes, off, ln, f, co)  # noqa: E731
+        units = 8 * n
+    else:
+        tok, off, ln = synth.device_dense_corpus(lens, 256, "bf16", 9, dev)
+        q = synth.queries(8, NQ, 256, "bf16", 9).to(dev)
+        run = lambda: tms.score_dense_shared(q, tok, off, ln, ids)  # noqa: E731
+        units = 8 * n
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    assert tms.device_error() == 0
+    print(json.dumps({"profile_case": args.profile_case, "kernel_ms": ms, "docs_per_s": units / (ms * 1e-3)}),
+          flush=True)
+
+
 def main():
     args = parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -6,7 +6,9 @@
 // lists in pinned memory, and enqueues on its own stream: the host-to-
 // device copies, tms_score_dense (dense requests) or tms_build_pq_lut +
 // tms_score_pq (PQ requests), tms_topk, and the device-to-host copy of the
-// top-k.  Two buffer slots alternate, so while the GPU runs one batch the
+// top-k -- dense and PQ requests on two streams, so the HBM-bound dense
+// scoring and the shared-memory-bound PQ scoring of a batch overlap.  Two
+// buffer slots alternate, so while the GPU runs one batch the
 // worker completes the previous one and stages the next: requests that
 // arrive during a launch go into the following one (continuous batching).
 // Batch composition never changes a result: every score has one owner and
@@ -60,7 +62,7 @@ struct Slot {
     float* d_ts[2] = {nullptr, nullptr};
     int32_t* d_tp[2] = {nullptr, nullptr};
     float* d_lut = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done[2] = {nullptr, nullptr};
     std::vector<RequestPtr> reqs[2];
     tms_status status = TMS_OK;
 };
@@ -73,7 +75,7 @@ struct tms_server {
     tms_server_config cfg;
     int device = 0;
     size_t qbytes = 0;  // bytes of one query
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream[2] = {nullptr, nullptr};  // dense, PQ
     tms::server::Slot slots[2];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -120,7 +122,8 @@ bool alloc_slot(tms_server* s, Slot& sl) {
         !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_lut),
                             nb * static_cast<size_t>(c.nq) * c.pq_m * c.pq_k * 4)))
         return false;
-    return cuda_ok(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+    return cuda_ok(cudaEventCreateWithFlags(&sl.done[0], cudaEventDisableTiming)) &&
+           cuda_ok(cudaEventCreateWithFlags(&sl.done[1], cudaEventDisableTiming));
 }
 
 void free_slot(Slot& sl) {
@@ -138,12 +141,13 @@ void free_slot(Slot& sl) {
         cudaFree(sl.d_tp[st]);
     }
     cudaFree(sl.d_lut);
-    if (sl.done) cudaEventDestroy(sl.done);
+    for (int st = 0; st < 2; ++st)
+        if (sl.done[st]) cudaEventDestroy(sl.done[st]);
     (void)cudaGetLastError();
 }
 
 // Stage a batch into `sl` and enqueue its work; the result lands in the
-// slot's pinned buffers when sl.done completes.
+// slot's pinned buffers when both sl.done events complete.
 void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
     const tms_server_config& c = s->cfg;
     sl.reqs[0].clear();
@@ -164,37 +168,40 @@ void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
             sl.h_co[st][i + 1] = total;
         }
         tms_status rc = TMS_OK;
-        if (!cuda_ok(cudaMemcpyAsync(sl.d_q[st], sl.h_q[st], nb * s->qbytes, cudaMemcpyHostToDevice, s->stream)) ||
-            !cuda_ok(cudaMemcpyAsync(sl.d_c[st], sl.h_c[st], total * 4, cudaMemcpyHostToDevice, s->stream)) ||
-            !cuda_ok(cudaMemcpyAsync(sl.d_co[st], sl.h_co[st], (nb + 1) * 8, cudaMemcpyHostToDevice, s->stream)))
+        if (!cuda_ok(cudaMemcpyAsync(sl.d_q[st], sl.h_q[st], nb * s->qbytes, cudaMemcpyHostToDevice, s->stream[st])) ||
+            !cuda_ok(cudaMemcpyAsync(sl.d_c[st], sl.h_c[st], total * 4, cudaMemcpyHostToDevice, s->stream[st])) ||
+            !cuda_ok(cudaMemcpyAsync(sl.d_co[st], sl.h_co[st], (nb + 1) * 8, cudaMemcpyHostToDevice, s->stream[st])))
             rc = TMS_ERR_CUDA;
         if (rc == TMS_OK && st == 0)
             rc = tms_score_dense(sl.d_q[st], c.dtype, nb, c.nq, c.d, c.doc_tokens, c.n_tokens, c.doc_offsets,
-                                 c.doc_lengths, c.n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st], s->stream);
+                                 c.doc_lengths, c.n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st], s->stream[st]);
         if (rc == TMS_OK && st == 1) {
             rc = tms_build_pq_lut(sl.d_q[st], c.dtype, nb, c.nq, c.d, c.pq_codebook, c.pq_m, c.pq_k, sl.d_lut,
-                                  s->stream);
+                                  s->stream[st]);
             if (rc == TMS_OK)
                 rc = tms_score_pq(sl.d_lut, nb, c.nq, c.pq_m, c.pq_k, c.pq_codes, c.pq_n_tokens, c.pq_offsets,
-                                  c.pq_lengths, c.pq_n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st], s->stream);
+                                  c.pq_lengths, c.pq_n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st], s->stream[st]);
         }
-        if (rc == TMS_OK) rc = tms_topk(sl.d_sc[st], sl.d_co[st], nb, c.topk, sl.d_ts[st], sl.d_tp[st], s->stream);
+        if (rc == TMS_OK) rc = tms_topk(sl.d_sc[st], sl.d_co[st], nb, c.topk, sl.d_ts[st], sl.d_tp[st], s->stream[st]);
         if (rc == TMS_OK &&
             (!cuda_ok(cudaMemcpyAsync(sl.h_ts[st], sl.d_ts[st], static_cast<size_t>(nb) * c.topk * 4,
-                                      cudaMemcpyDeviceToHost, s->stream)) ||
+                                      cudaMemcpyDeviceToHost, s->stream[st])) ||
              !cuda_ok(cudaMemcpyAsync(sl.h_tp[st], sl.d_tp[st], static_cast<size_t>(nb) * c.topk * 4,
-                                      cudaMemcpyDeviceToHost, s->stream))))
+                                      cudaMemcpyDeviceToHost, s->stream[st]))))
             rc = TMS_ERR_CUDA;
         if (rc != TMS_OK) sl.status = rc;
     }
     if (inject) sl.status = TMS_ERR_CUDA;
-    if (!cuda_ok(cudaEventRecord(sl.done, s->stream))) sl.status = TMS_ERR_CUDA;
+    for (int st = 0; st < 2; ++st)
+        if (s->stream[st] && !cuda_ok(cudaEventRecord(sl.done[st], s->stream[st]))) sl.status = TMS_ERR_CUDA;
 }
 
 // Wait for a slot's batch and hand each request its result.
 void complete(tms_server* s, Slot& sl) {
     const tms_server_config& c = s->cfg;
-    if (!cuda_ok(cudaEventSynchronize(sl.done)) && sl.status == TMS_OK) sl.status = TMS_ERR_CUDA;
+    for (int st = 0; st < 2; ++st)
+        if (s->stream[st] && !cuda_ok(cudaEventSynchronize(sl.done[st])) && sl.status == TMS_OK)
+            sl.status = TMS_ERR_CUDA;
     const Clock::time_point now = Clock::now();
     uint64_t n = 0, cands = 0;
     for (int st = 0; st < 2; ++st) {
@@ -286,7 +293,8 @@ bool config_ok(const tms_server_config& c) {
 
 void destroy(tms_server* s) {
     for (auto& sl : s->slots) free_slot(sl);
-    if (s->stream) cudaStreamDestroy(s->stream);
+    for (int st = 0; st < 2; ++st)
+        if (s->stream[st]) cudaStreamDestroy(s->stream[st]);
     (void)cudaGetLastError();
     delete s;
 }
@@ -302,7 +310,9 @@ extern "C" tms_status tms_server_create(const tms_server_config* cfg, tms_server
     if (!s) return TMS_ERR_CUDA;
     s->cfg = *cfg;
     s->qbytes = static_cast<size_t>(cfg->nq) * cfg->d * 2;
-    if (!cuda_ok(cudaGetDevice(&s->device)) || !cuda_ok(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) ||
+    if (!cuda_ok(cudaGetDevice(&s->device)) ||
+        !cuda_ok(cudaStreamCreateWithFlags(&s->stream[0], cudaStreamNonBlocking)) ||
+        (cfg->pq_codes && !cuda_ok(cudaStreamCreateWithFlags(&s->stream[1], cudaStreamNonBlocking))) ||
         !alloc_slot(s, s->slots[0]) || !alloc_slot(s, s->slots[1])) {
         destroy(s);
         return TMS_ERR_CUDA;
