@@ -240,6 +240,19 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel(const Args a) {
 // gather loop never waits on global memory.  While a piece is scored, the
 // warp has already issued the copy of the next piece (of this document or of
 // the next one, whose metadata was fetched one document ahead).
+//
+// Gathers are 64-bit: the table chunk is laid out in 256-byte rows
+//     byte ((s / 2) * KS + k) * 256 + (s % 2) * 128 + (m % 4) * 32 + i * 4
+// for subspace m = 4 s + (m % 4), code k and query token i (KS = 4096 / M
+// rows per block), and lane (dt = lane / 16, g = (lane / 4) % 4,
+// ip = lane % 4) reads the entries of query tokens 2 ip and 2 ip + 1 for
+// subspace 4 s + g of document token 2 a + dt of a group of four.  One byte
+// permute builds the whole address -- the code byte times 256 plus the lane
+// offset g * 32 + ip * 8 -- and each half-warp's 16 lanes hit 32 distinct
+// banks (one wavefront per half-warp, 64 lookups per instruction).  A
+// transposed shuffle reduction over the four subspace lanes (3 shuffles per
+// four tokens) leaves lane (dt, a = bit 3, u = bit 2, ip) with the full dot
+// of token 2 a + dt and query token 2 ip + u.
 constexpr int kPieceBytes = 2048;  // per buffer: 128 tokens at M = 16
 
 template <int M>
@@ -267,24 +280,33 @@ struct PendingMeta {
     int len;
 };
 
+// Table bytes of the staged variant: the last block holds 256 rows so that
+// a code >= k still reads inside the allocation.
+__host__ __device__ constexpr int staged_table_bytes(int M) { return ((M / 8 - 1) * (4096 / M) + 256) * 256; }
+
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args a, int lut_bytes) {
     constexpr int kPiece = kPieceBytes / M;  // tokens per piece
+    constexpr int KS = 4096 / M;             // table rows per block
     extern __shared__ __align__(128) uint8_t smem_raw[];
     float* lut_s = reinterpret_cast<float*>(smem_raw);
+    const uint8_t* tbl = smem_raw;
     uint8_t* bufs = smem_raw + lut_bytes;  // [kWarps][2][kPieceBytes]
     __shared__ uint64_t bars[kWarps][2];
     __shared__ int next_local;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int g = lane >> 3;
-    const int i = lane & 7;
-    const uint32_t sel = 0x4440u | static_cast<uint32_t>(g);
-    const float* lut_lane = lut_s + lane;
+    const int dt = lane >> 4;                          // token of a pair this half-warp scores
+    const int g = (lane >> 2) & 3;                     // subspace within each group of four
+    const int ip = lane & 3;                           // query tokens 2 ip, 2 ip + 1
+    const int qt = 2 * ip + ((lane >> 2) & 1);         // query token this lane ends with
+    const uint32_t lane_off = static_cast<uint32_t>(g * 32 + ip * 8);
+    // byte permute: result byte 0 = lane offset, byte 1 = code byte g, bytes 2-3 = 0
+    const uint32_t sel = 0x6504u | (static_cast<uint32_t>(g) << 4);
     const int K = a.K;
     const int nchunks = (a.nq + kQC - 1) / kQC;
-    const int words = kQC * M * K;
+    const int words = lut_bytes / 4;
     uint8_t* wbuf = bufs + warp * 2 * kPieceBytes;
     uint64_t* wbar = bars[warp];
 
@@ -312,11 +334,13 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args
             for (int w = threadIdx.x; w < words; w += blockDim.x) {
                 const int ii = w & 7;
                 const int ml = (w >> 3) & 3;
-                const int rest = w >> 5;
-                const int kk = rest % K;
-                const int mh = rest / K;
+                const int slo = (w >> 5) & 1;
+                const int rest = w >> 6;
+                const int shi = min(rest / KS, M / 8 - 1);
+                const int kk = rest - shi * KS;
+                const int m = 4 * (2 * shi + slo) + ml;
                 const int qi = ch * kQC + ii;
-                lut_s[w] = (qi < a.nq) ? __ldg(src + (static_cast<int64_t>(qi) * M + mh * 4 + ml) * K + kk) : 0.f;
+                lut_s[w] = (qi < a.nq && kk < K) ? __ldg(src + (static_cast<int64_t>(qi) * M + m) * K + kk) : 0.f;
             }
             if (threadIdx.x == 0) next_local = 0;
             __syncthreads();
@@ -412,23 +436,35 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args
                     const uint8_t* base = wbuf + b * kPieceBytes;
                     const int last = cnt - 1;
                     for (int j = 0; j < cnt; j += 4) {
-                        CodeRow<M> c[4];
+                        // this lane's tokens: j + dt and j + 2 + dt (a duplicate of the
+                        // last token past the end cannot change a max)
+                        const CodeRow<M> c0 = smem_codes<M>(base + min(j + dt, last) * M);
+                        const CodeRow<M> c1 = smem_codes<M>(base + min(j + 2 + dt, last) * M);
+                        float v00 = 0.f, v01 = 0.f, v10 = 0.f, v11 = 0.f;  // [token pair a][query token u]
 #pragma unroll
-                        for (int tt = 0; tt < 4; ++tt) c[tt] = smem_codes<M>(base + min(j + tt, last) * M);
-                        float p[4];
-#pragma unroll
-                        for (int tt = 0; tt < 4; ++tt) p[tt] = lane_partial<M>(lut_lane, c[tt], sel, K);
-                        const bool up16 = (lane & 16) != 0;
-                        float k0 = up16 ? p[2] : p[0];
-                        float k1 = up16 ? p[3] : p[1];
-                        const float s0 = up16 ? p[0] : p[2];
-                        const float s1 = up16 ? p[1] : p[3];
-                        k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-                        k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-                        const bool up8 = (lane & 8) != 0;
-                        float kk = up8 ? k1 : k0;
-                        const float ss = up8 ? k0 : k1;
-                        kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+                        for (int sg = 0; sg < M / 4; ++sg) {
+                            const int boff = (sg >> 1) * KS * 256 + (sg & 1) * 128;
+                            const float2 t0 =
+                                *reinterpret_cast<const float2*>(tbl + boff + __byte_perm(c0.w[sg], lane_off, sel));
+                            const float2 t1 =
+                                *reinterpret_cast<const float2*>(tbl + boff + __byte_perm(c1.w[sg], lane_off, sel));
+                            v00 += t0.x;
+                            v01 += t0.y;
+                            v10 += t1.x;
+                            v11 += t1.y;
+                        }
+                        // sum over the four subspace lanes: keep pair a = bit 3, then u = bit 2
+                        const bool b3 = (lane & 8) != 0;
+                        float k0 = b3 ? v10 : v00;
+                        float k1 = b3 ? v11 : v01;
+                        const float s0 = b3 ? v00 : v10;
+                        const float s1 = b3 ? v01 : v11;
+                        k0 += __shfl_xor_sync(0xffffffffu, s0, 8);
+                        k1 += __shfl_xor_sync(0xffffffffu, s1, 8);
+                        const bool b2 = (lane & 4) != 0;
+                        float kk = b2 ? k1 : k0;
+                        const float ss = b2 ? k0 : k1;
+                        kk += __shfl_xor_sync(0xffffffffu, ss, 4);
                         rmax = fmaxf(rmax, kk);
                     }
                     __syncwarp();
@@ -436,7 +472,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args
                 if (!ok) break;
                 rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 8));
                 rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 16));
-                float v = (ch * kQC + i < a.nq) ? rmax : 0.f;
+                float v = (ch * kQC + qt < a.nq) ? rmax : 0.f;
                 v += __shfl_xor_sync(0xffffffffu, v, 1);
                 v += __shfl_xor_sync(0xffffffffu, v, 2);
                 v += __shfl_xor_sync(0xffffffffu, v, 4);
@@ -523,7 +559,8 @@ extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int 
     // The last subspace group is sized for 256 codes so that a code >= k
     // still indexes inside the allocation.
     const int smem = ((m / 4 - 1) * k + 256) * 32 * 4;
-    const int smem_st = smem + pq::kWarps * 2 * pq::kPieceBytes;  // staged variant: table + piece buffers
+    const int tbl_st = pq::staged_table_bytes(m >= 16 ? m : 16);
+    const int smem_st = tbl_st + pq::kWarps * 2 * pq::kPieceBytes;  // staged variant: table + piece buffers
     if ((m >= 16 ? smem_st : smem) > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(dev.sm_count, n_cand));
     cudaError_t e = cudaSuccess;
@@ -539,12 +576,12 @@ extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int 
         case 16:
             e = cudaFuncSetAttribute(pq::score_kernel_staged<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
             if (e == cudaSuccess)
-                pq::score_kernel_staged<16><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, smem);
+                pq::score_kernel_staged<16><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, tbl_st);
             break;
         default:
             e = cudaFuncSetAttribute(pq::score_kernel_staged<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
             if (e == cudaSuccess)
-                pq::score_kernel_staged<32><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, smem);
+                pq::score_kernel_staged<32><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, tbl_st);
             break;
     }
     if (e != cudaSuccess) return launch_status(e);
