@@ -148,9 +148,18 @@ extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int 
     a.group = 0;
     a.n_queries = n_queries;
     a.nq = nq;
-    a.nchunks = (d + dense::chunk_elems(false) - 1) / dense::chunk_elems(false);
+    a.nchunks = (d + dense::chunk_elems(dense::kF16) - 1) / dense::chunk_elems(dense::kF16);
 
     if (dtype == TMS_F32) {
+        // split TF32 on the tensor cores; the exact CUDA-core kernel below
+        // covers the shapes whose query tile does not fit
+        dense::Args at = a;
+        at.nchunks = (d + dense::chunk_elems(dense::kTF32) - 1) / dense::chunk_elems(dense::kTF32);
+        at.bpc = (nq + 31) / 32;
+        at.qbox = 32 * at.bpc;
+        st = dense::launch_tc<1, false, dense::kTF32>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, at,
+                                                       stream);
+        if (st != TMS_ERR_UNSUPPORTED) return st;
         const int smem = 32 * (d + 4) * 4;
         if (smem > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
         if (cudaFuncSetAttribute(dense::dense_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -164,7 +173,7 @@ extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int 
     }
     a.bpc = (nq + 31) / 32;
     a.qbox = 32 * a.bpc;
-    return dense::launch_tc<1, false, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+    return dense::launch_tc<1, false, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
 }
 
 extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
@@ -199,7 +208,7 @@ extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtyp
     a.n_cand = n_cand;
     a.n_queries = n_queries;
     a.nq = nq;
-    a.nchunks = (d + dense::chunk_elems(false) - 1) / dense::chunk_elems(false);
+    a.nchunks = (d + dense::chunk_elems(dense::kF16) - 1) / dense::chunk_elems(dense::kF16);
     // Queries per group (32 MMA columns each): up to 8; a smaller group when
     // the stacked query tile would not fit shared memory at this d.
     for (int group = n_queries >= 5 ? 8 : (n_queries >= 3 ? 4 : 2); group >= 2; group /= 2) {
@@ -209,9 +218,9 @@ extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtyp
         a.group = group;
         a.bpc = group;
         a.qbox = 32;
-        st = group == 8 ? dense::launch_tc<2, true, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+        st = group == 8 ? dense::launch_tc<2, true, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
                                                           stream)
-                        : dense::launch_tc<1, true, false>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                        : dense::launch_tc<1, true, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
                                                           stream);
         if (st != TMS_ERR_UNSUPPORTED) return st;
     }

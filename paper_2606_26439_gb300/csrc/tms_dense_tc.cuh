@@ -2,8 +2,11 @@
 //
 // Computes Eq. 1 of the TileMaxSim paper, score = sum_i max_j q_i . d_j,
 // for every candidate of every query, in one persistent launch, with the
-// document and query rows stored as fp16 / bf16 or as FP8 E4M3 codes with
-// one fp32 scale per row (F8).
+// document and query rows stored as fp16 / bf16, as FP8 E4M3 codes with one
+// fp32 scale per row (F8), or as fp32 scored by split TF32 (TF: each
+// operand x = hi + lo with hi = x rounded to TF32 and lo the exact rest;
+// hi.hi + hi.lo + lo.hi on the tensor cores, the lo.lo term of relative
+// size 2^-22 dropped -- FP32-level accuracy).
 //
 // Orientation: the MMA computes S^T = Q D^T, query tokens along M (tensor-
 // memory lanes, one per epilogue thread) and document rows along N
@@ -32,9 +35,13 @@
 //     by parallel lanes (128-byte swizzle).  Each token is read from HBM
 //     once (Theorem 1 with BQ = Nq, or the whole group of queries in the
 //     shared schedule).
+//   * TF only -- four splitter warps: split every landed chunk stage (hi in
+//     place, lo beside it) and every new query tile before the MMA reads
+//     them.
 //   * MMA warp: one thread issues tcgen05.mma (M = 128 query rows, K = 32
 //     bytes: 16 fp16/bf16 elements with kind::f16, 32 E4M3 elements with
-//     kind::f8f6f4) over every dimension chunk of a super-tile,
+//     kind::f8f6f4, 8 TF32 elements -- three products -- with kind::tf32)
+//     over every dimension chunk of a super-tile,
 //     accumulating the partial dot products in tensor memory before any
 //     max is taken -- the paper's dimension tiling (Section 3), with the K
 //     loop running through TMEM.
@@ -64,8 +71,10 @@ namespace tms {
 namespace dense {
 
 constexpr int kRows = 128;                    // document rows per tile
+// Row types: fp16 / bf16, FP8 E4M3 codes + row scales, fp32 by split TF32.
+enum : int { kF16 = 0, kE4M3 = 1, kTF32 = 2 };
 // Elements per 128-byte dimension chunk (one 128-byte swizzle row).
-__host__ __device__ constexpr int chunk_elems(bool f8) { return f8 ? 128 : 64; }
+__host__ __device__ constexpr int chunk_elems(int kind) { return kind == kE4M3 ? 128 : (kind == kTF32 ? 32 : 64); }
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per planner lane)
 // Super-tile records in flight: 8 with 256-row super-tiles (one CTA per
@@ -77,6 +86,8 @@ constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a
 constexpr int kEpiWarps = 4;
 constexpr int kLoaderWarp = 2 + kEpiWarps;
 constexpr int kThreads = 32 * (kLoaderWarp + 1);  // planner, MMA, four epilogue warps, loader
+constexpr int kSplitWarps = 4;                    // TF: splitter warps after the loader
+__host__ __device__ constexpr int kernel_threads(int kind) { return kThreads + (kind == kTF32 ? 32 * kSplitWarps : 0); }
 constexpr int kAcc = 2;                       // accumulator buffers (each H x STR TMEM columns)
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
@@ -134,7 +145,7 @@ struct Args {
 };
 
 struct Layout {
-    int q_off, stage_off, part_off, sc_off, st_off, bar_off, misc_off, total;
+    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, st_off, bar_off, misc_off, total;
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
@@ -143,15 +154,20 @@ struct Layout {
 // the stage ring -- always inside the allocation, and they only feed
 // accumulator rows that nothing reads.  A stage holds the full super-tile
 // of str rows, so the document operand (N <= str) never reads past it.
-__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, bool f8) {
+// TF: the query region and every stage have a lo twin right after them.
+__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind) {
+    const bool f8 = kind == kE4M3;
+    const int twin = kind == kTF32 ? 2 : 1;
     Layout L;
     L.q_off = 0;
-    L.stage_off = (qslots * nchunks * rows_alloc * 128 + 1023) & ~1023;
-    L.part_off = L.stage_off + stages * str * 128;
+    L.qlo_off = qslots * nchunks * rows_alloc * 128;
+    L.stage_off = (twin * L.qlo_off + 1023) & ~1023;
+    L.stage_stride = twin * str * 128;
+    L.part_off = L.stage_off + stages * L.stage_stride;
     L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
     L.st_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
     L.bar_off = L.st_off + st_ring(str) * static_cast<int>(sizeof(StSlot));
-    const int nbar = 2 * stages + 2 * kAcc + 2 * qslots + 2 * st_ring(str) + 8 + 2 * kScaleRing + 1;
+    const int nbar = 3 * stages + 2 * kAcc + 3 * qslots + 2 * st_ring(str) + 8 + 2 * kScaleRing + 1;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
@@ -221,6 +237,14 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
     }
 }
 
+// x rounded to the nearest TF32 value (ties away from zero), as an fp32
+// bit pattern with the low 13 mantissa bits zero.
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 // Tensor maps of one launch.  doc[h] covers document rows with a box of
 // 8 (h + 1) rows x one 128-byte chunk, so a tile of r rows is always ONE
 // box per chunk (at most 7 rows of over-fetch).  scales (F8): the
@@ -240,9 +264,12 @@ struct Maps {
 // writes one score per query of the group.
 // F8: rows are E4M3 codes; similarities are scaled by the document row's
 // scale before the max and by the query token's scale before the sum.
-template <int H, int STR, int CTAS, bool SH, bool F8>
-__global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
-    constexpr int CE = chunk_elems(F8);
+template <int H, int STR, int CTAS, bool SH, int KIND>
+__global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
+    dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
+    constexpr bool F8 = KIND == kE4M3;
+    constexpr bool TF = KIND == kTF32;
+    constexpr int CE = chunk_elems(KIND);
     constexpr int STAGE_BYTES = STR * 128;
     constexpr uint32_t TCOLS = kAcc * H * STR;
     constexpr int kStRing = st_ring(STR);
@@ -254,9 +281,11 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
     const int QS = a.qslots;
     const int NCH = a.nchunks;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, F8);
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND);
+    const int SSTRIDE = L.stage_stride;  // bytes between stages (TF: hi, then lo)
 
     uint8_t* q_base = smem + L.q_off;
+    uint8_t* qlo_base = smem + L.qlo_off;  // TF: the lo twin of the query region
     uint8_t* stage_base = smem + L.stage_off;
     float* part = reinterpret_cast<float*>(smem + L.part_off);  // [copy][parity][block]
     float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // [kScaleRing][kScalePitch]
@@ -275,6 +304,8 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
     uint64_t* sfull = pempty + 4;           // [kScaleRing]
     uint64_t* sempty = sfull + kScaleRing;  // [kScaleRing]
     uint64_t* mdone = sempty + kScaleRing;
+    uint64_t* conv = mdone + 1;   // TF: [S] stage split
+    uint64_t* qconv = conv + S;   // TF: [QS] query tile split
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
 
@@ -296,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
         }
         for (int i = 0; i < kStRing; ++i) {
             mbar_init(&xfull[i], 1);
-            mbar_init(&xempty[i], 2 + kEpiWarps);  // loader, MMA thread, epilogue warps
+            mbar_init(&xempty[i], 2 + kEpiWarps + (TF ? kSplitWarps : 0));  // loader, MMA, epilogue, splitters
         }
         for (int i = 0; i < 4; ++i) {
             mbar_init(&pfull[i], a.bpc);
@@ -307,6 +338,8 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
             mbar_init(&sempty[i], kEpiWarps);
         }
         mbar_init(mdone, 1);
+        for (int i = 0; i < S; ++i) mbar_init(&conv[i], kSplitWarps);
+        for (int i = 0; i < QS; ++i) mbar_init(&qconv[i], kSplitWarps);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -554,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                 }
                 if (lane == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(h.rows * 128));
                 __syncwarp();
-                if (has) tma_load_2d(stage_base + s * STAGE_BYTES + col * 128, dmap, kc * CE, row0, &full[s], pol_stream);
+                if (has) tma_load_2d(stage_base + s * SSTRIDE + col * 128, dmap, kc * CE, row0, &full[s], pol_stream);
                 ++issued;
                 if (++s == S) {
                     s = 0;
@@ -577,6 +610,60 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
             }
         }
         __syncwarp();
+    } else if (TF && warp > kLoaderWarp) {
+        // ------------------------------------------------------ splitters
+        // Split each new query tile and every landed chunk stage into
+        // hi = x rounded to TF32 (in place) and lo = x - hi (exact) in the
+        // twin region, then publish the split to the MMA thread.  Elements
+        // are independent, so the 128-byte swizzle needs no decoding: hi and
+        // lo keep the same byte positions.
+        const int tid = (warp - kLoaderWarp - 1) * 32 + lane;
+        constexpr int kSplitThreads = 32 * kSplitWarps;
+        auto split = [&](uint8_t* hi_p, uint8_t* lo_p, int bytes) {
+            float4* hv = reinterpret_cast<float4*>(hi_p);
+            float4* lv = reinterpret_cast<float4*>(lo_p);
+            for (int v = tid; v < bytes / 16; v += kSplitThreads) {
+                const float4 x = hv[v];
+                const float4 h = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
+                lv[v] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+                hv[v] = h;
+            }
+            fence_proxy_async_smem();  // generic-proxy writes, read next by the tensor cores
+            __syncwarp();
+        };
+        int s = 0;
+        uint32_t ph = 0;
+        int qi = 0, cur_q = -1;
+        for (int t = 0;; ++t) {
+            const int xs = t % kStRing;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            const StHdr h = slots[xs].h;
+            if (h.flags & kEnd) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xempty[xs]);
+            bool ok = true;
+            if (h.q != cur_q) {
+                const int slot = qi % QS;
+                if (!warp_wait_all(&qfull[slot], (qi / QS) & 1, abort_flag, a.err)) break;
+                split(q_base + slot * qslot_bytes, qlo_base + slot * qslot_bytes, qslot_bytes);
+                if (lane == 0) mbar_arrive(&qconv[slot]);
+                ++qi;
+                cur_q = h.q;
+            }
+            for (int kc = 0; kc < NCH; ++kc) {
+                if (!warp_wait_all(&full[s], ph, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                split(stage_base + s * SSTRIDE, stage_base + s * SSTRIDE + STAGE_BYTES, h.rows * 128);
+                if (lane == 0) mbar_arrive(&conv[s]);
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            if (!ok) break;
+        }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA
         // One thread runs this role: every wait is its own (no warp votes),
@@ -596,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                 if (x.q != cur_q) {
                     if (cur_q >= 0) mma_commit(&qempty[qslot]);
                     qslot = qi % QS;
-                    if (!mbar_wait(&qfull[qslot], (qi / QS) & 1, abort_flag, a.err)) break;
+                    if (!mbar_wait(TF ? &qconv[qslot] : &qfull[qslot], (qi / QS) & 1, abort_flag, a.err)) break;
                     ++qi;
                     cur_q = x.q;
                 }
@@ -606,22 +693,29 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
                 bool ok = true;
                 const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * H * STR);
                 const uint64_t q_desc = desc_sw128(smem_u32(q_base + qslot * qslot_bytes));
+                const uint64_t qlo_desc = desc_sw128(smem_u32(qlo_base + qslot * qslot_bytes));
                 const uint32_t idesc = a.idesc | (static_cast<uint32_t>(x.n >> 3) << 17);
                 for (int kc = 0; kc < NCH; ++kc) {
-                    if (!mbar_wait(&full[s], ph, abort_flag, a.err)) {
+                    if (!mbar_wait(TF ? &conv[s] : &full[s], ph, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t b_desc = desc_sw128(smem_u32(stage_base + s * STAGE_BYTES));
+                    const uint64_t b_desc = desc_sw128(smem_u32(stage_base + s * SSTRIDE));
+                    const uint64_t blo_desc = desc_sw128(smem_u32(stage_base + s * SSTRIDE + STAGE_BYTES));
 #pragma unroll
                     for (int h = 0; h < H; ++h) {
-                        const uint64_t a_desc =
-                            q_desc + static_cast<uint64_t>(((kc * a.rows_alloc + h * 128) * 128) >> 4);
+                        const uint64_t qoff = static_cast<uint64_t>(((kc * a.rows_alloc + h * 128) * 128) >> 4);
+                        const uint64_t a_desc = q_desc + qoff;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint32_t accumulate = (kc > 0 || kk > 0) ? 1u : 0u;
-                            if (F8)
+                            if (TF) {  // hi.hi + hi.lo + lo.hi
+                                const uint32_t dt = d_tmem + static_cast<uint32_t>(h * STR);
+                                mma_tf32(dt, a_desc + 2 * kk, b_desc + 2 * kk, idesc, accumulate);
+                                mma_tf32(dt, a_desc + 2 * kk, blo_desc + 2 * kk, idesc, 1u);
+                                mma_tf32(dt, qlo_desc + qoff + 2 * kk, b_desc + 2 * kk, idesc, 1u);
+                            } else if (F8)
                                 mma_f8(d_tmem + static_cast<uint32_t>(h * STR), a_desc + 2 * kk, b_desc + 2 * kk, idesc,
                                        accumulate);
                             else
@@ -810,18 +904,22 @@ __global__ void __launch_bounds__(kThreads, CTAS) dense_tc_kernel(const __grid_c
 // by default; per-query lists on the FP8 store prefer two CTAs per SM with
 // 128-row super-tiles (two of every pipeline role per SM; measured faster
 // for its 128-byte rows, slower for fp16/bf16); a shared group of 8
-// (H = 2) takes one CTA with 128-row super-tiles.  F8 ignores `dtype` (rows are E4M3
-// codes; t_scales in `a`).  The caller sets a.nchunks =
-// ceil(d / chunk_elems(F8)), and a.bpc / a.qbox: per-query ceil(nq / 32)
+// (H = 2) takes one CTA with 128-row super-tiles; split TF32 (fp32 rows,
+// stages twice the size) one CTA with 128-row super-tiles.  KIND selects the row type;
+// kE4M3 ignores `dtype` (rows are E4M3 codes; t_scales in `a`).  The caller sets a.nchunks =
+// ceil(d / chunk_elems(KIND)), and a.bpc / a.qbox: per-query ceil(nq / 32)
 // and 32 bpc, shared mode the group size and 32.
-template <int H, bool SH, bool F8>
+template <int H, bool SH, int KIND>
 tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
                      const void* doc_tokens, int64_t n_tokens, Args a, cudaStream_t stream) {
-    constexpr int CE = chunk_elems(F8);
-    const CUtensorMapDataType tdt = F8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+    constexpr bool F8 = KIND == kE4M3;
+    constexpr bool TF = KIND == kTF32;
+    constexpr int CE = chunk_elems(KIND);
+    const CUtensorMapDataType tdt = F8   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                  : TF ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                   : dtype == TMS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const uint64_t row_bytes = static_cast<uint64_t>(d) * (F8 ? 1 : 2);
+    const uint64_t row_bytes = static_cast<uint64_t>(d) * (F8 ? 1 : (TF ? 4 : 2));
     // With no document rows nothing is ever loaded through the document
     // maps; describe the query buffer so that they still encode.
     const void* dbase = n_tokens > 0 ? doc_tokens : queries;
@@ -842,8 +940,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
             for (int rp = max_reps; rp >= 1; rp /= 2) {
                 int best = -1;
                 for (int qs = 2; qs >= 1; --qs) {
-                    const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, F8);
-                    const int sts = std::min(kMaxStages, (limit - L0.total) / (str * 128 + 16));
+                    const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND);
+                    const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
                     if (sts > best) {
                         best = sts;
                         stages = sts;
@@ -859,6 +957,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     };
     int stages = 0, qslots = 1, reps = 0, str = 0, ctas = 0;
     if (H == 2) {
+        if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
+    } else if (TF) {
         if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
     } else if (!SH && F8) {
         if (plan(128, 2, stages, qslots, reps)) str = 128, ctas = 2;
@@ -880,24 +980,26 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     } else {
         maps.scales = maps.q;  // never used
     }
-    // format code 0 is f16 under kind::f16 and E4M3 under kind::f8f6f4
-    a.idesc = make_idesc(128, 0, (!F8 && dtype == TMS_BF16) ? 1u : 0u);
+    // format code 0 is f16 under kind::f16 and E4M3 under kind::f8f6f4; 2 is TF32
+    a.idesc = make_idesc(128, 0, TF ? 2u : ((!F8 && dtype == TMS_BF16) ? 1u : 0u));
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, F8);
+    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND);
     const int smem = L.total + 1024;
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {
-        kern = dense_tc_kernel<2, 128, 1, SH, F8>;
+        kern = dense_tc_kernel<2, 128, 1, SH, KIND>;
+    } else if constexpr (TF) {
+        kern = dense_tc_kernel<1, 128, 1, false, kTF32>;
     } else if constexpr (SH || !F8) {
-        kern = dense_tc_kernel<1, 256, 1, SH, F8>;
+        kern = dense_tc_kernel<1, 256, 1, SH, KIND>;
     } else {
-        kern = str == 128 ? dense_tc_kernel<1, 128, 2, false, true> : dense_tc_kernel<1, 256, 1, false, true>;
+        kern = str == 128 ? dense_tc_kernel<1, 128, 2, false, kE4M3> : dense_tc_kernel<1, 256, 1, false, kE4M3>;
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
-    kern<<<static_cast<unsigned>(grid), kThreads, smem, stream>>>(maps, a);
+    kern<<<static_cast<unsigned>(grid), kernel_threads(KIND), smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
 }
 

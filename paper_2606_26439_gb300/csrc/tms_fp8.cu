@@ -112,7 +112,7 @@ tms_status prepare(const uint8_t* q_codes, const float* q_scales, int n_queries,
     a->n_cand = n_cand;
     a->n_queries = n_queries;
     a->nq = nq;
-    a->nchunks = (d + dense::chunk_elems(true) - 1) / dense::chunk_elems(true);
+    a->nchunks = (d + dense::chunk_elems(dense::kE4M3) - 1) / dense::chunk_elems(dense::kE4M3);
     return TMS_OK;
 }
 
@@ -159,7 +159,7 @@ extern "C" tms_status tms_score_fp8(const uint8_t* q_codes, const float* q_scale
     a.group = 0;
     a.bpc = (nq + 31) / 32;
     a.qbox = 32 * a.bpc;
-    return dense::launch_tc<1, false, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
+    return dense::launch_tc<1, false, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
 }
 
 extern "C" tms_status tms_score_fp8_shared(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq,
@@ -183,9 +183,9 @@ extern "C" tms_status tms_score_fp8_shared(const uint8_t* q_codes, const float* 
         a.group = group;
         a.bpc = group;
         a.qbox = 32;
-        st = group == 8 ? dense::launch_tc<2, true, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
+        st = group == 8 ? dense::launch_tc<2, true, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
                                                          stream)
-                        : dense::launch_tc<1, true, true>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
+                        : dense::launch_tc<1, true, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
                                                          stream);
         if (st != TMS_ERR_UNSUPPORTED) return st;
     }
