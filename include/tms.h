@@ -80,8 +80,10 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
  * rounded up to a multiple of 32 and d to a multiple of 64, nq * d * 2
  * bytes must not exceed 160,256 (nq > 96 at d > 576 and nq > 64 at d > 832
  * return TMS_ERR_UNSUPPORTED).  fp16/bf16 run on the tensor cores
- * (tcgen05, fp32 accumulation in tensor memory); fp32 runs on an exact
- * fp32 path.  A candidate with a bad id or row range scores NaN and sets
+ * (tcgen05, fp32 accumulation in tensor memory); fp32 runs split TF32 on
+ * the tensor cores (x = hi + lo, hi = x rounded to TF32; hi.hi + hi.lo +
+ * lo.hi, FP32-level accuracy) when its doubled query tile fits, else an
+ * exact fp32 CUDA-core kernel (any supported nq, d).  A candidate with a bad id or row range scores NaN and sets
  * TMS_DEVERR_BAD_ID / TMS_DEVERR_BAD_RANGE.
  */
 tms_status tms_score_dense(const void *queries, tms_dtype dtype, int n_queries, int nq, int d,
