@@ -93,6 +93,25 @@ tms_status tms_score_dense(const void *queries, tms_dtype dtype, int n_queries, 
                            float *out_scores, cudaStream_t stream);
 
 /*
+ * Autotuner for tms_score_dense: the same arguments and effect (out_scores
+ * holds the scores when it returns), but first every tensor-core launch
+ * configuration that fits this shape is timed on these inputs -- rows per
+ * super-tile (256 / 128), CTAs per SM (1 / 2) and copies of the query
+ * tile (4 / 2 / 1), stages derived -- and the fastest is remembered for
+ * every later tms_score_dense call on this device with the same dtype
+ * class (fp16/bf16 or fp32), ceil(nq / 32) and number of dimension
+ * chunks.  Scores do not depend on the configuration (bitwise).  This call
+ * synchronises `stream`.  *n_configs (HOST, may be NULL) receives the
+ * number of configurations timed (0 when fp32 falls back to the CUDA-core
+ * kernel, which has none).
+ */
+tms_status tms_tune_dense(const void *queries, tms_dtype dtype, int n_queries, int nq, int d,
+                          const void *doc_tokens, int64_t n_tokens,
+                          const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                          const int32_t *cand_ids, const int64_t *cand_offsets, int64_t n_cand,
+                          float *out_scores, cudaStream_t stream, int *n_configs);
+
+/*
  * Dense MaxSim of n_queries queries that all score ONE candidate list
  * (e.g. every query over the whole corpus, the dimension-scaling workload
  * of Section 6.8).  Same arithmetic as tms_score_dense, but queries are

@@ -111,12 +111,16 @@ __global__ void __launch_bounds__(kF32Warps * 32)
 
 }  // namespace tms
 
-extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
-                                      const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
-                                      const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
-                                      const int64_t* cand_offsets, int64_t n_cand, float* out_scores,
-                                      cudaStream_t stream) {
-    using namespace tms;
+namespace tms {
+namespace {
+
+// tms_score_dense, or (tune) tms_tune_dense: the same checks and launch,
+// the tensor-core configurations timed first.
+tms_status score_dense(const void* queries, tms_dtype dtype, int n_queries, int nq, int d, const void* doc_tokens,
+                       int64_t n_tokens, const int64_t* doc_offsets, const int32_t* doc_lengths, int64_t n_docs,
+                       const int32_t* cand_ids, const int64_t* cand_offsets, int64_t n_cand, float* out_scores,
+                       cudaStream_t stream, bool tune, int* n_timed) {
+    if (n_timed) *n_timed = 0;
     if (dtype != TMS_F16 && dtype != TMS_BF16 && dtype != TMS_F32) return TMS_ERR_INVALID_ARG;
     if (n_queries < 1 || n_queries > 4096 || nq < 1 || nq > 128 || d < 8 || d > 1024 || d % 8 != 0)
         return TMS_ERR_INVALID_ARG;
@@ -148,17 +152,17 @@ extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int 
     a.group = 0;
     a.n_queries = n_queries;
     a.nq = nq;
-    a.nchunks = (d + dense::chunk_elems(dense::kF16) - 1) / dense::chunk_elems(dense::kF16);
+    a.bpc = (nq + 31) / 32;
+    a.qbox = 32 * a.bpc;
 
     if (dtype == TMS_F32) {
         // split TF32 on the tensor cores; the exact CUDA-core kernel below
         // covers the shapes whose query tile does not fit
-        dense::Args at = a;
-        at.nchunks = (d + dense::chunk_elems(dense::kTF32) - 1) / dense::chunk_elems(dense::kTF32);
-        at.bpc = (nq + 31) / 32;
-        at.qbox = 32 * at.bpc;
-        st = dense::launch_tc<1, false, dense::kTF32>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, at,
-                                                       stream);
+        a.nchunks = (d + dense::chunk_elems(dense::kTF32) - 1) / dense::chunk_elems(dense::kTF32);
+        st = tune ? dense::tune_tc<1, false, dense::kTF32>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens,
+                                                           a, stream, n_timed)
+                  : dense::launch_tc<1, false, dense::kTF32>(dev, queries, dtype, n_queries, nq, d, doc_tokens,
+                                                             n_tokens, a, stream);
         if (st != TMS_ERR_UNSUPPORTED) return st;
         const int smem = 32 * (d + 4) * 4;
         if (smem > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
@@ -171,9 +175,32 @@ extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int 
             static_cast<const float*>(queries), static_cast<const float*>(doc_tokens), a, d);
         return launch_status(cudaGetLastError());
     }
-    a.bpc = (nq + 31) / 32;
-    a.qbox = 32 * a.bpc;
-    return dense::launch_tc<1, false, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+    a.nchunks = (d + dense::chunk_elems(dense::kF16) - 1) / dense::chunk_elems(dense::kF16);
+    return tune ? dense::tune_tc<1, false, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                        stream, n_timed)
+                : dense::launch_tc<1, false, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens,
+                                                          a, stream);
+}
+
+}  // namespace
+}  // namespace tms
+
+extern "C" tms_status tms_score_dense(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                      const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
+                                      const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
+                                      const int64_t* cand_offsets, int64_t n_cand, float* out_scores,
+                                      cudaStream_t stream) {
+    return tms::score_dense(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets, doc_lengths, n_docs,
+                            cand_ids, cand_offsets, n_cand, out_scores, stream, false, nullptr);
+}
+
+extern "C" tms_status tms_tune_dense(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                     const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
+                                     const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
+                                     const int64_t* cand_offsets, int64_t n_cand, float* out_scores,
+                                     cudaStream_t stream, int* n_configs) {
+    return tms::score_dense(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets, doc_lengths, n_docs,
+                            cand_ids, cand_offsets, n_cand, out_scores, stream, true, n_configs);
 }
 
 extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,

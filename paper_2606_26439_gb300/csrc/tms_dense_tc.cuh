@@ -62,6 +62,8 @@
 #pragma once
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "tms_common.cuh"
 #include "tms_internal.h"
@@ -899,19 +901,62 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     }
 }
 
+// A launch configuration: rows per super-tile, CTAs per SM, copies of the
+// query blocks stacked in M.
+struct Config {
+    int str;
+    int ctas;
+    int reps;
+};
+
+// Configurations chosen by the autotuner, per device and launch shape.
+struct TuneKey {
+    int device, kind, h, sh, nchunks, bpc;
+    bool operator<(const TuneKey& o) const {
+        const int x[6] = {device, kind, h, sh, nchunks, bpc};
+        const int y[6] = {o.device, o.kind, o.h, o.sh, o.nchunks, o.bpc};
+        for (int i = 0; i < 6; ++i)
+            if (x[i] != y[i]) return x[i] < y[i];
+        return false;
+    }
+};
+inline std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+inline std::map<TuneKey, Config>& tune_table() {
+    static std::map<TuneKey, Config> t;
+    return t;
+}
+
+// The configurations an instantiation has kernels for.
+template <int H, bool SH, int KIND>
+inline int config_shapes(Config* out) {
+    if (H == 2 || KIND == kTF32) {
+        out[0] = {128, 1, 0};
+        return 1;
+    }
+    out[0] = {256, 1, 0};
+    out[1] = {128, 2, 0};
+    return 2;
+}
+
 // Plan shared memory, encode the tensor maps and launch dense_tc_kernel.
-// One CTA per SM with 256-row super-tiles (about two documents per MMA run)
-// by default; per-query lists on the FP8 store prefer two CTAs per SM with
-// 128-row super-tiles (two of every pipeline role per SM; measured faster
-// for its 128-byte rows, slower for fp16/bf16); a shared group of 8
-// (H = 2) takes one CTA with 128-row super-tiles; split TF32 (fp32 rows,
-// stages twice the size) one CTA with 128-row super-tiles.  KIND selects the row type;
-// kE4M3 ignores `dtype` (rows are E4M3 codes; t_scales in `a`).  The caller sets a.nchunks =
-// ceil(d / chunk_elems(KIND)), and a.bpc / a.qbox: per-query ceil(nq / 32)
-// and 32 bpc, shared mode the group size and 32.
+// Without a tuned or forced configuration: one CTA per SM with 256-row
+// super-tiles (about two documents per MMA run) by default; per-query lists
+// on the FP8 store prefer two CTAs per SM with 128-row super-tiles (two of
+// every pipeline role per SM; measured faster for its 128-byte rows, slower
+// for fp16/bf16); a shared group of 8 (H = 2) and split TF32 (fp32 rows,
+// stages twice the size) take one CTA with 128-row super-tiles.  KIND
+// selects the row type; kE4M3 ignores `dtype` (rows are E4M3 codes;
+// t_scales in `a`).  The caller sets a.nchunks = ceil(d / chunk_elems(KIND)),
+// and a.bpc / a.qbox: per-query ceil(nq / 32) and 32 bpc, shared mode the
+// group size and 32.  `force` (the autotuner's) overrides the choice;
+// TMS_ERR_UNSUPPORTED when it does not fit.
 template <int H, bool SH, int KIND>
 tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
-                     const void* doc_tokens, int64_t n_tokens, Args a, cudaStream_t stream) {
+                     const void* doc_tokens, int64_t n_tokens, Args a, cudaStream_t stream,
+                     const Config* force = nullptr) {
     constexpr bool F8 = KIND == kE4M3;
     constexpr bool TF = KIND == kTF32;
     constexpr int CE = chunk_elems(KIND);
@@ -927,44 +972,62 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
                                    CE, static_cast<uint32_t>(a.qbox));
     if (st != TMS_OK) return st;
-    // Shared-memory plan for a configuration (rows per super-tile, CTAs per
-    // SM): as many copies of the query blocks as fit with a ring of at
-    // least 4 chunk stages (fewer copies only deal documents to fewer
-    // warps), else -- one CTA per SM only -- at least 2; within a plan the
-    // query-slot count (2, else 1) that gives the most stages.
-    auto plan = [&](int str, int ctas, int& stages, int& qslots, int& reps) {
+    // Shared-memory plan for (rows per super-tile, CTAs per SM, copies):
+    // the query-slot count (2, else 1) that gives the most stages; the
+    // plan fits with at least 4 chunk stages (2 with one CTA per SM).
+    const int max_reps = H == 2 ? 1 : (a.bpc == 3 ? 1 : 4 / a.bpc);
+    auto fits = [&](int str, int ctas, int rp, int need, int& stages, int& qslots) {
+        if (rp < 1 || rp > max_reps) return false;
         const int limit = ctas == 2 ? dev.smem_per_sm / 2 - dev.smem_reserved - 1024
                                     : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
-        const int max_reps = H == 2 ? 1 : (a.bpc == 3 ? 1 : 4 / a.bpc);
+        int best = -1;
+        for (int qs = 2; qs >= 1; --qs) {
+            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND);
+            const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
+            if (sts > best) {
+                best = sts;
+                stages = sts;
+                qslots = qs;
+            }
+        }
+        return best >= std::max(need, ctas == 2 ? 4 : 2);
+    };
+    // default: as many copies as fit with 4 stages, else (one CTA) with 2
+    auto plan = [&](int str, int ctas, int& stages, int& qslots, int& reps) {
         for (int need = 4; need >= (ctas == 2 ? 4 : 2); need -= 2)
-            for (int rp = max_reps; rp >= 1; rp /= 2) {
-                int best = -1;
-                for (int qs = 2; qs >= 1; --qs) {
-                    const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND);
-                    const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
-                    if (sts > best) {
-                        best = sts;
-                        stages = sts;
-                        qslots = qs;
-                    }
-                }
-                if (best >= need) {
+            for (int rp = max_reps; rp >= 1; rp /= 2)
+                if (fits(str, ctas, rp, need, stages, qslots)) {
                     reps = rp;
                     return true;
                 }
-            }
         return false;
     };
     int stages = 0, qslots = 1, reps = 0, str = 0, ctas = 0;
-    if (H == 2) {
-        if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
-    } else if (TF) {
-        if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
-    } else if (!SH && F8) {
-        if (plan(128, 2, stages, qslots, reps)) str = 128, ctas = 2;
-        else if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
-    } else {
-        if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+    Config tuned{0, 0, 0};
+    if (!force) {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        const auto it = tune_table().find(TuneKey{dev.ordinal, KIND, H, SH ? 1 : 0, a.nchunks, a.bpc});
+        if (it != tune_table().end()) tuned = it->second;
+    }
+    const Config* want = force ? force : (tuned.ctas ? &tuned : nullptr);
+    if (want) {
+        if (fits(want->str, want->ctas, want->reps, 2, stages, qslots)) {
+            str = want->str;
+            ctas = want->ctas;
+            reps = want->reps;
+        } else if (force) {
+            return TMS_ERR_UNSUPPORTED;
+        }
+    }
+    if (ctas == 0) {
+        if (H == 2 || TF) {
+            if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
+        } else if (!SH && F8) {
+            if (plan(128, 2, stages, qslots, reps)) str = 128, ctas = 2;
+            else if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+        } else {
+            if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+        }
     }
     if (ctas == 0) return TMS_ERR_UNSUPPORTED;
     a.reps = reps;
@@ -991,16 +1054,74 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         kern = dense_tc_kernel<2, 128, 1, SH, KIND>;
     } else if constexpr (TF) {
         kern = dense_tc_kernel<1, 128, 1, false, kTF32>;
-    } else if constexpr (SH || !F8) {
-        kern = dense_tc_kernel<1, 256, 1, SH, KIND>;
     } else {
-        kern = str == 128 ? dense_tc_kernel<1, 128, 2, false, kE4M3> : dense_tc_kernel<1, 256, 1, false, kE4M3>;
+        kern = str == 128 ? dense_tc_kernel<1, 128, 2, SH, KIND> : dense_tc_kernel<1, 256, 1, SH, KIND>;
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
     kern<<<static_cast<unsigned>(grid), kernel_threads(KIND), smem, stream>>>(maps, a);
     return launch_status(cudaGetLastError());
+}
+
+// Autotuner: time every configuration this instantiation has kernels for
+// that fits the launch (3 timed launches after one warm-up each, CUDA
+// events on `stream`), remember the fastest for the launch shape, and
+// report how many were timed.  Each launch writes the scores.
+template <int H, bool SH, int KIND>
+tms_status tune_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                   const void* doc_tokens, int64_t n_tokens, const Args& a, cudaStream_t stream, int* n_timed) {
+    Config shapes[2];
+    const int ns = config_shapes<H, SH, KIND>(shapes);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        (void)cudaGetLastError();
+        return TMS_ERR_CUDA;
+    }
+    float best_ms = 0.f;
+    Config best{0, 0, 0};
+    int timed = 0;
+    tms_status st = TMS_OK;
+    for (int i = 0; i < ns && st == TMS_OK; ++i) {
+        for (int rp = 4; rp >= 1; rp /= 2) {
+            const Config c{shapes[i].str, shapes[i].ctas, rp};
+            tms_status r = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                  stream, &c);
+            if (r == TMS_ERR_UNSUPPORTED) continue;
+            if (r != TMS_OK) {
+                st = r;
+                break;
+            }
+            cudaEventRecord(e0, stream);
+            for (int k = 0; k < 3 && r == TMS_OK; ++k)
+                r = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream, &c);
+            cudaEventRecord(e1, stream);
+            float ms = 0.f;
+            if (r != TMS_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = r != TMS_OK ? r : TMS_ERR_CUDA;
+                break;
+            }
+            ++timed;
+            if (best.ctas == 0 || ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    if (st != TMS_OK) return st;
+    if (best.ctas == 0) return TMS_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        tune_table()[TuneKey{dev.ordinal, KIND, H, SH ? 1 : 0, a.nchunks, a.bpc}] = best;
+    }
+    // leave the scores of the chosen configuration in place
+    st = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream, &best);
+    if (n_timed) *n_timed = timed;
+    return st;
 }
 
 }  // namespace dense

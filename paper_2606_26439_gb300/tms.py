@@ -30,7 +30,7 @@ TMS_DEVERR_TIMEOUT = 4
 TMS_DEVERR_BAD_CSR = 8
 
 #: every symbol include/tms.h declares
-EXPORTS = ("tms_score_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
+EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
            "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk", "tms_server_create",
            "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy",
            "tms_get_device_error", "tms_status_string", "tms_version")
@@ -83,6 +83,8 @@ def lib(build_if_missing: bool = True):
                 raise RuntimeError("libtms.so is missing and could not be built")
             L = ctypes.CDLL(path)
             L.tms_score_dense.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_tune_dense.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p,
+                                         ctypes.POINTER(ctypes.c_int)]
             L.tms_score_dense_shared.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p]
             L.tms_quantize_e4m3.argtypes = [_p, _i32, _i64, _i32, _p, _p, _p]
             L.tms_score_fp8.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
@@ -100,7 +102,7 @@ def lib(build_if_missing: bool = True):
             L.tms_status_string.argtypes = [_i32]
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
-            for name in ("tms_score_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
+            for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
                          "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
                          "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
                          "tms_server_destroy", "tms_get_device_error", "tms_version"):
@@ -215,6 +217,23 @@ def score_dense(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, cand_of
         _dev(cand_ids, torch.int32), _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32),
         _stream_ptr(stream)))
     return out
+
+
+def tune_dense(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, cand_offsets, out=None, stream=None):
+    """tms_tune_dense: score_dense after timing the launch configurations;
+    returns (scores, number of configurations timed)."""
+    torch = _torch()
+    nQ, nq, d = queries.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty(n_cand, dtype=torch.float32, device=queries.device)
+    n = ctypes.c_int(0)
+    _check("tms_tune_dense", lib().tms_tune_dense(
+        _dev(queries), _dtype_code(queries), nQ, nq, d, _dev(doc_tokens, queries.dtype), doc_tokens.shape[0],
+        _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
+        _dev(cand_ids, torch.int32), _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32),
+        _stream_ptr(stream), ctypes.byref(n)))
+    return out, n.value
 
 
 def score_dense_shared(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, out=None, stream=None):

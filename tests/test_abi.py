@@ -113,3 +113,10 @@ def test_server_rejects_bad_config(lib):
     assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG
     assert lib.tms_server_destroy(None) == tms.TMS_ERR_INVALID_ARG
     assert "admission" in tms.status_string(tms.TMS_ERR_BUSY)
+
+
+def test_tune_dense_rejects_like_score_dense(lib):
+    n = ctypes.c_int(-1)
+    st = lib.tms_tune_dense(DUMMY, 0, 1, 0, 128, DUMMY, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL,
+                            ctypes.byref(n))
+    assert st == tms.TMS_ERR_INVALID_ARG and n.value == 0
