@@ -61,7 +61,7 @@ def parse_args():
     p.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     p.add_argument("--workload", choices=["headline", "small"], default="headline",
                    help="small: 100,000 docs, 1 query x 100,000 candidates (sized for ncu captures)")
-    p.add_argument("--profile-case", choices=["fp8_small", "pq_small", "shared_small"], default=None,
+    p.add_argument("--profile-case", choices=["fp8_small", "pq_small", "pq16_small", "shared_small"], default=None,
                    help="run only one small secondary kernel (sized for ncu captures) and print its timing")
     args = p.parse_args()
     if args.workload == "small":
@@ -639,7 +639,10 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
         tms.build_pq_lut(Q, cb, out=lut, stream=stream)
         tms.score_pq(lut, codes, off, ln, f, c, out=out, stream=stream)
     torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    out16 = torch.empty_like(out)
+    with torch.cuda.stream(stream):
+        tms.score_pq(lut, codes, off, ln, f, c, out=out16, stream=stream, f16_table=True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     reps = 2
     with torch.cuda.stream(stream):
         e[0].record(stream)
@@ -649,9 +652,14 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
         for _ in range(reps):
             tms.score_pq(lut, codes, off, ln, f, c, out=out, stream=stream)
         e[2].record(stream)
+        for _ in range(reps):
+            tms.score_pq(lut, codes, off, ln, f, c, out=out16, stream=stream, f16_table=True)
+        e[3].record(stream)
     torch.cuda.synchronize()
     lut_ms = e[0].elapsed_time(e[1]) / reps
     pq_ms = e[1].elapsed_time(e[2]) / reps
+    pq16_ms = e[2].elapsed_time(e[3]) / reps
+    rel = ((out16 - out).abs() / out.abs().clamp_min(NQ * 1e-3)).max().item()
     tok4 = int(len4.astype(np.int64).sum()) * nQ4
     alg = iomodel.pq_alg_bytes(tok4, nQ4 * n4, nQ4, NQ, M, K)
     lds = iomodel.pq_lut_reads_bytes(tok4, NQ, M)
@@ -661,6 +669,13 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
                            "frac_hbm": alg / (pq_ms * 1e-3) / 1e9 / hbm_peak,
                            "lds_gbs": lds / (pq_ms * 1e-3) / 1e9, "lds_peak_gbs": lds_peak,
                            "frac_lds": lds / (pq_ms * 1e-3) / 1e9 / lds_peak}
+    # the same pass through the fp16 table: half the shared-memory bytes per lookup
+    lds16 = lds // 2
+    rows["pq_m16_k256_f16_table"] = {"docs_per_s": nQ4 * n4 / (pq16_ms * 1e-3), "kernel_ms": pq16_ms,
+                                     "speedup_vs_fp32_table": pq_ms / pq16_ms,
+                                     "max_rel_diff_vs_fp32_table": rel,
+                                     "lds_gbs": lds16 / (pq16_ms * 1e-3) / 1e9, "lds_peak_gbs": lds_peak,
+                                     "frac_lds": lds16 / (pq16_ms * 1e-3) / 1e9 / lds_peak}
     return rows
 
 
@@ -730,8 +745,9 @@ def run_tms(args, ws, rank, local):
 def profile_case(args):
     """One secondary kernel on a small case (100,000 documents, a few GB):
     fp8_small -- FP8 store, 1 query x 100,000 candidates; pq_small -- PQ
-    M=16 K=256, 8 queries over all documents; shared_small -- bf16 d=256,
-    8 queries over all documents in the shared schedule."""
+    M=16 K=256, 8 queries over all documents (pq16_small: the same through
+    the fp16 table); shared_small -- bf16 d=256, 8 queries over all
+    documents in the shared schedule."""
     import torch
     from paper_2606_26439_gb300 import tms
     dev = torch.device("cuda")
@@ -746,13 +762,14 @@ def profile_case(args):
         co = torch.tensor([0, n], dtype=torch.int64, device=dev)
         run = lambda: tms.score_fp8(qc, qs, tc, ts, off, ln, ids, co)  # noqa: E731
         units = n
-    elif args.profile_case == "pq_small":
+    elif args.profile_case in ("pq_small", "pq16_small"):
         cb, codes, off, ln = synth.device_pq_corpus(lens, 16, 256, 8, 9, device=dev)
         q = synth.queries(8, NQ, 128, "f16", 9).to(dev)
         lut = tms.build_pq_lut(q, cb)
         f = ids.repeat(8)
         co = torch.arange(0, 9 * n, n, dtype=torch.int64, device=dev)
-        run = lambda: tms.score_pq(lut, codes, off, ln, f, co)  # noqa: E731
+        half = args.profile_case == "pq16_small"
+        run = lambda: tms.score_pq(lut, codes, off, ln, f, co, f16_table=half)  # noqa: E731
         units = 8 * n
     else:
         tok, off, ln = synth.device_dense_corpus(lens, 256, "bf16", 9, dev)

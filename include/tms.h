@@ -226,6 +226,28 @@ tms_status tms_score_pq(const float *lut, int n_queries, int nq, int m, int k,
                         float *out_scores, cudaStream_t stream);
 
 /*
+ * Fused PQ MaxSim through an fp16 table: tms_score_pq with every table
+ * entry rounded to the nearest fp16 (ties to even) when it is staged into
+ * shared memory.  Same arguments, layouts and error behaviour as
+ * tms_score_pq; the entries of one token are added in fp32 (each fp16
+ * entry widened exactly), so the only departure from the fp32 table is the
+ * rounding of each entry to 11 significant bits (Section 4.2 keeps the
+ * table in fp32; this is a precision variant of it).  Entries beyond the
+ * fp16 range (|x| > 65504) round to +-inf: use tms_score_pq for such tables.
+ * The table is processed in chunks of 16 query tokens, so a 128 KB chunk
+ * serves twice the query tokens of tms_score_pq and each gather returns
+ * twice the entries.
+ *
+ * Limits: m in {16, 32} (TMS_ERR_UNSUPPORTED otherwise); the rest as for
+ * tms_score_pq.
+ */
+tms_status tms_score_pq_f16(const float *lut, int n_queries, int nq, int m, int k,
+                            const uint8_t *codes, int64_t n_tokens,
+                            const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                            const int32_t *cand_ids, const int64_t *cand_offsets, int64_t n_cand,
+                            float *out_scores, cudaStream_t stream);
+
+/*
  * Top-k per query over scores laid out like out_scores above (Section 6.8).
  *
  *   scores        [n_cand] fp32, query q's list at cand_offsets[q]..[q+1].

@@ -200,9 +200,12 @@ def pq_lut(queries, codebook, *, qdtype=None):
 
 
 def pq_lut_scores(lut, codes, offsets, lengths, cand_ids):
-    """Section 4.2 Phase 2 with a given table ``lut[nq][M][K]`` (fp32 or fp64)."""
+    """Section 4.2 Phase 2 with a given table ``lut[nq][M][K]`` (fp16, fp32 or
+    fp64; every entry read exactly, sums in double)."""
     lt = np.ascontiguousarray(lut)
-    if lt.dtype == np.float32:
+    if lt.dtype == np.float16:
+        ltype = F16
+    elif lt.dtype == np.float32:
         ltype = F32
     else:
         lt = lt.astype(np.float64, copy=False)

@@ -447,7 +447,9 @@ int tmso_pq_lut(const void *queries, int qdtype, int nq, int d,
 /*
  * PQ MaxSim through a distance table (Section 4.2, Phase 2):
  *   score = sum_i max_j sum_m lut[i][m][code_{j,m}]
- * with lut given as [nq][M][K] of ltype (fp32 or fp64), read exactly.
+ * with lut given as [nq][M][K] of ltype (fp16, fp32 or fp64), read exactly
+ * (an fp16 table is the fp32 table of Section 4.2 rounded entry by entry;
+ * the sums stay in double).
  */
 int tmso_pq_lut_scores(const void *lut, int ltype, int nq, int M, int K,
                        const uint8_t *codes, int64_t n_tokens,
@@ -455,7 +457,7 @@ int tmso_pq_lut_scores(const void *lut, int ltype, int nq, int M, int K,
                        const int32_t *cand_ids, int64_t n_cand, double *out)
 {
     if (nq <= 0 || M <= 0 || K <= 0 || n_cand < 0 ||
-        (ltype != TMSO_F32 && ltype != TMSO_F64))
+        (ltype != TMSO_F16 && ltype != TMSO_F32 && ltype != TMSO_F64))
         return -1;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < n_cand; ++c) {

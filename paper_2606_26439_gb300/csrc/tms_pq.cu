@@ -125,7 +125,6 @@ template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel(const Args a) {
     extern __shared__ float lut_s[];  // [M/4][K][4][8]
     __shared__ int next_local;
-    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int g = lane >> 3;  // subspace group
     const int i = lane & 7;   // query token within the chunk
@@ -241,18 +240,30 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel(const Args a) {
 // warp has already issued the copy of the next piece (of this document or of
 // the next one, whose metadata was fetched one document ahead).
 //
-// Gathers are 64-bit: the table chunk is laid out in 256-byte rows
-//     byte ((s / 2) * KS + k) * 256 + (s % 2) * 128 + (m % 4) * 32 + i * 4
+// Gathers are 128-bit: the table chunk is laid out in 256-byte rows
+//     byte ((s / 2) * KS + k) * 256 + (s % 2) * 128 + (m % 4) * 32 + i * E
 // for subspace m = 4 s + (m % 4), code k and query token i (KS = 4096 / M
-// rows per block), and lane (dt = lane / 16, g = (lane / 4) % 4,
-// ip = lane % 4) reads the entries of query tokens 2 ip and 2 ip + 1 for
-// subspace 4 s + g of document token 2 a + dt of a group of four.  One byte
-// permute builds the whole address -- the code byte times 256 plus the lane
-// offset g * 32 + ip * 8 -- and each half-warp's 16 lanes hit 32 distinct
-// banks (one wavefront per half-warp, 64 lookups per instruction).  A
-// transposed shuffle reduction over the four subspace lanes (3 shuffles per
-// four tokens) leaves lane (dt, a = bit 3, u = bit 2, ip) with the full dot
-// of token 2 a + dt and query token 2 ip + u.
+// rows per block; E = 4 bytes and 8 query tokens for the fp32 table, E = 2
+// and 16 query tokens for the fp16 one).  Lane (r = lane / 2, ip = lane % 2)
+// scores document token j + r of a group of sixteen against the query
+// tokens of 16-byte slot ip of a 32-byte section: 4 ip .. 4 ip + 3 for the
+// fp32 table, 8 ip .. 8 ip + 7 for the fp16 one.  Each lane sums all M
+// subspaces of its own token, in an order rotated by g = r % 4: at inner
+// step t of subspace group s it reads subspace 4 s + (t + g) % 4.  One byte
+// permute builds the offset (the code byte times 256 plus the lane offset
+// ((t + g) % 4) * 32 + ip * 16); in each quarter-warp the four values of g
+// meet four different 32-byte sections and the two values of ip the two
+// slots, so the 8 lanes cover all 32 banks (one wavefront per quarter-warp)
+// whatever the codes are.  No cross-lane reduction is needed per token: a
+// lane holds the whole dot of its token and keeps the running max of its
+// query tokens in registers; the lanes of one slot are combined once per
+// document.  fp32 entries are added pairwise with add.rn.f32x2 (two IEEE
+// fp32 additions in one instruction).
+//
+// fp16 table (H16): each entry is rounded to the nearest fp16 when the chunk
+// is staged and added to an fp32 accumulator exactly widened
+// (add.rn.f32.f16); a 128 KB chunk then serves 16 query tokens and every
+// gather returns 8 entries.
 constexpr int kPieceBytes = 2048;  // per buffer: 128 tokens at M = 16
 
 template <int M>
@@ -273,6 +284,47 @@ __device__ __forceinline__ CodeRow<M> smem_codes(const uint8_t* row) {
     return c;
 }
 
+// acc0 += lo half of w, acc1 += hi half of w (fp16 widened exactly, one
+// fp32 rounding per add)
+__device__ __forceinline__ void add_f16x2(float& acc0, float& acc1, uint32_t w) {
+    asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "add.rn.f32.f16 %0, lo, %0;\n\tadd.rn.f32.f16 %1, hi, %1;\n\t}"
+        : "+f"(acc0), "+f"(acc1)
+        : "r"(w));
+}
+
+// 16-byte shared-memory load at shared-window address addr + OFF
+template <int OFF>
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr), "n"(OFF));
+    return v;
+}
+
+// acc (two fp32 in one 64-bit register, x low) += (x, y), element-wise
+__device__ __forceinline__ void add_f32x2(unsigned long long& acc, uint32_t x, uint32_t y) {
+    asm("{\n\t.reg .b64 e;\n\tmov.b64 e, {%1, %2};\n\tadd.rn.f32x2 %0, %0, e;\n\t}"
+        : "+l"(acc)
+        : "r"(x), "r"(y));
+}
+
+// All M table entries of one token for this lane: subspace group sg, inner
+// step t reads subspace 4 sg + (t + g) % 4 at the shared-window address
+// tbl + block offset of sg + code * 256 + lane offset; f consumes each
+// 16-byte gather in order.
+template <int M, int KS, int SG = 0, typename F>
+__device__ __forceinline__ void gather_groups(const CodeRow<M>& c, uint32_t tbl, const uint32_t (&lane_off)[4],
+                                              const uint32_t (&sel)[4], F&& f) {
+    if constexpr (SG < M / 4) {
+        constexpr int kOff = (SG >> 1) * KS * 256 + (SG & 1) * 128;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) f(lds128<kOff>(tbl + __byte_perm(c.w[SG], lane_off[t], sel[t])));
+        gather_groups<M, KS, SG + 1>(c, tbl, lane_off, sel, static_cast<F&&>(f));
+    }
+}
+
 struct PendingMeta {
     int64_t li;  // local candidate index (>= n_local: none)
     int id;
@@ -284,29 +336,36 @@ struct PendingMeta {
 // a code >= k still reads inside the allocation.
 __host__ __device__ constexpr int staged_table_bytes(int M) { return ((M / 8 - 1) * (4096 / M) + 256) * 256; }
 
-template <int M>
+template <int M, bool H16>
 __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args a, int lut_bytes) {
     constexpr int kPiece = kPieceBytes / M;  // tokens per piece
     constexpr int KS = 4096 / M;             // table rows per block
+    constexpr int QC = H16 ? 16 : kQC;       // query tokens per chunk
     extern __shared__ __align__(128) uint8_t smem_raw[];
     float* lut_s = reinterpret_cast<float*>(smem_raw);
-    const uint8_t* tbl = smem_raw;
+    const uint32_t tbl_sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw));
     uint8_t* bufs = smem_raw + lut_bytes;  // [kWarps][2][kPieceBytes]
     __shared__ uint64_t bars[kWarps][2];
     __shared__ int next_local;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int dt = lane >> 4;                          // token of a pair this half-warp scores
-    const int g = (lane >> 2) & 3;                     // subspace within each group of four
-    const int ip = lane & 3;                           // query tokens 2 ip, 2 ip + 1
-    const int qt = 2 * ip + ((lane >> 2) & 1);         // query token this lane ends with
-    const uint32_t lane_off = static_cast<uint32_t>(g * 32 + ip * 8);
-    // byte permute: result byte 0 = lane offset, byte 1 = code byte g, bytes 2-3 = 0
-    const uint32_t sel = 0x6504u | (static_cast<uint32_t>(g) << 4);
+    constexpr int QL = H16 ? 8 : 4;                    // query tokens per lane
+    const int r = lane >> 1;                           // token of the group of sixteen
+    const int g = r & 3;                               // rotation of the subspace order
+    const int ip = lane & 1;                           // 16-byte slot: query tokens QL ip .. QL ip + QL - 1
+    const int qt = QL * ip;
+    // byte permute per inner step t: result byte 0 = lane offset, byte 1 =
+    // code byte (t + g) % 4 of the group's word, bytes 2-3 = 0
+    uint32_t lane_off[4], sel[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const uint32_t mm = static_cast<uint32_t>((t + g) & 3);
+        lane_off[t] = mm * 32 + static_cast<uint32_t>(ip * 16);
+        sel[t] = 0x6504u | (mm << 4);
+    }
     const int K = a.K;
-    const int nchunks = (a.nq + kQC - 1) / kQC;
-    const int words = lut_bytes / 4;
+    const int nchunks = (a.nq + QC - 1) / QC;
     uint8_t* wbuf = bufs + warp * 2 * kPieceBytes;
     uint64_t* wbar = bars[warp];
 
@@ -330,17 +389,47 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args
         const int64_t n_local = (c1 - c0 - blockIdx.x + gridDim.x - 1) / gridDim.x;
         for (int ch = 0; ch < nchunks; ++ch) {
             __syncthreads();
-            const float* src = a.lut + static_cast<int64_t>(q) * a.nq * M * K;
-            for (int w = threadIdx.x; w < words; w += blockDim.x) {
-                const int ii = w & 7;
-                const int ml = (w >> 3) & 3;
-                const int slo = (w >> 5) & 1;
-                const int rest = w >> 6;
-                const int shi = min(rest / KS, M / 8 - 1);
-                const int kk = rest - shi * KS;
-                const int m = 4 * (2 * shi + slo) + ml;
-                const int qi = ch * kQC + ii;
-                lut_s[w] = (qi < a.nq && kk < K) ? __ldg(src + (static_cast<int64_t>(qi) * M + m) * K + kk) : 0.f;
+            // Table chunk -> shared memory.  A warp fills 8 rows x one 128-byte
+            // half (slo) per task; lane (ii, ml) reads 8 consecutive codes of
+            // table row (query token, subspace) -- whole sectors -- and each
+            // store instruction writes 32 consecutive words.  Rows of codes >= k
+            // and query tokens >= nq are filled with zeros.
+            {
+                const float* src = a.lut + static_cast<int64_t>(q) * a.nq * M * K;
+                const int ii = lane & 7;
+                const int ml = lane >> 3;
+                const int tasks = (lut_bytes / 256 / 8) * 2;
+                for (int task = warp; task < tasks; task += kWarps) {
+                    const int slo = task & 1;
+                    const int rho0 = (task >> 1) * 8;               // KS is a multiple of 8
+                    const int shi = min(rho0 / KS, M / 8 - 1);
+                    const int kk0 = rho0 - shi * KS;
+                    const int m = 4 * (2 * shi + slo) + ml;
+                    float* dst = lut_s + rho0 * 64 + slo * 32 + ml * 8 + ii;
+                    if constexpr (H16) {  // query tokens 2 ii and 2 ii + 1, rounded to nearest fp16
+                        const int qi = ch * QC + 2 * ii;
+                        const float* r0 = src + (static_cast<int64_t>(qi) * M + m) * K;
+                        const float* r1 = r0 + static_cast<int64_t>(M) * K;
+                        const bool ok0 = qi < a.nq, ok1 = qi + 1 < a.nq;
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) {
+                            const int kk = kk0 + x;
+                            const float t0 = (ok0 && kk < K) ? __ldg(r0 + kk) : 0.f;
+                            const float t1 = (ok1 && kk < K) ? __ldg(r1 + kk) : 0.f;
+                            const __half2 h = __floats2half2_rn(t0, t1);
+                            dst[x * 64] = *reinterpret_cast<const float*>(&h);
+                        }
+                    } else {
+                        const int qi = ch * QC + ii;
+                        const float* r0 = src + (static_cast<int64_t>(qi) * M + m) * K;
+                        const bool ok0 = qi < a.nq;
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) {
+                            const int kk = kk0 + x;
+                            dst[x * 64] = (ok0 && kk < K) ? __ldg(r0 + kk) : 0.f;
+                        }
+                    }
+                }
             }
             if (threadIdx.x == 0) next_local = 0;
             __syncthreads();
@@ -417,7 +506,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args
             while (f >= 0 && ok) {
                 int64_t nf = -1, noff = 0;
                 int nlen = 0;
-                float rmax = -INFINITY;
+                float rmax[QL];
+#pragma unroll
+                for (int u = 0; u < QL; ++u) rmax[u] = -INFINITY;
                 for (int start = 0; start < len; start += kPiece) {
                     const int cnt = min(kPiece, len - start);
                     if (start + kPiece < len) {
@@ -435,47 +526,52 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args
                     }
                     const uint8_t* base = wbuf + b * kPieceBytes;
                     const int last = cnt - 1;
-                    for (int j = 0; j < cnt; j += 4) {
-                        // this lane's tokens: j + dt and j + 2 + dt (a duplicate of the
-                        // last token past the end cannot change a max)
-                        const CodeRow<M> c0 = smem_codes<M>(base + min(j + dt, last) * M);
-                        const CodeRow<M> c1 = smem_codes<M>(base + min(j + 2 + dt, last) * M);
-                        float v00 = 0.f, v01 = 0.f, v10 = 0.f, v11 = 0.f;  // [token pair a][query token u]
+                    // this lane's token j + r (a duplicate of the last token past the
+                    // end cannot change a max); the next group's codes load early
+                    CodeRow<M> c = smem_codes<M>(base + min(r, last) * M);
+                    for (int j = 0; j < cnt; j += 16) {
+                        const CodeRow<M> cn = smem_codes<M>(base + min(j + 16 + r, last) * M);
+                        float acc[QL];
+                        if constexpr (H16) {
 #pragma unroll
-                        for (int sg = 0; sg < M / 4; ++sg) {
-                            const int boff = (sg >> 1) * KS * 256 + (sg & 1) * 128;
-                            const float2 t0 =
-                                *reinterpret_cast<const float2*>(tbl + boff + __byte_perm(c0.w[sg], lane_off, sel));
-                            const float2 t1 =
-                                *reinterpret_cast<const float2*>(tbl + boff + __byte_perm(c1.w[sg], lane_off, sel));
-                            v00 += t0.x;
-                            v01 += t0.y;
-                            v10 += t1.x;
-                            v11 += t1.y;
+                            for (int u = 0; u < QL; ++u) acc[u] = 0.f;
+                            gather_groups<M, KS>(c, tbl_sa, lane_off, sel, [&](const uint4& e) {
+                                add_f16x2(acc[0], acc[1], e.x);
+                                add_f16x2(acc[2], acc[3], e.y);
+                                add_f16x2(acc[4], acc[5], e.z);
+                                add_f16x2(acc[6], acc[7], e.w);
+                            });
+                        } else {
+                            unsigned long long p01 = 0ull, p23 = 0ull;  // (acc0, acc1), (acc2, acc3)
+                            gather_groups<M, KS>(c, tbl_sa, lane_off, sel, [&](const uint4& e) {
+                                add_f32x2(p01, e.x, e.y);
+                                add_f32x2(p23, e.z, e.w);
+                            });
+                            acc[0] = __uint_as_float(static_cast<uint32_t>(p01));
+                            acc[1] = __uint_as_float(static_cast<uint32_t>(p01 >> 32));
+                            acc[2] = __uint_as_float(static_cast<uint32_t>(p23));
+                            acc[3] = __uint_as_float(static_cast<uint32_t>(p23 >> 32));
                         }
-                        // sum over the four subspace lanes: keep pair a = bit 3, then u = bit 2
-                        const bool b3 = (lane & 8) != 0;
-                        float k0 = b3 ? v10 : v00;
-                        float k1 = b3 ? v11 : v01;
-                        const float s0 = b3 ? v00 : v10;
-                        const float s1 = b3 ? v01 : v11;
-                        k0 += __shfl_xor_sync(0xffffffffu, s0, 8);
-                        k1 += __shfl_xor_sync(0xffffffffu, s1, 8);
-                        const bool b2 = (lane & 4) != 0;
-                        float kk = b2 ? k1 : k0;
-                        const float ss = b2 ? k0 : k1;
-                        kk += __shfl_xor_sync(0xffffffffu, ss, 4);
-                        rmax = fmaxf(rmax, kk);
+#pragma unroll
+                        for (int u = 0; u < QL; ++u) rmax[u] = fmaxf(rmax[u], acc[u]);
+                        c = cn;
                     }
                     __syncwarp();
                 }
                 if (!ok) break;
-                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 8));
-                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, 16));
-                float v = (ch * kQC + qt < a.nq) ? rmax : 0.f;
+                // max over the sixteen token lanes of each slot, then the sum over
+                // this chunk's query tokens (u ascending, then the two slots)
+                float v = 0.f;
+#pragma unroll
+                for (int u = 0; u < QL; ++u) {
+                    float m = rmax[u];
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+                    v += (ch * QC + qt + u < a.nq) ? m : 0.f;
+                }
                 v += __shfl_xor_sync(0xffffffffu, v, 1);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
                 if (lane == 0) a.out[f] = (ch == 0) ? v : a.out[f] + v;
                 f = nf;
                 off = noff;
@@ -522,14 +618,16 @@ extern "C" tms_status tms_build_pq_lut(const void* queries, tms_dtype qdtype, in
     return launch_status(cudaGetLastError());
 }
 
-extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int m, int k, const uint8_t* codes,
-                                   int64_t n_tokens, const int64_t* doc_offsets, const int32_t* doc_lengths,
-                                   int64_t n_docs, const int32_t* cand_ids, const int64_t* cand_offsets,
-                                   int64_t n_cand, float* out_scores, cudaStream_t stream) {
-    using namespace tms;
+namespace tms {
+namespace pq {
+
+// Shared host checks and launch of tms_score_pq / tms_score_pq_f16.
+tms_status score(const float* lut, int n_queries, int nq, int m, int k, const uint8_t* codes, int64_t n_tokens,
+                 const int64_t* doc_offsets, const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
+                 const int64_t* cand_offsets, int64_t n_cand, float* out_scores, bool half, cudaStream_t stream) {
     if (n_queries < 1 || n_queries > 4096 || nq < 1 || nq > 128 || k < 1 || k > 256) return TMS_ERR_INVALID_ARG;
     if (m != 4 && m != 8 && m != 16 && m != 32) return TMS_ERR_UNSUPPORTED;
-    if (m * k > 4096) return TMS_ERR_UNSUPPORTED;
+    if (m * k > 4096 || (half && m < 16)) return TMS_ERR_UNSUPPORTED;
     if (n_tokens < 0 || n_docs < 0 || n_cand < 0 || n_cand >= (int64_t(1) << 31)) return TMS_ERR_INVALID_ARG;
     if (!lut || !cand_offsets || !aligned16(lut) || !aligned16(cand_offsets)) return TMS_ERR_INVALID_ARG;
     if (n_cand > 0 && (!cand_ids || !out_scores || !aligned16(cand_ids) || !aligned16(out_scores)))
@@ -541,7 +639,7 @@ extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int 
     DeviceInfo dev;
     tms_status st = current_device(&dev);
     if (st != TMS_OK) return st;
-    pq::Args a{};
+    Args a{};
     a.lut = lut;
     a.codes = codes;
     a.offsets = doc_offsets;
@@ -559,31 +657,49 @@ extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int 
     // The last subspace group is sized for 256 codes so that a code >= k
     // still indexes inside the allocation.
     const int smem = ((m / 4 - 1) * k + 256) * 32 * 4;
-    const int tbl_st = pq::staged_table_bytes(m >= 16 ? m : 16);
-    const int smem_st = tbl_st + pq::kWarps * 2 * pq::kPieceBytes;  // staged variant: table + piece buffers
+    const int tbl_st = staged_table_bytes(m >= 16 ? m : 16);
+    const int smem_st = tbl_st + kWarps * 2 * kPieceBytes;  // staged variant: table + piece buffers
     if ((m >= 16 ? smem_st : smem) > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(dev.sm_count, n_cand));
-    cudaError_t e = cudaSuccess;
-    switch (m) {
-        case 4:
-            e = cudaFuncSetAttribute(pq::score_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e == cudaSuccess) pq::score_kernel<4><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
-            break;
-        case 8:
-            e = cudaFuncSetAttribute(pq::score_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e == cudaSuccess) pq::score_kernel<8><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem, stream>>>(a);
-            break;
-        case 16:
-            e = cudaFuncSetAttribute(pq::score_kernel_staged<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
-            if (e == cudaSuccess)
-                pq::score_kernel_staged<16><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, tbl_st);
-            break;
-        default:
-            e = cudaFuncSetAttribute(pq::score_kernel_staged<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
-            if (e == cudaSuccess)
-                pq::score_kernel_staged<32><<<static_cast<unsigned>(grid), pq::kWarps * 32, smem_st, stream>>>(a, tbl_st);
-            break;
-    }
+    const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(dev.sm_count, n_cand)));
+    const unsigned threads = kWarps * 32;
+    auto staged = [&](auto kernel) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
+        if (e == cudaSuccess) kernel<<<grid, threads, smem_st, stream>>>(a, tbl_st);
+        return e;
+    };
+    auto plain = [&](auto kernel) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) kernel<<<grid, threads, smem, stream>>>(a);
+        return e;
+    };
+    cudaError_t e;
+    if (m == 4)
+        e = plain(score_kernel<4>);
+    else if (m == 8)
+        e = plain(score_kernel<8>);
+    else if (m == 16)
+        e = half ? staged(score_kernel_staged<16, true>) : staged(score_kernel_staged<16, false>);
+    else
+        e = half ? staged(score_kernel_staged<32, true>) : staged(score_kernel_staged<32, false>);
     if (e != cudaSuccess) return launch_status(e);
     return launch_status(cudaGetLastError());
+}
+
+}  // namespace pq
+}  // namespace tms
+
+extern "C" tms_status tms_score_pq(const float* lut, int n_queries, int nq, int m, int k, const uint8_t* codes,
+                                   int64_t n_tokens, const int64_t* doc_offsets, const int32_t* doc_lengths,
+                                   int64_t n_docs, const int32_t* cand_ids, const int64_t* cand_offsets,
+                                   int64_t n_cand, float* out_scores, cudaStream_t stream) {
+    return tms::pq::score(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs, cand_ids,
+                          cand_offsets, n_cand, out_scores, false, stream);
+}
+
+extern "C" tms_status tms_score_pq_f16(const float* lut, int n_queries, int nq, int m, int k, const uint8_t* codes,
+                                       int64_t n_tokens, const int64_t* doc_offsets, const int32_t* doc_lengths,
+                                       int64_t n_docs, const int32_t* cand_ids, const int64_t* cand_offsets,
+                                       int64_t n_cand, float* out_scores, cudaStream_t stream) {
+    return tms::pq::score(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs, cand_ids,
+                          cand_offsets, n_cand, out_scores, true, stream);
 }

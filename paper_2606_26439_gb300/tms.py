@@ -31,8 +31,8 @@ TMS_DEVERR_BAD_CSR = 8
 
 #: every symbol include/tms.h declares
 EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
-           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk", "tms_server_create",
-           "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy",
+           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16", "tms_topk",
+           "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy",
            "tms_get_device_error", "tms_status_string", "tms_version")
 
 TMS_STORE_DENSE, TMS_STORE_PQ = 0, 1
@@ -91,6 +91,7 @@ def lib(build_if_missing: bool = True):
             L.tms_score_fp8_shared.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p]
             L.tms_build_pq_lut.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _p]
             L.tms_score_pq.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_score_pq_f16.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
             L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
             L.tms_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
             L.tms_server_submit.argtypes = [_p, _i32, _p, _p, _i64, ctypes.POINTER(ctypes.c_uint64)]
@@ -103,7 +104,7 @@ def lib(build_if_missing: bool = True):
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
             for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
-                         "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_topk",
+                         "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16", "tms_topk",
                          "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
                          "tms_server_destroy", "tms_get_device_error", "tms_version"):
                 getattr(L, name).restype = ctypes.c_int
@@ -158,6 +159,12 @@ def tms_score_pq(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_len
                  cand_ids, cand_offsets, n_cand, out_scores, stream) -> int:
     return lib().tms_score_pq(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs,
                               cand_ids, cand_offsets, n_cand, out_scores, stream)
+
+
+def tms_score_pq_f16(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs,
+                     cand_ids, cand_offsets, n_cand, out_scores, stream) -> int:
+    return lib().tms_score_pq_f16(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs,
+                                  cand_ids, cand_offsets, n_cand, out_scores, stream)
 
 
 def tms_topk(scores, cand_offsets, n_queries, topk, out_scores, out_pos, stream) -> int:
@@ -311,14 +318,19 @@ def build_pq_lut(queries, codebook, out=None, stream=None):
     return out
 
 
-def score_pq(lut, codes, doc_offsets, doc_lengths, cand_ids, cand_offsets, out=None, stream=None):
-    """Fused PQ MaxSim from a table [n_queries][nq][m][k] and codes [n_tokens][m]."""
+def score_pq(lut, codes, doc_offsets, doc_lengths, cand_ids, cand_offsets, out=None, stream=None,
+             f16_table=False):
+    """Fused PQ MaxSim from a table [n_queries][nq][m][k] and codes [n_tokens][m].
+
+    ``f16_table=True`` scores through the table rounded to fp16
+    (tms_score_pq_f16)."""
     torch = _torch()
     nQ, nq, m, k = lut.shape
     n_cand = cand_ids.shape[0]
     if out is None:
         out = torch.empty(n_cand, dtype=torch.float32, device=lut.device)
-    _check("tms_score_pq", tms_score_pq(
+    fn, name = (tms_score_pq_f16, "tms_score_pq_f16") if f16_table else (tms_score_pq, "tms_score_pq")
+    _check(name, fn(
         _dev(lut, torch.float32), nQ, nq, m, k, _dev(codes, torch.uint8), codes.shape[0],
         _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
         _dev(cand_ids, torch.int32), _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32),

@@ -4,6 +4,12 @@
 * code gathering: bit-exact -- with an integer-valued table every sum is
   exact, so the GPU score must equal the oracle's exact table-sum score;
 * scores: within 1e-3 relative of FP64 decompress-then-dot (fp16 queries).
+
+The fp16-table variant (tms_score_pq_f16) runs every check too, with two of
+its own: a table of multiples of 1/2 whose fp16 rounding includes exact ties
+scores bit for bit like the oracle on the table rounded to nearest-even
+fp16 (rounded sums stay exact in fp32), and a random table stays within the
+fp32 summation bound of that rounded-table score.
 """
 from __future__ import annotations
 
@@ -27,13 +33,13 @@ def _gpu_lut(Q, cb):
     return lut
 
 
-def _gpu_pq(lut_d, codes, off, ln, cands):
+def _gpu_pq(lut_d, codes, off, ln, cands, f16=False):
     import torch
     from paper_2606_26439_gb300 import tms
     flat, co = gc.csr(cands)
     c_d, o_d, l_d, f_d, co_d = gc.to_dev(codes, off, ln, flat, co)
     out = torch.full((len(flat),), 12345.0, dtype=torch.float32, device="cuda")
-    tms.score_pq(lut_d, c_d, o_d, l_d, f_d, co_d, out=out)
+    tms.score_pq(lut_d, c_d, o_d, l_d, f_d, co_d, out=out, f16_table=f16)
     torch.cuda.synchronize()
     return out.cpu().numpy(), tms.device_error()
 
@@ -81,8 +87,9 @@ def test_pq_gather_bit_exact_integer_table(cuda_lib, M, nq):
     assert np.array_equal(got[fin].astype(np.float64), want[fin])
 
 
+@pytest.mark.parametrize("f16", [False, True])
 @pytest.mark.parametrize("nq", [32, 9])
-def test_pq_scores_vs_decompress(cuda_lib, nq):
+def test_pq_scores_vs_decompress(cuda_lib, nq, f16):
     """GPU table (tms_build_pq_lut) + fused scoring vs FP64
     decompress-then-dot on the same fp16 queries and fp32 codebook."""
     M, K, dsub = 16, 256, 8
@@ -92,15 +99,28 @@ def test_pq_scores_vs_decompress(cuda_lib, nq):
     Q = synth.queries(3, nq, d, "f16", 50)
     cands = [synth.candidates(400, n, 50, i) for i, n in enumerate((400, 250, 37))]
     lut_d = _gpu_lut(Q, cb)
-    got, flags = _gpu_pq(lut_d, codes, off, ln, cands)
+    got, flags = _gpu_pq(lut_d, codes, off, ln, cands, f16)
     assert flags == 0
     qa, qdt = oracle_view(Q)
     want = np.concatenate([oracle.pq_decompress_scores(qa[i], cb, codes, off, ln, c, qdtype=qdt)
                            for i, c in enumerate(cands)])
-    assert_scores_close(got, want, "f16", nq)
+    if not f16:
+        assert_scores_close(got, want, "f16", nq)
+        return
+    # fp16 table: each entry carries a relative rounding error <= 2^-11 on top
+    # of the fp32 table error (<= 2 dsub 2^-24 sum_t |q_t c_t|) and the fp32
+    # sums, so |err| <= (2^-11 + 2^-24 (2 dsub + M + nq + 2)) * A with
+    # A = sum_i max_j sum_m sum_t |q_t| |c_t| -- a bound on the table's
+    # magnitude, not on the score, which may nearly cancel.
+    qabs = np.abs(Q.double().numpy())
+    A = np.concatenate([oracle.pq_lut_scores(oracle.pq_lut(qabs[i], np.abs(cb), qdtype=oracle.F64), codes, off,
+                                             ln, c) for i, c in enumerate(cands)])
+    bound = (2.0 ** -11 + 2.0 ** -24 * (2 * dsub + M + nq + 2)) * A
+    assert np.all(np.abs(got - want) <= bound)
 
 
-def test_pq_edge_documents_and_flags(cuda_lib):
+@pytest.mark.parametrize("f16", [False, True])
+def test_pq_edge_documents_and_flags(cuda_lib, f16):
     """Empty documents score -inf, bad ids NaN with the error flag raised."""
     from paper_2606_26439_gb300 import tms
     import torch
@@ -110,27 +130,29 @@ def test_pq_edge_documents_and_flags(cuda_lib):
     codes = np.random.default_rng(1).integers(0, K, size=(8, M)).astype(np.uint8)
     T = np.random.default_rng(2).standard_normal((1, nq, M, K)).astype(np.float32)
     got, flags = _gpu_pq(torch.from_numpy(T).cuda(), codes, off, lengths,
-                         [np.array([0, 1, 2, 3, -5, 4], np.int32)])
+                         [np.array([0, 1, 2, 3, -5, 4], np.int32)], f16)
     assert got[0] == -np.inf and got[2] == -np.inf
     assert np.isnan(got[4]) and np.isnan(got[5])
     assert np.isfinite(got[1]) and np.isfinite(got[3])
     assert flags & tms.TMS_DEVERR_BAD_ID
 
 
-def test_pq_bitwise_repeatable(cuda_lib):
+@pytest.mark.parametrize("f16", [False, True])
+def test_pq_bitwise_repeatable(cuda_lib, f16):
     M, K, dsub = 16, 256, 8
     lengths = synth.lengths_uniform(800, 32, 300, 51)
     cb, codes, _, off, ln = synth.pq_corpus(lengths, M, K, dsub, 51)
     Q = synth.queries(2, 32, M * dsub, "f16", 51)
     cands = [synth.candidates(800, 800, 51, 0), synth.candidates(800, 300, 51, 1)]
     lut_d = _gpu_lut(Q, cb)
-    a, _ = _gpu_pq(lut_d, codes, off, ln, cands)
-    b, _ = _gpu_pq(lut_d, codes, off, ln, cands)
+    a, _ = _gpu_pq(lut_d, codes, off, ln, cands, f16)
+    b, _ = _gpu_pq(lut_d, codes, off, ln, cands, f16)
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
 @pytest.mark.slow
-def test_config4_pq_full_size_sampled(cuda_lib):
+@pytest.mark.parametrize("f16", [False, True])
+def test_config4_pq_full_size_sampled(cuda_lib, f16):
     """1,000,000 documents, Nd ~ U[32, 180], M = 16, K = 256, dsub = 8,
     Gaussian centroids + N(0, 0.05) noise, nearest-centroid codes; 64 fp16
     queries each over all documents.  Sampled parity vs decompress-then-dot."""
@@ -146,7 +168,7 @@ def test_config4_pq_full_size_sampled(cuda_lib):
     cands = [np.arange(n_docs, dtype=np.int32)] * n_queries
     flat, co = gc.csr(cands)
     f_d, co_d = gc.to_dev(flat, co)
-    out = tms.score_pq(lut_d, codes_d, off_d, ln_d, f_d, co_d)
+    out = tms.score_pq(lut_d, codes_d, off_d, ln_d, f_d, co_d, f16_table=f16)
     torch.cuda.synchronize()
     assert tms.device_error() == 0
     scores = out.cpu().numpy()
@@ -168,3 +190,75 @@ def test_config4_pq_full_size_sampled(cuda_lib):
         want[sel] = oracle.pq_decompress_scores(qa[qi], cb, sub_codes, sub_off, sub_len, sel.astype(np.int32),
                                                 qdtype=qdt)
     assert_scores_close(scores[pos], want, "f16", nq)
+
+
+def _ragged_pq_case(M, K, nq, seed, n_queries=2):
+    g = np.random.default_rng(seed)
+    lengths = np.array(gc.EDGE_LENGTHS + list(g.integers(1, 150, 60)) + [77], np.int32)
+    off = synth.offsets_of(lengths)
+    codes = g.integers(0, K, size=(int(lengths.sum()), M)).astype(np.uint8)
+    cands = gc.edge_candidates(len(lengths), n_queries, seed)
+    return g, lengths, off, codes, cands
+
+
+@pytest.mark.parametrize("M", [16, 32])
+@pytest.mark.parametrize("nq", [1, 7, 15, 16, 17, 32, 33, 128])
+def test_pq_f16_half_integer_table_bit_exact(cuda_lib, M, nq):
+    """Table entries are multiples of 1/2 up to 4000 in magnitude, so fp16
+    rounding meets exact ties (x.5 in [1024, 2048), odd integers in
+    [2048, 4096)).  Every rounded entry is a multiple of 1/2 and every sum
+    stays exact in fp32, so the GPU must equal the oracle on the table
+    rounded to nearest-even fp16 bit for bit (a truncating or
+    ties-away rounding, a wrong query token or half of a word would not)."""
+    import torch
+    K = 256 if M == 16 else 128
+    n_queries = 2
+    g, lengths, off, codes, cands = _ragged_pq_case(M, K, nq, M * 1000 + nq)
+    T = (g.integers(-8000, 8001, size=(n_queries, nq, M, K)) / 2).astype(np.float32)
+    T16 = T.astype(np.float16)   # IEEE round to nearest, ties to even
+    assert np.any(T16.astype(np.float32) != T)   # ties and roundings were met
+    got, flags = _gpu_pq(torch.from_numpy(T).cuda(), codes, off, lengths, cands, f16=True)
+    want = np.concatenate([oracle.pq_lut_scores(T16[qi], codes, off, lengths, c) for qi, c in enumerate(cands)])
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.array_equal(got[ok].astype(np.float64), want[ok])
+
+
+@pytest.mark.parametrize("M,K", [(16, 256), (32, 128), (16, 100)])
+@pytest.mark.parametrize("nq", [9, 32])
+def test_pq_f16_random_table_within_fp32_sum_bound(cuda_lib, M, K, nq):
+    """Random fp32 table: the GPU score is the score of the fp16-rounded
+    table up to fp32 summation, |err| <= 2^-24 (M + nq + 2) sum_i max_j
+    sum_m |T16| -- far below one fp16 rounding step of one entry in most
+    scores, so a table read in fp32 (not rounded) fails too."""
+    import torch
+    n_queries = 2
+    g, lengths, off, codes, cands = _ragged_pq_case(M, K, nq, 7 * M + nq + K)
+    T = (g.standard_normal((n_queries, nq, M, K)) * 0.7).astype(np.float32)
+    T16 = T.astype(np.float16)
+    got, flags = _gpu_pq(torch.from_numpy(T).cuda(), codes, off, lengths, cands, f16=True)
+    want = np.concatenate([oracle.pq_lut_scores(T16[qi], codes, off, lengths, c) for qi, c in enumerate(cands)])
+    want32 = np.concatenate([oracle.pq_lut_scores(T[qi], codes, off, lengths, c) for qi, c in enumerate(cands)])
+    mag = np.concatenate([oracle.pq_lut_scores(np.abs(T16[qi]).astype(np.float64), codes, off, lengths, c)
+                          for qi, c in enumerate(cands)])
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    fin = np.isfinite(want)
+    assert np.array_equal(got[~fin & ~np.isnan(want)], want[~fin & ~np.isnan(want)])
+    bound = 2.0 ** -24 * (M + nq + 2) * mag[fin]
+    assert np.all(np.abs(got[fin] - want[fin]) <= bound)
+    # the rounding is really applied: the fp32-table score is outside the bound somewhere
+    assert np.any(np.abs(got[fin] - want32[fin]) > bound)
+
+
+def test_pq_f16_rejects_small_m(cuda_lib):
+    import torch
+    from paper_2606_26439_gb300 import tms
+    T = torch.zeros((1, 4, 8, 16), dtype=torch.float32, device="cuda")
+    codes = torch.zeros((4, 8), dtype=torch.uint8, device="cuda")
+    off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ln = torch.full((1,), 4, dtype=torch.int32, device="cuda")
+    f = torch.zeros(1, dtype=torch.int32, device="cuda")
+    co = torch.tensor([0, 1], dtype=torch.int64, device="cuda")
+    with pytest.raises(tms.TmsError) as e:
+        tms.score_pq(T, codes, off, ln, f, co, f16_table=True)
+    assert e.value.status == tms.TMS_ERR_UNSUPPORTED

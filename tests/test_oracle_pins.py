@@ -306,6 +306,37 @@ def test_pq_lut_scores_integer_table_exact():
         assert got[c] == want
 
 
+def test_pq_lut_scores_f16_table_brute_force():
+    """An fp16 table is read exactly: the score equals the brute-force
+    Python-float evaluation of sum_i max_j sum_m T[i][m][c] over the fp16
+    values (m ascending, the oracle's order), and the same values given as
+    fp64 (a misread half -- wrong byte order, exponent bias or subnormal --
+    changes the score)."""
+    g = np.random.default_rng(25)
+    nq, M, K = 5, 16, 64
+    T = (g.standard_normal((nq, M, K)) * 3).astype(np.float16)
+    T[0, 0, :8] = np.array([6e-8, -6e-8, 1e-5, 65504, -65504, 0.0, -0.0, 2.0 ** -14], np.float16)
+    lengths = np.array([1, 3, 9], np.int32)
+    off = synth.offsets_of(lengths)
+    codes = g.integers(0, K, size=(int(lengths.sum()), M)).astype(np.uint8)
+    codes[0, 0] = 3   # the 65504 entry
+    cand = np.array([2, 0, 1], np.int32)
+    got = oracle.pq_lut_scores(T, codes, off, lengths, cand)
+    np.testing.assert_array_equal(got, oracle.pq_lut_scores(T.astype(np.float64), codes, off, lengths, cand))
+    for c, doc in enumerate(cand):
+        rows = codes[off[doc]:off[doc] + lengths[doc]]
+        total = 0.0
+        for i in range(nq):
+            best = -math.inf
+            for r in rows:
+                acc = 0.0
+                for m in range(M):
+                    acc += float(T[i, m, r[m]])
+                best = max(best, acc)
+            total += best
+        assert got[c] == total
+
+
 def test_pq_invalid_code_is_nan():
     cb = np.zeros((2, 4, 2), np.float32)
     codes = np.array([[0, 4]], np.uint8)
