@@ -264,14 +264,15 @@ tms_status tms_topk(const float *scores, const int64_t *cand_offsets, int n_quer
 
 /*
  * Serving loop: a device-resident corpus (a dense store and optionally a PQ
- * store) and a worker thread that scores requests -- one query of nq tokens
+ * store and an FP8 copy of the dense store) and a worker thread that scores
+ * requests -- one query of nq tokens
  * against its own candidate list, top-k back to the host -- with continuous
  * batching: every launch takes all pending requests that fit the batch
  * buffers, requests arriving meanwhile go into the next launch, and the
  * host side of one batch (staging, completion) overlaps the GPU work of the
- * next.  Scores come from tms_score_dense / tms_score_pq and tms_topk, whose
- * results do not depend on the batch they run in: a request's result is
- * bitwise the same alone and in any mix.
+ * next.  Scores come from tms_score_dense / tms_score_pq / tms_score_fp8
+ * and tms_topk, whose results do not depend on the batch they run in: a
+ * request's result is bitwise the same alone and in any mix.
  *
  * The config's device pointers are owned by the caller and must stay valid
  * until tms_server_destroy; the server owns its own batch buffers (device
@@ -280,7 +281,7 @@ tms_status tms_topk(const float *scores, const int64_t *cand_offsets, int n_quer
  */
 typedef struct tms_server tms_server;
 
-typedef enum { TMS_STORE_DENSE = 0, TMS_STORE_PQ = 1 } tms_store;
+typedef enum { TMS_STORE_DENSE = 0, TMS_STORE_PQ = 1, TMS_STORE_FP8 = 2 } tms_store;
 
 typedef struct {
     /* dense store (required), as for tms_score_dense */
@@ -301,6 +302,18 @@ typedef struct {
     const int64_t *pq_offsets;
     const int32_t *pq_lengths;
     int64_t pq_n_docs;
+    /* FP8 store (optional: fp8_codes == NULL for none): the dense store's
+     * documents as E4M3 codes with one fp32 scale per token (as written by
+     * tms_quantize_e4m3 from doc_tokens), with the dense store's ids,
+     * offsets and lengths; needs d % 16 == 0.  A request to it has its
+     * query quantized on the device and every candidate scored by
+     * tms_score_fp8; with rescore_k > 0 its rescore_k best candidates are
+     * scored again on the dense store (tms_score_dense) and the top-k is
+     * taken from those fp16 scores, so the returned scores are the dense
+     * store's; with rescore_k == 0 they are the FP8 scores. */
+    const uint8_t *fp8_codes;   /* [n_tokens][d] */
+    const float *fp8_scales;    /* [n_tokens], 16-byte aligned */
+    int rescore_k;              /* 0, or topk..1024 */
     /* requests */
     int nq;                        /* query tokens per request, 1..128 */
     int topk;                      /* results per request, 1..1024 */
@@ -324,10 +337,11 @@ tms_status tms_server_create(const tms_server_config *cfg, tms_server **out);
 
 /*
  * Submit one request (HOST pointers, copied): query [nq][d] of the dense
- * store's dtype, cand_ids [n_cand] document ids of `store`.  *ticket
- * receives its handle.  Returns TMS_ERR_BUSY when max_pending requests are
- * unfinished, TMS_ERR_UNSUPPORTED when n_cand exceeds max_batch_candidates
- * or the PQ store is absent.
+ * store's dtype, cand_ids [n_cand] document ids of `store` (the FP8 store
+ * shares the dense store's ids).  *ticket receives its handle.  Returns
+ * TMS_ERR_BUSY when max_pending requests are unfinished,
+ * TMS_ERR_UNSUPPORTED when n_cand exceeds max_batch_candidates or the
+ * store is absent.
  */
 tms_status tms_server_submit(tms_server *s, tms_store store, const void *query, const int32_t *cand_ids,
                              int64_t n_cand, uint64_t *ticket);

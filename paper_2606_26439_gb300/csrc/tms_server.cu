@@ -1,13 +1,16 @@
 // tms_server.cu -- the serving loop: continuous batching of MaxSim requests
-// over a device-resident corpus (a dense store and optionally a PQ store).
+// over a device-resident corpus (a dense store, optionally a PQ store and an
+// FP8 copy of the dense store).
 //
 // One worker thread per server.  Each turn it takes every pending request
 // that fits the batch buffers (FIFO), stages their queries and candidate
-// lists in pinned memory, and enqueues on its own stream: the host-to-
-// device copies, tms_score_dense (dense requests) or tms_build_pq_lut +
-// tms_score_pq (PQ requests), tms_topk, and the device-to-host copy of the
-// top-k -- dense and PQ requests on two streams, so the HBM-bound dense
-// scoring and the shared-memory-bound PQ scoring of a batch overlap.  Two
+// lists in pinned memory, and enqueues, per store on its own stream: the
+// host-to-device copies, the scoring -- tms_score_dense (dense requests),
+// tms_build_pq_lut + tms_score_pq (PQ requests), or tms_quantize_e4m3 +
+// tms_score_fp8 followed by an exact fp16 re-score of each request's
+// shortlist (FP8 requests) -- tms_topk, and the device-to-host copy of the
+// top-k.  The HBM-bound dense and FP8 scoring and the shared-memory-bound
+// PQ scoring of a batch overlap on their streams.  Two
 // buffer slots alternate, so while the GPU runs one batch the
 // worker completes the previous one and stages the next: requests that
 // arrive during a launch go into the following one (continuous batching).
@@ -48,22 +51,35 @@ struct Request {
 
 using RequestPtr = std::shared_ptr<Request>;
 
-// Buffers of one batch in flight, per store (0 dense, 1 PQ).
+constexpr int kStores = 3;  // dense, PQ, FP8
+
+// Buffers of one batch in flight, per store (0 dense, 1 PQ, 2 FP8).
 struct Slot {
-    void* h_q[2] = {nullptr, nullptr};
-    int32_t* h_c[2] = {nullptr, nullptr};
-    int64_t* h_co[2] = {nullptr, nullptr};
-    float* h_ts[2] = {nullptr, nullptr};
-    int32_t* h_tp[2] = {nullptr, nullptr};
-    void* d_q[2] = {nullptr, nullptr};
-    int32_t* d_c[2] = {nullptr, nullptr};
-    int64_t* d_co[2] = {nullptr, nullptr};
-    float* d_sc[2] = {nullptr, nullptr};
-    float* d_ts[2] = {nullptr, nullptr};
-    int32_t* d_tp[2] = {nullptr, nullptr};
+    void* h_q[kStores] = {};
+    int32_t* h_c[kStores] = {};
+    int64_t* h_co[kStores] = {};
+    float* h_ts[kStores] = {};
+    int32_t* h_tp[kStores] = {};
+    void* d_q[kStores] = {};
+    int32_t* d_c[kStores] = {};
+    int64_t* d_co[kStores] = {};
+    float* d_sc[kStores] = {};
+    float* d_ts[kStores] = {};
+    int32_t* d_tp[kStores] = {};
     float* d_lut = nullptr;
-    cudaEvent_t done[2] = {nullptr, nullptr};
-    std::vector<RequestPtr> reqs[2];
+    // FP8 requests: quantized queries, the shortlist (top rescore_k
+    // positions), its CSR offsets and ids, and its fp16 scores
+    uint8_t* d_qc = nullptr;
+    float* d_qs = nullptr;
+    float* d_rts = nullptr;
+    int32_t* d_rtp = nullptr;
+    int32_t* h_rtp = nullptr;
+    int64_t* h_cor = nullptr;
+    int64_t* d_cor = nullptr;
+    int32_t* d_cr = nullptr;
+    float* d_scr = nullptr;
+    cudaEvent_t done[kStores] = {};
+    std::vector<RequestPtr> reqs[kStores];
     tms_status status = TMS_OK;
 };
 
@@ -75,7 +91,7 @@ struct tms_server {
     tms_server_config cfg;
     int device = 0;
     size_t qbytes = 0;  // bytes of one query
-    cudaStream_t stream[2] = {nullptr, nullptr};  // dense, PQ
+    cudaStream_t stream[tms::server::kStores] = {};  // dense, PQ, FP8
     tms::server::Slot slots[2];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -99,12 +115,16 @@ inline bool cuda_ok(cudaError_t e) {
     return false;
 }
 
+bool has_store(const tms_server_config& c, int st) {
+    return st == 0 || (st == 1 && c.pq_codes) || (st == 2 && c.fp8_codes);
+}
+
 bool alloc_slot(tms_server* s, Slot& sl) {
     const tms_server_config& c = s->cfg;
     const size_t nb = static_cast<size_t>(c.max_batch_requests);
     const size_t nc = static_cast<size_t>(c.max_batch_candidates);
-    const int stores = c.pq_codes ? 2 : 1;
-    for (int st = 0; st < stores; ++st) {
+    for (int st = 0; st < kStores; ++st) {
+        if (!has_store(c, st)) continue;
         if (!cuda_ok(cudaMallocHost(&sl.h_q[st], nb * s->qbytes)) ||
             !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_c[st]), nc * 4)) ||
             !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_co[st]), (nb + 1) * 8)) ||
@@ -122,12 +142,26 @@ bool alloc_slot(tms_server* s, Slot& sl) {
         !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_lut),
                             nb * static_cast<size_t>(c.nq) * c.pq_m * c.pq_k * 4)))
         return false;
-    return cuda_ok(cudaEventCreateWithFlags(&sl.done[0], cudaEventDisableTiming)) &&
-           cuda_ok(cudaEventCreateWithFlags(&sl.done[1], cudaEventDisableTiming));
+    if (c.fp8_codes) {
+        const size_t rk = static_cast<size_t>(c.rescore_k > 0 ? c.rescore_k : 1);
+        if (!cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_qc), nb * c.nq * c.d)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_qs), nb * c.nq * 4)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_rts), nb * rk * 4)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_rtp), nb * rk * 4)) ||
+            !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_rtp), nb * rk * 4)) ||
+            !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_cor), (nb + 1) * 8)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_cor), (nb + 1) * 8)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_cr), nb * rk * 4)) ||
+            !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_scr), nb * rk * 4)))
+            return false;
+    }
+    for (int st = 0; st < kStores; ++st)
+        if (!cuda_ok(cudaEventCreateWithFlags(&sl.done[st], cudaEventDisableTiming))) return false;
+    return true;
 }
 
 void free_slot(Slot& sl) {
-    for (int st = 0; st < 2; ++st) {
+    for (int st = 0; st < kStores; ++st) {
         cudaFreeHost(sl.h_q[st]);
         cudaFreeHost(sl.h_c[st]);
         cudaFreeHost(sl.h_co[st]);
@@ -141,21 +175,44 @@ void free_slot(Slot& sl) {
         cudaFree(sl.d_tp[st]);
     }
     cudaFree(sl.d_lut);
-    for (int st = 0; st < 2; ++st)
+    cudaFree(sl.d_qc);
+    cudaFree(sl.d_qs);
+    cudaFree(sl.d_rts);
+    cudaFree(sl.d_rtp);
+    cudaFreeHost(sl.h_rtp);
+    cudaFreeHost(sl.h_cor);
+    cudaFree(sl.d_cor);
+    cudaFree(sl.d_cr);
+    cudaFree(sl.d_scr);
+    for (int st = 0; st < kStores; ++st)
         if (sl.done[st]) cudaEventDestroy(sl.done[st]);
     (void)cudaGetLastError();
 }
 
+// FP8 requests: the ids of request i's shortlist -- the first cor[i+1] -
+// cor[i] positions of its top-rescore_k (all valid: a list shorter than
+// rescore_k contributes all of its candidates) -- packed at cor[i].
+__global__ void shortlist_ids(const int32_t* __restrict__ pos, int rk, const int64_t* __restrict__ co,
+                              const int64_t* __restrict__ cor, const int32_t* __restrict__ cands, int nb,
+                              int32_t* __restrict__ out) {
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= static_cast<int64_t>(nb) * rk) return;
+    const int i = static_cast<int>(idx / rk);
+    const int j = static_cast<int>(idx - static_cast<int64_t>(i) * rk);
+    if (j >= cor[i + 1] - cor[i]) return;
+    const int32_t p = pos[idx];
+    out[cor[i] + j] = p >= 0 ? cands[co[i] + p] : -1;
+}
+
 // Stage a batch into `sl` and enqueue its work; the result lands in the
-// slot's pinned buffers when both sl.done events complete.
+// slot's pinned buffers when every sl.done event completes.
 void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
     const tms_server_config& c = s->cfg;
-    sl.reqs[0].clear();
-    sl.reqs[1].clear();
+    for (auto& v : sl.reqs) v.clear();
     for (auto& r : batch) sl.reqs[r->store].push_back(r);
     sl.status = TMS_OK;
     const bool inject = c.inject_error_batch > 0 && s->batch_ordinal == static_cast<uint64_t>(c.inject_error_batch);
-    for (int st = 0; st < 2 && !inject; ++st) {
+    for (int st = 0; st < kStores && !inject; ++st) {
         const int nb = static_cast<int>(sl.reqs[st].size());
         if (nb == 0) continue;
         int64_t total = 0;
@@ -182,7 +239,50 @@ void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
                 rc = tms_score_pq(sl.d_lut, nb, c.nq, c.pq_m, c.pq_k, c.pq_codes, c.pq_n_tokens, c.pq_offsets,
                                   c.pq_lengths, c.pq_n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st], s->stream[st]);
         }
-        if (rc == TMS_OK) rc = tms_topk(sl.d_sc[st], sl.d_co[st], nb, c.topk, sl.d_ts[st], sl.d_tp[st], s->stream[st]);
+        const bool rescore = st == 2 && c.rescore_k > 0;
+        if (rc == TMS_OK && st == 2) {
+            rc = tms_quantize_e4m3(sl.d_q[st], c.dtype, static_cast<int64_t>(nb) * c.nq, c.d, sl.d_qc, sl.d_qs,
+                                   s->stream[st]);
+            if (rc == TMS_OK)
+                rc = tms_score_fp8(sl.d_qc, sl.d_qs, nb, c.nq, c.d, c.fp8_codes, c.fp8_scales, c.n_tokens,
+                                   c.doc_offsets, c.doc_lengths, c.n_docs, sl.d_c[st], sl.d_co[st], total, sl.d_sc[st],
+                                   s->stream[st]);
+            if (rc == TMS_OK && rescore) {
+                // shortlist: the rescore_k best FP8 scores of each request,
+                // scored again on the dense store
+                const int rk = c.rescore_k;
+                rc = tms_topk(sl.d_sc[st], sl.d_co[st], nb, rk, sl.d_rts, sl.d_rtp, s->stream[st]);
+                sl.h_cor[0] = 0;
+                for (int i = 0; i < nb; ++i) {
+                    const int64_t n = static_cast<int64_t>(sl.reqs[st][i]->cands.size());
+                    sl.h_cor[i + 1] = sl.h_cor[i] + (n < rk ? n : rk);
+                }
+                const int64_t total_r = sl.h_cor[nb];
+                if (rc == TMS_OK &&
+                    !cuda_ok(cudaMemcpyAsync(sl.d_cor, sl.h_cor, (nb + 1) * 8, cudaMemcpyHostToDevice, s->stream[st])))
+                    rc = TMS_ERR_CUDA;
+                if (rc == TMS_OK) {
+                    const int64_t n = static_cast<int64_t>(nb) * rk;
+                    shortlist_ids<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s->stream[st]>>>(
+                        sl.d_rtp, rk, sl.d_co[st], sl.d_cor, sl.d_c[st], nb, sl.d_cr);
+                    if (!cuda_ok(cudaGetLastError())) rc = TMS_ERR_CUDA;
+                }
+                if (rc == TMS_OK)
+                    rc = tms_score_dense(sl.d_q[st], c.dtype, nb, c.nq, c.d, c.doc_tokens, c.n_tokens, c.doc_offsets,
+                                         c.doc_lengths, c.n_docs, sl.d_cr, sl.d_cor, total_r, sl.d_scr,
+                                         s->stream[st]);
+                if (rc == TMS_OK &&
+                    !cuda_ok(cudaMemcpyAsync(sl.h_rtp, sl.d_rtp, static_cast<size_t>(nb) * rk * 4,
+                                             cudaMemcpyDeviceToHost, s->stream[st])))
+                    rc = TMS_ERR_CUDA;
+            }
+        }
+        if (rc == TMS_OK) {
+            if (rescore)
+                rc = tms_topk(sl.d_scr, sl.d_cor, nb, c.topk, sl.d_ts[st], sl.d_tp[st], s->stream[st]);
+            else
+                rc = tms_topk(sl.d_sc[st], sl.d_co[st], nb, c.topk, sl.d_ts[st], sl.d_tp[st], s->stream[st]);
+        }
         if (rc == TMS_OK &&
             (!cuda_ok(cudaMemcpyAsync(sl.h_ts[st], sl.d_ts[st], static_cast<size_t>(nb) * c.topk * 4,
                                       cudaMemcpyDeviceToHost, s->stream[st])) ||
@@ -192,19 +292,20 @@ void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
         if (rc != TMS_OK) sl.status = rc;
     }
     if (inject) sl.status = TMS_ERR_CUDA;
-    for (int st = 0; st < 2; ++st)
+    for (int st = 0; st < kStores; ++st)
         if (s->stream[st] && !cuda_ok(cudaEventRecord(sl.done[st], s->stream[st]))) sl.status = TMS_ERR_CUDA;
 }
 
 // Wait for a slot's batch and hand each request its result.
 void complete(tms_server* s, Slot& sl) {
     const tms_server_config& c = s->cfg;
-    for (int st = 0; st < 2; ++st)
+    for (int st = 0; st < kStores; ++st)
         if (s->stream[st] && !cuda_ok(cudaEventSynchronize(sl.done[st])) && sl.status == TMS_OK)
             sl.status = TMS_ERR_CUDA;
     const Clock::time_point now = Clock::now();
     uint64_t n = 0, cands = 0;
-    for (int st = 0; st < 2; ++st) {
+    for (int st = 0; st < kStores; ++st) {
+        const bool rescore = st == 2 && c.rescore_k > 0;
         for (size_t i = 0; i < sl.reqs[st].size(); ++i) {
             Request& r = *sl.reqs[st][i];
             r.status = sl.status;
@@ -213,9 +314,14 @@ void complete(tms_server* s, Slot& sl) {
             if (sl.status == TMS_OK) {
                 const float* ts = sl.h_ts[st] + i * c.topk;
                 const int32_t* tp = sl.h_tp[st] + i * c.topk;
+                const int32_t* rp = rescore ? sl.h_rtp + i * static_cast<size_t>(c.rescore_k) : nullptr;
+                const int64_t n_list = static_cast<int64_t>(r.cands.size());
+                const int64_t n_short = rescore ? (n_list < c.rescore_k ? n_list : c.rescore_k) : n_list;
                 for (int j = 0; j < c.topk; ++j) {
                     r.scores[j] = ts[j];
-                    r.ids[j] = (tp[j] >= 0 && static_cast<size_t>(tp[j]) < r.cands.size()) ? r.cands[tp[j]] : -1;
+                    int64_t p = (tp[j] >= 0 && tp[j] < n_short) ? tp[j] : -1;  // position in the scored list
+                    if (rescore && p >= 0) p = rp[p];                             // shortlist -> request's list
+                    r.ids[j] = (p >= 0 && p < n_list) ? r.cands[p] : -1;
                 }
             }
             r.t_done = now;
@@ -225,14 +331,13 @@ void complete(tms_server* s, Slot& sl) {
     }
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        for (int st = 0; st < 2; ++st)
+        for (int st = 0; st < kStores; ++st)
             for (auto& r : sl.reqs[st]) r->done = true;
         s->unfinished -= static_cast<int>(n);
         s->stats.requests += n;
         s->stats.candidates += cands;
     }
-    sl.reqs[0].clear();
-    sl.reqs[1].clear();
+    for (auto& v : sl.reqs) v.clear();
     s->cv_done.notify_all();
 }
 
@@ -288,12 +393,18 @@ bool config_ok(const tms_server_config& c) {
         if (c.pq_m != 4 && c.pq_m != 8 && c.pq_m != 16 && c.pq_m != 32) return false;
         if (c.pq_k < 1 || c.pq_k > 256 || c.pq_m * c.pq_k > 4096 || c.d % c.pq_m != 0) return false;
     }
+    if (c.fp8_codes) {
+        if (!c.fp8_scales || c.d < 16 || c.d % 16 != 0) return false;
+        if (c.rescore_k != 0 && (c.rescore_k < c.topk || c.rescore_k > 1024)) return false;
+    } else if (c.rescore_k != 0) {
+        return false;
+    }
     return true;
 }
 
 void destroy(tms_server* s) {
     for (auto& sl : s->slots) free_slot(sl);
-    for (int st = 0; st < 2; ++st)
+    for (int st = 0; st < kStores; ++st)
         if (s->stream[st]) cudaStreamDestroy(s->stream[st]);
     (void)cudaGetLastError();
     delete s;
@@ -313,6 +424,7 @@ extern "C" tms_status tms_server_create(const tms_server_config* cfg, tms_server
     if (!cuda_ok(cudaGetDevice(&s->device)) ||
         !cuda_ok(cudaStreamCreateWithFlags(&s->stream[0], cudaStreamNonBlocking)) ||
         (cfg->pq_codes && !cuda_ok(cudaStreamCreateWithFlags(&s->stream[1], cudaStreamNonBlocking))) ||
+        (cfg->fp8_codes && !cuda_ok(cudaStreamCreateWithFlags(&s->stream[2], cudaStreamNonBlocking))) ||
         !alloc_slot(s, s->slots[0]) || !alloc_slot(s, s->slots[1])) {
         destroy(s);
         return TMS_ERR_CUDA;
@@ -331,8 +443,9 @@ extern "C" tms_status tms_server_submit(tms_server* s, tms_store store, const vo
                                         int64_t n_cand, uint64_t* ticket) {
     using namespace tms::server;
     if (!s || !query || !ticket || n_cand < 0 || (n_cand > 0 && !cand_ids)) return TMS_ERR_INVALID_ARG;
-    if (store != TMS_STORE_DENSE && store != TMS_STORE_PQ) return TMS_ERR_INVALID_ARG;
-    if (store == TMS_STORE_PQ && !s->cfg.pq_codes) return TMS_ERR_UNSUPPORTED;
+    if (store != TMS_STORE_DENSE && store != TMS_STORE_PQ && store != TMS_STORE_FP8) return TMS_ERR_INVALID_ARG;
+    if ((store == TMS_STORE_PQ && !s->cfg.pq_codes) || (store == TMS_STORE_FP8 && !s->cfg.fp8_codes))
+        return TMS_ERR_UNSUPPORTED;
     if (n_cand > s->cfg.max_batch_candidates) return TMS_ERR_UNSUPPORTED;
     auto r = std::make_shared<Request>();
     r->store = store;

@@ -35,7 +35,7 @@ EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_q
            "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy",
            "tms_get_device_error", "tms_status_string", "tms_version")
 
-TMS_STORE_DENSE, TMS_STORE_PQ = 0, 1
+TMS_STORE_DENSE, TMS_STORE_PQ, TMS_STORE_FP8 = 0, 1, 2
 
 
 class ServerConfig(ctypes.Structure):
@@ -47,6 +47,7 @@ class ServerConfig(ctypes.Structure):
         ("pq_codes", ctypes.c_void_p), ("pq_codebook", ctypes.c_void_p), ("pq_m", ctypes.c_int),
         ("pq_k", ctypes.c_int), ("pq_n_tokens", ctypes.c_int64), ("pq_offsets", ctypes.c_void_p),
         ("pq_lengths", ctypes.c_void_p), ("pq_n_docs", ctypes.c_int64),
+        ("fp8_codes", ctypes.c_void_p), ("fp8_scales", ctypes.c_void_p), ("rescore_k", ctypes.c_int),
         ("nq", ctypes.c_int), ("topk", ctypes.c_int), ("max_batch_requests", ctypes.c_int),
         ("max_batch_candidates", ctypes.c_int64), ("max_pending", ctypes.c_int),
         ("inject_error_batch", ctypes.c_int),
@@ -363,12 +364,16 @@ def device_error(stream=None) -> int:
 # --------------------------------------------------------------- serving
 
 class Server:
-    """Serving loop over a device-resident dense store (and optional PQ
-    store): submit requests from the host, wait for their top-k.  The
-    config's device tensors must outlive the server."""
+    """Serving loop over a device-resident dense store (and optional PQ store
+    and FP8 copy of the dense store): submit requests from the host, wait for
+    their top-k.  The config's device tensors must outlive the server.
+
+    ``pq``: (codes, codebook, offsets, lengths); ``fp8``: (codes, scales) of
+    the dense store's tokens (quantize_e4m3), scored with an fp16 re-score
+    of each request's ``rescore_k`` best candidates (0: FP8 scores)."""
 
     def __init__(self, doc_tokens, doc_offsets, doc_lengths, nq, topk, max_batch_requests,
-                 max_batch_candidates, max_pending, pq=None, inject_error_batch=0):
+                 max_batch_candidates, max_pending, pq=None, inject_error_batch=0, fp8=None, rescore_k=0):
         torch = _torch()
         cfg = ServerConfig()
         cfg.doc_tokens = _dev(doc_tokens)
@@ -387,6 +392,11 @@ class Server:
             cfg.pq_offsets = _dev(offsets, torch.int64)
             cfg.pq_lengths = _dev(lengths, torch.int32)
             cfg.pq_n_docs = offsets.shape[0]
+        if fp8 is not None:
+            codes, scales = fp8
+            cfg.fp8_codes = _dev(codes, torch.uint8)
+            cfg.fp8_scales = _dev(scales, torch.float32)
+        cfg.rescore_k = rescore_k
         cfg.nq, cfg.topk = nq, topk
         cfg.max_batch_requests = max_batch_requests
         cfg.max_batch_candidates = max_batch_candidates

@@ -107,6 +107,17 @@ def test_server_rejects_bad_config(lib):
         setattr(cfg, field, bad)
         assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG, field
         setattr(cfg, field, good)
+    cfg.rescore_k = 20  # a re-score without an FP8 store
+    assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG
+    cfg.fp8_codes = DUMMY  # FP8 store without scales
+    assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG
+    cfg.fp8_scales = DUMMY
+    for field, bad in (("rescore_k", 5), ("rescore_k", 1025), ("d", 120)):  # < topk, > 1024, d % 16 != 0
+        good = getattr(cfg, field)
+        setattr(cfg, field, bad)
+        assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG, (field, bad)
+        setattr(cfg, field, good)
+    cfg.fp8_codes, cfg.fp8_scales, cfg.rescore_k = None, None, 0
     cfg.pq_codes, cfg.pq_codebook, cfg.pq_offsets, cfg.pq_lengths = DUMMY, DUMMY, DUMMY, DUMMY
     cfg.pq_n_tokens, cfg.pq_n_docs, cfg.pq_k = 100, 10, 256
     cfg.pq_m = 12  # unsupported subspace count

@@ -1,9 +1,14 @@
 """Serving loop (tms_server_*): continuous batching of requests over a
-device-resident dense store and PQ store.
+device-resident dense store, PQ store and FP8 copy of the dense store.
 
 * parity: every request's top-k against the FP64 oracle's scores of its
   own candidates (dense: Eq. 1; PQ: decompress-then-dot), within the 1e-3
   tolerance, positions a valid top-k up to tolerance ties;
+* FP8 store: with a re-score, the returned scores are the oracle's fp16
+  scores of the returned documents and the set is a valid top-k of the
+  whole list under those scores (the shortlist kept every document that
+  belongs); without one, the scores are Eq. 1 on the E4M3 values (the
+  store written by the oracle's quantizer from the same fp16 tokens);
 * a request's result is bitwise the same alone (batches of one) and mixed
   with others in large batches;
 * admission by pending budget, a host-injected batch failure, bounded
@@ -22,6 +27,7 @@ from tests._common import assert_topk_consistent, oracle_view
 pytestmark = pytest.mark.gpu
 
 NQ, D, TOPK, M, K, DSUB = 32, 128, 10, 16, 256, 8
+RESCORE = 40
 
 
 @pytest.fixture(scope="module")
@@ -32,24 +38,28 @@ def stores(cuda_lib):
     plen = synth.lengths_uniform(500, 1, 180, 71)
     cb, codes, _, poff, pln = synth.pq_corpus(plen, M, K, DSUB, 71)
     dev = gc.to_dev(tok, off, ln, codes, cb, poff, pln)
+    ta, tdt = oracle_view(tok)
+    f8c, f8s = oracle.quantize_e4m3(ta, dtype=tdt)
+    f8 = gc.to_dev(f8c, f8s)
     torch.cuda.synchronize()
-    return dict(tok=tok, off=off, ln=ln, cb=cb, codes=codes, poff=poff, pln=pln, dev=dev)
+    return dict(tok=tok, off=off, ln=ln, cb=cb, codes=codes, poff=poff, pln=pln, dev=dev, f8c=f8c, f8s=f8s, f8=f8)
 
 
 def _server(stores, **kw):
     from paper_2606_26439_gb300 import tms
     tok_d, off_d, ln_d, codes_d, cb_d, poff_d, pln_d = stores["dev"]
-    args = dict(nq=NQ, topk=TOPK, max_batch_requests=64, max_batch_candidates=200_000, max_pending=256)
+    args = dict(nq=NQ, topk=TOPK, max_batch_requests=64, max_batch_candidates=200_000, max_pending=256,
+                fp8=tuple(stores["f8"]), rescore_k=RESCORE)
     args.update(kw)
     return tms.Server(tok_d, off_d, ln_d, pq=(codes_d, cb_d, poff_d, pln_d), **args)
 
 
-def _requests(n, seed):
+def _requests(n, seed, n_stores=2):
     g = np.random.default_rng(seed)
     reqs = []
     for i in range(n):
-        store = int(g.integers(0, 2))
-        n_docs = 600 if store == 0 else 500
+        store = int(g.integers(0, n_stores))
+        n_docs = 500 if store == 1 else 600
         size = int(g.choice([0, 1, 7, 10, 33, 250, n_docs]))
         cands = g.choice(n_docs, size, replace=False).astype(np.int32)
         if size > 20 and i % 5 == 0:
@@ -92,7 +102,7 @@ def test_server_parity_with_oracle(stores):
 
 
 def test_alone_equals_mixed(stores):
-    reqs = _requests(48, 2)
+    reqs = _requests(48, 2, n_stores=3)
     with _server(stores, max_batch_requests=1) as srv:   # every request alone
         alone = [srv.wait(srv.submit(q, c, s))[:2] for s, q, c in reqs]
     with _server(stores, max_batch_requests=64) as srv:  # all submitted at once, batched
@@ -154,3 +164,54 @@ def test_bounded_wait_unknown_ticket_and_oversize(stores):
         assert e.value.status == tms.TMS_ERR_TIMEOUT
         for t in tickets:                 # still waitable after a timeout
             srv.wait(t)
+
+
+def _fp8_oracle_scores(stores, q, cands):
+    qa, qdt = oracle_view(q[None])
+    qc, qs = oracle.quantize_e4m3(qa.reshape(NQ, D), dtype=qdt)
+    return oracle.dense_scores_scaled(qc, qs, stores["f8c"], stores["f8s"], stores["off"], stores["ln"], cands,
+                                      qdtype=oracle.E4M3, tdtype=oracle.E4M3)
+
+
+@pytest.mark.parametrize("rescore", [RESCORE, 0])
+def test_server_fp8_store(stores, rescore):
+    """FP8 requests: with a re-score the results are exact fp16 scores of a
+    valid top-k; without one they are the FP8 scores of a valid top-k."""
+    from paper_2606_26439_gb300 import tms
+    g = np.random.default_rng(7 + rescore)
+    reqs = []
+    for i in range(30):
+        size = int(g.choice([0, 1, 9, 10, 11, 40, 41, 300, 600]))
+        cands = g.choice(600, size, replace=False).astype(np.int32)
+        if size > 20 and i % 4 == 0:
+            cands[5] = 600 + 3       # a bad id: scores NaN, sorts last
+        reqs.append((synth.queries(1, NQ, D, "f16", 900 + i)[0], cands))
+    with _server(stores, rescore_k=rescore) as srv:
+        results = [srv.wait(srv.submit(q, c, tms.TMS_STORE_FP8)) for q, c in reqs]
+    for (q, cands), (sc, ids, _) in zip(reqs, results):
+        n_valid = min(TOPK, len(cands))
+        assert np.all(ids[n_valid:] == -1) and np.all(np.isneginf(sc[n_valid:]))
+        if len(cands) == 0:
+            continue
+        want = _oracle_scores(stores, 0, q, cands) if rescore else _fp8_oracle_scores(stores, q, cands)
+        pos = np.array([int(np.nonzero(cands == i)[0][0]) for i in ids[:n_valid]])
+        tol = 2e-3 * max(1.0, np.nanmax(np.abs(want)))
+        assert_topk_consistent(sc[:n_valid], pos, want, TOPK, tol)
+        fin = np.isfinite(want[pos])
+        assert np.array_equal(np.isnan(sc[:n_valid]), np.isnan(want[pos]))
+        assert np.all(np.abs(sc[:n_valid][fin] - want[pos][fin]) <= 1e-3 * np.maximum(np.abs(want[pos][fin]),
+                                                                                       NQ * 1e-3))
+
+
+def test_server_fp8_rescore_uses_fp16_scores(stores):
+    """A re-scored FP8 request returns the same scores and ids as the same
+    request to the dense store whenever the dense top-k is inside the FP8
+    shortlist -- here a list no longer than the shortlist, so always."""
+    from paper_2606_26439_gb300 import tms
+    q = synth.queries(1, NQ, D, "f16", 77)[0]
+    cands = np.random.default_rng(77).choice(600, RESCORE, replace=False).astype(np.int32)
+    with _server(stores) as srv:
+        s8, i8, _ = srv.wait(srv.submit(q, cands, tms.TMS_STORE_FP8))
+        sd, idd, _ = srv.wait(srv.submit(q, cands, tms.TMS_STORE_DENSE))
+    assert np.array_equal(s8.view(np.uint32), sd.view(np.uint32))
+    assert np.array_equal(i8, idd)
