@@ -438,7 +438,6 @@ def serving_row():
     each arrival rate: p50 / p99 latency (submit to result) and docs/s with
     continuous batching, and with one request per launch (the plain
     per-request baseline, same kernels)."""
-    import threading
     import torch
     from paper_2606_26439_gb300 import tms
     dev = torch.device("cuda")
@@ -455,48 +454,113 @@ def serving_row():
     mean_cands = float(np.mean([len(p[2]) for p in pool]))
 
     def run(rate, batched, duration=3.0):
-        srv = tms.Server(tok, off, ln, nq=NQ, topk=TOPK, max_batch_requests=256 if batched else 1,
-                         max_batch_candidates=4_000_000, max_pending=1 << 20, pq=(codes, cb, poff, pln))
-        n_req = int(rate * duration)
-        gaps = np.random.default_rng(11).exponential(1.0 / rate, n_req)
-        tickets = [None] * n_req
-        ready = threading.Semaphore(0)
-
-        def submitter():
-            t0 = time.perf_counter()
-            due = 0.0
-            for i in range(n_req):
-                due += gaps[i]
-                delay = t0 + due - time.perf_counter()
-                if delay > 0:
-                    time.sleep(delay)
-                store, q, c = pool[i % len(pool)]
-                tickets[i] = (srv.submit(q, c, store), len(c))
-                ready.release()
-
-        th = threading.Thread(target=submitter)
-        t_start = time.perf_counter()
-        th.start()
-        lat, docs = [], 0
-        for i in range(n_req):
-            ready.acquire()
-            t, n = tickets[i]
-            _, _, l = srv.wait(t, timeout_s=600.0)
-            lat.append(l)
-            docs += n
-        wall = time.perf_counter() - t_start
-        th.join()
-        st = srv.stats()
-        srv.close()
-        lat = np.array(lat) * 1e3
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "docs_per_s": docs / wall, "requests": n_req, "batches": st["batches"]}
+        with tms.Server(tok, off, ln, nq=NQ, topk=TOPK, max_batch_requests=256 if batched else 1,
+                        max_batch_candidates=4_000_000, max_pending=1 << 20, pq=(codes, cb, poff, pln)) as srv:
+            return serve_poisson(srv, pool, rate, duration)
 
     out = {"mean_candidates": mean_cands}
     for rate in (1000, 4000):
         out[f"{rate}_qps"] = {"demand_docs_per_s": rate * mean_cands, "batched": run(rate, True),
                               "one_per_launch": run(rate, False)}
-    del tok, codes
+    del codes
+    torch.cuda.empty_cache()
+    out_fp8 = serving_fp8_row(tok, off, ln)
+    del tok
+    torch.cuda.empty_cache()
+    return out, out_fp8
+
+
+def serve_poisson(srv, pool, rate, duration, store_of=None):
+    """Submit pool requests (cycling) at Poisson arrivals of `rate` per
+    second for `duration` seconds from a second thread, wait for each in
+    order; p50 / p99 latency (submit to result) and docs/s over the wall
+    time until the last result.  Pool entries are (query, cands) sent to
+    `store_of`, or (store, query, cands) when it is None."""
+    import threading
+    n_req = int(rate * duration)
+    gaps = np.random.default_rng(11).exponential(1.0 / rate, n_req)
+    tickets = [None] * n_req
+    ready = threading.Semaphore(0)
+
+    def submitter():
+        t0 = time.perf_counter()
+        due = 0.0
+        for i in range(n_req):
+            due += gaps[i]
+            delay = t0 + due - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            e = pool[i % len(pool)]
+            store, q, c = (store_of,) + tuple(e) if store_of is not None else e
+            tickets[i] = (srv.submit(q, c, store), len(c))
+            ready.release()
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    lat, docs = [], 0
+    for i in range(n_req):
+        ready.acquire()
+        t, n = tickets[i]
+        _, _, l = srv.wait(t, timeout_s=600.0)
+        lat.append(l)
+        docs += n
+    wall = time.perf_counter() - t_start
+    th.join()
+    st = srv.stats()
+    lat = np.array(lat) * 1e3
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "docs_per_s": docs / wall, "requests": n_req, "batches": st["batches"]}
+
+
+def serving_fp8_row(tok, off, ln):
+    """The served, batched FP8 form against plain per-request fp16 scoring:
+    the 1,000,000-document fp16 store of the serving row and its FP8 E4M3
+    copy (quantized on the device), dense requests only (32 query tokens,
+    lists log-uniform in [1,000, 100,000], top-10, Poisson arrivals).
+    FP8: batched (up to 256 requests per launch), each request's 100 best
+    FP8 candidates re-scored in fp16.  Plain: one fp16 request per launch.
+    Batched fp16 is reported beside them.  Top-10 overlap of the FP8 form
+    (with and without the re-score) against the fp16 top-10 of the same
+    requests, over 256 of them."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    n_docs = off.shape[0]
+    f8c, f8s = tms.quantize_e4m3(tok)
+    g = np.random.default_rng(17)
+    pool = []
+    for i in range(512):
+        n = int(np.exp(g.uniform(np.log(1_000), np.log(100_000))))
+        pool.append((synth.queries(1, NQ, D, "f16", 5000 + i)[0], g.integers(0, n_docs, n).astype(np.int32)))
+    mean_cands = float(np.mean([len(p[1]) for p in pool]))
+
+    def server(batched, rescore_k=100):
+        return tms.Server(tok, off, ln, nq=NQ, topk=TOPK, max_batch_requests=256 if batched else 1,
+                          max_batch_candidates=4_000_000, max_pending=1 << 20, fp8=(f8c, f8s), rescore_k=rescore_k)
+
+    out = {"mean_candidates": mean_cands, "rescore_k": 100}
+    # top-10 overlap against the fp16 scorer
+    with server(True) as srv, server(True, rescore_k=0) as raw:
+        ov, ov_raw = [], []
+        for q, c in pool[:256]:
+            _, ref, _ = srv.wait(srv.submit(q, c, tms.TMS_STORE_DENSE))
+            _, got, _ = srv.wait(srv.submit(q, c, tms.TMS_STORE_FP8))
+            _, got_raw, _ = raw.wait(raw.submit(q, c, tms.TMS_STORE_FP8))
+            ref_set = set(ref[ref >= 0].tolist())
+            ov.append(len(ref_set & set(got[got >= 0].tolist())) / max(1, len(ref_set)))
+            ov_raw.append(len(ref_set & set(got_raw[got_raw >= 0].tolist())) / max(1, len(ref_set)))
+    out["top10_overlap_rescored"] = float(np.mean(ov))
+    out["top10_overlap_rescored_min"] = float(np.min(ov))
+    out["top10_overlap_fp8_only"] = float(np.mean(ov_raw))
+    for rate in (4000, 7000, 10000):
+        row = {"demand_docs_per_s": rate * mean_cands}
+        for name, batched, store in (("fp8_batched_rescored", True, tms.TMS_STORE_FP8),
+                                     ("fp16_one_per_launch", False, tms.TMS_STORE_DENSE),
+                                     ("fp16_batched", True, tms.TMS_STORE_DENSE)):
+            with server(batched) as srv:
+                row[name] = serve_poisson(srv, pool, rate, 3.0, store)
+        out[f"{rate}_qps"] = row
+    del f8c, f8s
     torch.cuda.empty_cache()
     return out
 
@@ -562,7 +626,7 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     del w, tc, tsc, qc, qsc, out
     torch.cuda.empty_cache()
     rows["fp8_e4m3_shared_1m"] = fp8_store_row(stream, hbm_peak)
-    rows["serving_mix_1m_dense_1m_pq"] = serving_row()
+    rows["serving_mix_1m_dense_1m_pq"], rows["serving_fp8_vs_fp16_1m"] = serving_row()
     # dimension tiling: 200K docs, 32 queries over all docs, bf16, top-100
     n3 = 200_000
     len3 = synth.lengths_uniform(n3, LO, HI, 2)
