@@ -61,7 +61,8 @@ def parse_args():
     p.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     p.add_argument("--workload", choices=["headline", "small"], default="headline",
                    help="small: 100,000 docs, 1 query x 100,000 candidates (sized for ncu captures)")
-    p.add_argument("--profile-case", choices=["fp8_small", "pq_small", "pq16_small", "shared_small"], default=None,
+    p.add_argument("--profile-case", choices=["fp8_small", "pq_small", "pq16_small", "pqtc_small", "shared_small"],
+                   default=None,
                    help="run only one small secondary kernel (sized for ncu captures) and print its timing")
     args = p.parse_args()
     if args.workload == "small":
@@ -733,6 +734,26 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
                            "frac_hbm": alg / (pq_ms * 1e-3) / 1e9 / hbm_peak,
                            "lds_gbs": lds / (pq_ms * 1e-3) / 1e9, "lds_peak_gbs": lds_peak,
                            "frac_lds": lds / (pq_ms * 1e-3) / 1e9 / lds_peak}
+    # the same queries with the codes decompressed in shared memory and scored
+    # on the tensor cores (one shared list: every document)
+    ids = torch.arange(n4, dtype=torch.int32, device=dev)
+    out_tc = torch.empty((nQ4, n4), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        tms.score_pq_tc_shared(Q, cb, codes, off, ln, ids, out=out_tc, stream=stream)
+        e[0].record(stream)
+        for _ in range(reps):
+            tms.score_pq_tc_shared(Q, cb, codes, off, ln, ids, out=out_tc, stream=stream)
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    tc_ms = e[0].elapsed_time(e[1]) / reps
+    rel_tc = ((out_tc.view(-1) - out).abs() / out.abs().clamp_min(NQ * 1e-3)).max().item()
+    tc_flops = iomodel.dense_alg_flops(tok4, NQ, M * dsub)
+    rows["pq_m16_k256_tensor_core"] = {"docs_per_s": nQ4 * n4 / (tc_ms * 1e-3), "kernel_ms": tc_ms,
+                                       "speedup_vs_fp32_table": pq_ms / tc_ms,
+                                       "max_rel_diff_vs_fp32_table": rel_tc,
+                                       "tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
+                                       "codes_reads_gbs": tok4 // nQ4 * M * ((nQ4 + 3) // 4) / (tc_ms * 1e-3) / 1e9}
+    del out_tc
     # the same pass through the fp16 table: half the shared-memory bytes per lookup
     lds16 = lds // 2
     rows["pq_m16_k256_f16_table"] = {"docs_per_s": nQ4 * n4 / (pq16_ms * 1e-3), "kernel_ms": pq16_ms,
@@ -810,8 +831,9 @@ def profile_case(args):
     """One secondary kernel on a small case (100,000 documents, a few GB):
     fp8_small -- FP8 store, 1 query x 100,000 candidates; pq_small -- PQ
     M=16 K=256, 8 queries over all documents (pq16_small: the same through
-    the fp16 table); shared_small -- bf16 d=256, 8 queries over all
-    documents in the shared schedule."""
+    the fp16 table; pqtc_small: decompressed in shared memory, tensor
+    cores); shared_small -- bf16 d=256, 8 queries over all documents in the
+    shared schedule."""
     import torch
     from paper_2606_26439_gb300 import tms
     dev = torch.device("cuda")
@@ -826,14 +848,17 @@ def profile_case(args):
         co = torch.tensor([0, n], dtype=torch.int64, device=dev)
         run = lambda: tms.score_fp8(qc, qs, tc, ts, off, ln, ids, co)  # noqa: E731
         units = n
-    elif args.profile_case in ("pq_small", "pq16_small"):
+    elif args.profile_case in ("pq_small", "pq16_small", "pqtc_small"):
         cb, codes, off, ln = synth.device_pq_corpus(lens, 16, 256, 8, 9, device=dev)
         q = synth.queries(8, NQ, 128, "f16", 9).to(dev)
         lut = tms.build_pq_lut(q, cb)
         f = ids.repeat(8)
         co = torch.arange(0, 9 * n, n, dtype=torch.int64, device=dev)
         half = args.profile_case == "pq16_small"
-        run = lambda: tms.score_pq(lut, codes, off, ln, f, co, f16_table=half)  # noqa: E731
+        if args.profile_case == "pqtc_small":
+            run = lambda: tms.score_pq_tc_shared(q, cb, codes, off, ln, ids)  # noqa: E731
+        else:
+            run = lambda: tms.score_pq(lut, codes, off, ln, f, co, f16_table=half)  # noqa: E731
         units = 8 * n
     else:
         tok, off, ln = synth.device_dense_corpus(lens, 256, "bf16", 9, dev)

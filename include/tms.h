@@ -248,6 +248,35 @@ tms_status tms_score_pq_f16(const float *lut, int n_queries, int nq, int m, int 
                             float *out_scores, cudaStream_t stream);
 
 /*
+ * PQ MaxSim on the tensor cores for queries that share one candidate list
+ * (e.g. every query over the whole corpus): each document tile's codes are
+ * decompressed into shared memory -- token j's row is the concatenation of
+ * its centroids codebook[mm][codes[j][mm]] (Section 4.1's explicit
+ * decompression), each centroid rounded to the nearest fp16 -- and scored
+ * by Eq. 1 with the dense pipeline (fp32 accumulation), in groups of up to
+ * 8 queries per decompressed tile.  Unlike tms_score_pq nothing here
+ * depends on a per-query table, so the decompression is shared by the
+ * group.
+ *
+ *   queries      [n_queries][nq][d] fp16.
+ *   codebook     [m][k][d/m] fp32;  codes [n_tokens][m] uint8, packed like
+ *                doc_tokens.
+ *   cand_ids     [n_cand] int32, shared by all queries;  out_scores
+ *                [n_queries][n_cand], as for tms_score_dense_shared.
+ *
+ * Error bound against Eq. 1 on the fp32 centroids: each centroid element
+ * carries a relative rounding error <= 2^-11, plus the fp32 sums.
+ * Limits: qdtype TMS_F16, m = 16, d = 128 (dsub = 8), 1 <= k <= 256,
+ * 1 <= nq <= 32 (TMS_ERR_UNSUPPORTED otherwise); codes must be < k (a
+ * larger code reads a zero centroid); n_tokens < 2^31.
+ */
+tms_status tms_score_pq_tc_shared(const void *queries, tms_dtype qdtype, int n_queries, int nq, int d,
+                                  const float *codebook, int m, int k, const uint8_t *codes, int64_t n_tokens,
+                                  const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                                  const int32_t *cand_ids, int64_t n_cand, float *out_scores,
+                                  cudaStream_t stream);
+
+/*
  * Top-k per query over scores laid out like out_scores above (Section 6.8).
  *
  *   scores        [n_cand] fp32, query q's list at cand_offsets[q]..[q+1].

@@ -73,10 +73,15 @@ namespace tms {
 namespace dense {
 
 constexpr int kRows = 128;                    // document rows per tile
-// Row types: fp16 / bf16, FP8 E4M3 codes + row scales, fp32 by split TF32.
-enum : int { kF16 = 0, kE4M3 = 1, kTF32 = 2 };
+// Row types: fp16 / bf16, FP8 E4M3 codes + row scales, fp32 by split TF32,
+// PQ codes decompressed into fp16 rows in shared memory (kPQ: M = 16
+// subspaces of 8 dimensions, d = 128).
+enum : int { kF16 = 0, kE4M3 = 1, kTF32 = 2, kPQ = 3 };
 // Elements per 128-byte dimension chunk (one 128-byte swizzle row).
 __host__ __device__ constexpr int chunk_elems(int kind) { return kind == kE4M3 ? 128 : (kind == kTF32 ? 32 : 64); }
+constexpr int kPqM = 16;                      // kPQ: subspaces (16 code bytes per token)
+constexpr int kPqCbBytes = 256 * kPqM * 16;   // kPQ: fp16 codebook, all 256 codes (64 KB)
+constexpr int kCodeRing = 4;                  // kPQ: super-tiles whose code rows are in flight or held
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per planner lane)
 // Super-tile records in flight: 8 with 256-row super-tiles (one CTA per
@@ -88,8 +93,10 @@ constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a
 constexpr int kEpiWarps = 4;
 constexpr int kLoaderWarp = 2 + kEpiWarps;
 constexpr int kThreads = 32 * (kLoaderWarp + 1);  // planner, MMA, four epilogue warps, loader
-constexpr int kSplitWarps = 4;                    // TF: splitter warps after the loader
-__host__ __device__ constexpr int kernel_threads(int kind) { return kThreads + (kind == kTF32 ? 32 * kSplitWarps : 0); }
+constexpr int kSplitWarps = 4;                    // TF: splitter warps after the loader; kPQ: decompressors
+__host__ __device__ constexpr int kernel_threads(int kind) {
+    return kThreads + ((kind == kTF32 || kind == kPQ) ? 32 * kSplitWarps : 0);
+}
 constexpr int kAcc = 2;                       // accumulator buffers (each H x STR TMEM columns)
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
@@ -144,10 +151,13 @@ struct Args {
     int rows_alloc;  // query rows held per dimension chunk: 32 * bpc * reps
     int qbox;        // rows of one query TMA box: 32 * bpc (per-query), 32 (shared)
     uint32_t idesc;  // instruction descriptor, N field left 0 (set per super-tile)
+    const uint8_t* pq_codes;    // kPQ: [n_tokens][16] uint8
+    const float* pq_codebook;   // kPQ: [16][pq_k][8] fp32
+    int pq_k;                   // kPQ: centroids per subspace (codes >= pq_k read zeros)
 };
 
 struct Layout {
-    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, st_off, bar_off, misc_off, total;
+    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, cb_off, code_off, st_off, bar_off, misc_off, total;
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
@@ -167,9 +177,12 @@ __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunk
     L.stage_stride = twin * str * 128;
     L.part_off = L.stage_off + stages * L.stage_stride;
     L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
-    L.st_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
+    L.cb_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
+    L.code_off = L.cb_off + (kind == kPQ ? kPqCbBytes : 0);                        // kPQ: fp16 codebook
+    // kPQ: code-row ring, then per slot the valid rows of each 8-row group
+    L.st_off = L.code_off + (kind == kPQ ? kCodeRing * (str * kPqM + kMaxSeg * 4) : 0);
     L.bar_off = L.st_off + st_ring(str) * static_cast<int>(sizeof(StSlot));
-    const int nbar = 3 * stages + 2 * kAcc + 3 * qslots + 2 * st_ring(str) + 8 + 2 * kScaleRing + 1;
+    const int nbar = 3 * stages + 2 * kAcc + 3 * qslots + 2 * st_ring(str) + 8 + 2 * kScaleRing + 1 + 2 * kCodeRing;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
@@ -271,6 +284,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     dense_tc_kernel(const __grid_constant__ Maps maps, const Args a) {
     constexpr bool F8 = KIND == kE4M3;
     constexpr bool TF = KIND == kTF32;
+    constexpr bool PQ = KIND == kPQ;
     constexpr int CE = chunk_elems(KIND);
     constexpr int STAGE_BYTES = STR * 128;
     constexpr uint32_t TCOLS = kAcc * H * STR;
@@ -292,6 +306,9 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     float* part = reinterpret_cast<float*>(smem + L.part_off);  // [copy][parity][block]
     float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // [kScaleRing][kScalePitch]
     StSlot* slots = reinterpret_cast<StSlot*>(smem + L.st_off);
+    uint8_t* cb = smem + L.cb_off;           // kPQ: fp16 codebook, entry (code, m) at (code * 16 + m) * 16
+    uint8_t* code_ring = smem + L.code_off;  // kPQ: [kCodeRing][STR rows][16] code bytes
+    uint8_t* gvalid = code_ring + kCodeRing * STR * kPqM;  // kPQ: [kCodeRing][STR / 8] valid rows per 8-row group
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;
     uint64_t* empty = full + S;
@@ -308,6 +325,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     uint64_t* mdone = sempty + kScaleRing;
     uint64_t* conv = mdone + 1;   // TF: [S] stage split
     uint64_t* qconv = conv + S;   // TF: [QS] query tile split
+    uint64_t* codefull = qconv + QS;            // kPQ: [kCodeRing] code rows landed
+    uint64_t* codeempty = codefull + kCodeRing;  // kPQ: [kCodeRing] code rows consumed
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
 
@@ -316,7 +335,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
-            mbar_init(&full[i], 1);
+            mbar_init(&full[i], PQ ? kSplitWarps : 1);  // kPQ: every decompressor warp wrote its rows
             mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < kAcc; ++i) {
@@ -329,7 +348,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         }
         for (int i = 0; i < kStRing; ++i) {
             mbar_init(&xfull[i], 1);
-            mbar_init(&xempty[i], 2 + kEpiWarps + (TF ? kSplitWarps : 0));  // loader, MMA, epilogue, splitters
+            mbar_init(&xempty[i], 2 + kEpiWarps + ((TF || PQ) ? kSplitWarps : 0));  // loader, MMA, epilogue, splitters
         }
         for (int i = 0; i < 4; ++i) {
             mbar_init(&pfull[i], a.bpc);
@@ -342,6 +361,10 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         mbar_init(mdone, 1);
         for (int i = 0; i < S; ++i) mbar_init(&conv[i], kSplitWarps);
         for (int i = 0; i < QS; ++i) mbar_init(&qconv[i], kSplitWarps);
+        for (int i = 0; i < kCodeRing; ++i) {
+            mbar_init(&codefull[i], 1);
+            mbar_init(&codeempty[i], kSplitWarps);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -355,6 +378,25 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     if (warp == 1) {
         tmem_alloc(tmem_slot, TCOLS);
         tmem_relinquish();
+    }
+    if constexpr (PQ) {
+        // the codebook, rounded to fp16 (nearest even), for all 256 codes:
+        // codes >= pq_k get zeros
+        for (int e = threadIdx.x; e < 256 * kPqM; e += blockDim.x) {
+            const int code = e / kPqM;
+            const int m = e - code * kPqM;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (code < a.pq_k) {
+                const float4* src =
+                    reinterpret_cast<const float4*>(a.pq_codebook + (static_cast<int64_t>(m) * a.pq_k + code) * 8);
+                const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+                const __half2 h0 = __floats2half2_rn(x0.x, x0.y), h1 = __floats2half2_rn(x0.z, x0.w);
+                const __half2 h2 = __floats2half2_rn(x1.x, x1.y), h3 = __floats2half2_rn(x1.z, x1.w);
+                v = make_uint4(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
+                               *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
+            }
+            *reinterpret_cast<uint4*>(cb + e * 16) = v;
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -559,6 +601,49 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             if (qi > 0) drain_wait(&qfull[(qi - 1) % QS], ((qi - 1) / QS) & 1);
         }
         __syncwarp();
+    } else if (PQ && warp == kLoaderWarp) {
+        // --------------------------------------------------- loader (kPQ)
+        // Each super-tile's code rows (16 bytes per token, one bulk copy per
+        // tile) go to a ring slot; the decompressors turn them into rows.
+        int64_t issued = 0;
+        for (int t = 0;; ++t) {
+            const int xs = t % kStRing;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            const StHdr h = slots[xs].h;
+            if (h.flags & kEnd) break;
+            const bool has = lane < h.nseg;
+            int r = 0, row0 = 0, col = 0;
+            if (has) {
+                const SegInfo si = slots[xs].seg[lane];
+                r = si.r;
+                row0 = si.row0;
+                col = si.col;
+            }
+            int bytes = r * kPqM;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xempty[xs]);
+            const int cs = t % kCodeRing;
+            if (!warp_wait(&codeempty[cs], ((t / kCodeRing) & 1) ^ 1, abort_flag, a.err)) break;
+            if (has)  // valid rows of each 8-row group of this tile (a prefix of the group)
+                for (int g8 = 0; g8 < (r + 7) >> 3; ++g8)
+                    gvalid[cs * (STR / 8) + (col >> 3) + g8] = static_cast<uint8_t>(min(8, r - 8 * g8));
+            __syncwarp();
+            if (lane == 0) mbar_arrive_expect_tx(&codefull[cs], static_cast<uint32_t>(bytes));
+            __syncwarp();
+            if (has)
+                bulk_load(code_ring + (cs * STR + col) * kPqM, a.pq_codes + static_cast<int64_t>(row0) * kPqM,
+                          static_cast<uint32_t>(r * kPqM), &codefull[cs]);
+            ++issued;
+        }
+        // Let every copy still in flight land before the CTA can exit.
+        if (lane == 0) {
+            const int64_t n = issued < kCodeRing ? issued : kCodeRing;
+            for (int64_t i = 1; i <= n; ++i)
+                drain_wait(&codefull[(issued - i) % kCodeRing], static_cast<uint32_t>(((issued - i) / kCodeRing) & 1));
+        }
+        __syncwarp();
     } else if (warp == kLoaderWarp) {
         // -------------------------------------------------------- loader
         const uint64_t pol_stream = policy_evict_first();
@@ -612,6 +697,76 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             }
         }
         __syncwarp();
+    } else if (PQ && warp > kLoaderWarp) {
+        // ------------------------------------------------- decompressors
+        // Thread = (row, 16-byte unit) pairs of every chunk stage: the unit
+        // u of row R in chunk kc is the fp16 centroid of subspace 8 kc + u
+        // for that row's code, written at unit u ^ (R % 8) -- the 128-byte
+        // swizzle TMA would have produced -- so the MMA reads decompressed
+        // rows exactly as it reads loaded ones.  Padding rows of a tile are
+        // zero.  A quarter-warp covers one row: eight subspaces, eight
+        // distinct codebook bank groups, one 128-byte store.
+        const int tid = (warp - kLoaderWarp - 1) * 32 + lane;
+        constexpr int kDecThreads = 32 * kSplitWarps;
+        int s = 0;
+        uint32_t ph = 0;
+        for (int t = 0;; ++t) {
+            const int xs = t % kStRing;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            const StHdr h = slots[xs].h;
+            if (h.flags & kEnd) break;
+            const int cs = t % kCodeRing;
+            if (!warp_wait_all(&codefull[cs], (t / kCodeRing) & 1, abort_flag, a.err)) break;
+            const uint8_t* crow = code_ring + cs * STR * kPqM;
+            bool ok = true;
+            for (int kc = 0; kc < NCH; ++kc) {
+                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* stg = stage_base + s * SSTRIDE;
+                const uint8_t* gv = gvalid + cs * (STR / 8);
+                const int u = tid & 7;              // unit (subspace 8 kc + u) of every row this thread writes
+                const int m = kc * 8 + u;
+                // Rows tid / 8 + kRowStep j, eight per batch.  Every load of a
+                // batch is unconditional (a stale code byte of a padding row
+                // still indexes inside the codebook and the ring slot) and
+                // issued before the batch's stores, so the three dependent
+                // shared-memory loads of the eight rows overlap; padding rows
+                // are then written as zeros.
+                constexpr int kBatch = 8;
+                constexpr int kRowStep = kDecThreads / 8;
+                for (int r0 = tid >> 3; r0 < h.rows; r0 += kRowStep * kBatch) {
+                    uint4 v[kBatch];
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int R = min(r0 + kRowStep * j, STR - 1);
+                        const uint32_t code = crow[R * kPqM + m];
+                        const uint4 e = *reinterpret_cast<const uint4*>(cb + (code * kPqM + m) * 16);
+                        const bool ok = (R & 7) < gv[R >> 3];
+                        v[j] = ok ? e : make_uint4(0u, 0u, 0u, 0u);
+                    }
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int R = r0 + kRowStep * j;
+                        if (R < h.rows) *reinterpret_cast<uint4*>(stg + R * 128 + ((u ^ (R & 7)) << 4)) = v[j];
+                    }
+                }
+                fence_proxy_async_smem();  // generic-proxy writes, read next by the tensor cores
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[s]);
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&codeempty[cs]);
+                mbar_arrive(&xempty[xs]);
+            }
+        }
     } else if (TF && warp > kLoaderWarp) {
         // ------------------------------------------------------ splitters
         // Split each new query tile and every landed chunk stage into
@@ -936,6 +1091,10 @@ inline int config_shapes(Config* out) {
         out[0] = {128, 1, 0};
         return 1;
     }
+    if (KIND == kPQ) {  // one query half
+        out[0] = {256, 1, 0};
+        return 1;
+    }
     out[0] = {256, 1, 0};
     out[1] = {128, 2, 0};
     return 2;
@@ -959,6 +1118,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
                      const Config* force = nullptr) {
     constexpr bool F8 = KIND == kE4M3;
     constexpr bool TF = KIND == kTF32;
+    constexpr bool PQ = KIND == kPQ;
     constexpr int CE = chunk_elems(KIND);
     const CUtensorMapDataType tdt = F8   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                   : TF ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -1020,7 +1180,9 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         }
     }
     if (ctas == 0) {
-        if (H == 2 || TF) {
+        if (PQ && H == 1) {
+            if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+        } else if (H == 2 || TF) {
             if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
         } else if (!SH && F8) {
             if (plan(128, 2, stages, qslots, reps)) str = 128, ctas = 2;
@@ -1033,6 +1195,10 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.reps = reps;
     a.rows_alloc = 32 * a.bpc * reps;
     for (int h = 0; h < kBoxKinds; ++h) {
+        if (PQ) {  // rows are decompressed in shared memory, never loaded by TMA
+            maps.doc[h] = maps.q;
+            continue;
+        }
         st = encode_tmap_2d(&maps.doc[h], tdt, dbase, d, n_tokens, row_bytes, CE, static_cast<uint32_t>(8 * (h + 1)));
         if (st != TMS_OK) return st;
     }
@@ -1052,6 +1218,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {
         kern = dense_tc_kernel<2, 128, 1, SH, KIND>;
+    } else if constexpr (PQ) {
+        kern = dense_tc_kernel<1, 256, 1, true, kPQ>;  // H == 2 took the first branch
     } else if constexpr (TF) {
         kern = dense_tc_kernel<1, 128, 1, false, kTF32>;
     } else {

@@ -31,9 +31,9 @@ TMS_DEVERR_BAD_CSR = 8
 
 #: every symbol include/tms.h declares
 EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
-           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16", "tms_topk",
-           "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy",
-           "tms_get_device_error", "tms_status_string", "tms_version")
+           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
+           "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait",
+           "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_status_string", "tms_version")
 
 TMS_STORE_DENSE, TMS_STORE_PQ, TMS_STORE_FP8 = 0, 1, 2
 
@@ -93,6 +93,8 @@ def lib(build_if_missing: bool = True):
             L.tms_build_pq_lut.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _p]
             L.tms_score_pq.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
             L.tms_score_pq_f16.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_score_pq_tc_shared.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _i64, _p, _p, _i64,
+                                                 _p, _i64, _p, _p]
             L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
             L.tms_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
             L.tms_server_submit.argtypes = [_p, _i32, _p, _p, _i64, ctypes.POINTER(ctypes.c_uint64)]
@@ -105,8 +107,8 @@ def lib(build_if_missing: bool = True):
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
             for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
-                         "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16", "tms_topk",
-                         "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
+                         "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
+                         "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
                          "tms_server_destroy", "tms_get_device_error", "tms_version"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -166,6 +168,12 @@ def tms_score_pq_f16(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc
                      cand_ids, cand_offsets, n_cand, out_scores, stream) -> int:
     return lib().tms_score_pq_f16(lut, n_queries, nq, m, k, codes, n_tokens, doc_offsets, doc_lengths, n_docs,
                                   cand_ids, cand_offsets, n_cand, out_scores, stream)
+
+
+def tms_score_pq_tc_shared(queries, qdtype, n_queries, nq, d, codebook, m, k, codes, n_tokens, doc_offsets,
+                           doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream) -> int:
+    return lib().tms_score_pq_tc_shared(queries, qdtype, n_queries, nq, d, codebook, m, k, codes, n_tokens,
+                                        doc_offsets, doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream)
 
 
 def tms_topk(scores, cand_offsets, n_queries, topk, out_scores, out_pos, stream) -> int:
@@ -336,6 +344,23 @@ def score_pq(lut, codes, doc_offsets, doc_lengths, cand_ids, cand_offsets, out=N
         _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
         _dev(cand_ids, torch.int32), _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32),
         _stream_ptr(stream)))
+    return out
+
+
+def score_pq_tc_shared(queries, codebook, codes, doc_offsets, doc_lengths, cand_ids, out=None, stream=None):
+    """PQ MaxSim of queries [n_queries][nq][d] (fp16) sharing one candidate
+    list, codes decompressed in shared memory and scored on the tensor cores:
+    [n_queries][n_cand] fp32."""
+    torch = _torch()
+    nQ, nq, d = queries.shape
+    m, k, _ = codebook.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty((nQ, n_cand), dtype=torch.float32, device=queries.device)
+    _check("tms_score_pq_tc_shared", tms_score_pq_tc_shared(
+        _dev(queries), _dtype_code(queries), nQ, nq, d, _dev(codebook, torch.float32), m, k,
+        _dev(codes, torch.uint8), codes.shape[0], _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32),
+        doc_offsets.shape[0], _dev(cand_ids, torch.int32), n_cand, _dev(out, torch.float32), _stream_ptr(stream)))
     return out
 
 
