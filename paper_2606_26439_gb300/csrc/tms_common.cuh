@@ -194,6 +194,25 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 // Load 32 consecutive fp32 columns of this warp's 32 TMEM lanes (one lane
 // per thread) and wait for them.  The wait names every output register so
 // no use can be scheduled before it.
+// max(a, b, c) in one instruction; NaN inputs are ignored unless all are
+// NaN (as fmaxf ignores one).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// max(m, v[0..31]) with three-input maxima: 16 instructions.
+__device__ __forceinline__ float fold_max32(float m, const float (&v)[32]) {
+    float a[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) a[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    a[10] = fmaxf(v[30], v[31]);
+    const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
+    const float b3 = fmax3(a[9], a[10], m);
+    return fmax3(fmaxf(b0, b1), b2, b3);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile(

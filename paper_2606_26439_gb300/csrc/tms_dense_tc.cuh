@@ -980,11 +980,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
 #pragma unroll
                             for (int c = 0; c < 32; ++c) v[c] *= scl[c0 + c];
                         }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                            for (int c = 0; c < o; ++c) v[c] = fmaxf(v[c], v[c + o]);
-                        rmax[h] = fmaxf(rmax[h], v[0]);
+                        rmax[h] = fold_max32(rmax[h], v);
                     }
                 }
                 if (F8) {
