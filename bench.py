@@ -15,9 +15,14 @@ FP8 E4M3 store (per-token scales), dimension tiling at d = 64/256/512/768
 shared-candidate schedules), the FP8 store at 1,000,000 docs with 64
 queries over all of them (throughput, error and top-10 overlap against the
 fp16 scorer, with and without an fp16 re-score of the FP8 top-100),
-fused PQ (1,000,000 docs, M = 16, K = 256, 64 queries over all of them)
-and the serving loop on a mixed dense + PQ request stream (p50 / p99
-latency and docs/s, batched against one request per launch).
+fused PQ (1,000,000 docs, M = 16, K = 256, 64 queries over all of them:
+fp32 table, fp16 table, and codes decompressed in shared memory on the
+tensor cores), the serving loop on a mixed dense + PQ request stream
+(p50 / p99 latency and docs/s, batched against one request per launch),
+and the served FP8 form (batched, fp16 re-score of each request's top 100)
+against one fp16 request per launch, with top-10 overlap.  The headline
+line also carries the per-step time distribution (median, p10, p90 over
+the K steps) and the oracle's rate on all host cores and on one thread.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tms|reference]
 
@@ -225,19 +230,25 @@ def cpu_sample(lengths, cands, n_sample, seed=1):
     return q, t, off, ln, np.arange(len(ids), dtype=np.int32)
 
 
-def time_oracle(lengths, cands, target_s):
-    """Docs/s of the FP64 oracle on this host's cores (calibrated sample)."""
+def time_oracle(lengths, cands, target_s, threads=None):
+    """Docs/s of the FP64 oracle on this host's cores (calibrated sample),
+    on `threads` threads (default: all)."""
     import oracle
-    q, t, off, ln, c = cpu_sample(lengths, cands, 300)
-    t0 = time.perf_counter()
-    oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
-    rate = len(c) / (time.perf_counter() - t0)
-    n = int(max(300, min(N_CAND, rate * target_s)))
-    q, t, off, ln, c = cpu_sample(lengths, cands, n)
-    t0 = time.perf_counter()
-    oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
-    dt = time.perf_counter() - t0
-    return n / dt, n, dt, oracle.max_threads()
+    cores = oracle.max_threads()
+    oracle.set_threads(threads or cores)
+    try:
+        q, t, off, ln, c = cpu_sample(lengths, cands, 300)
+        t0 = time.perf_counter()
+        oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
+        rate = len(c) / (time.perf_counter() - t0)
+        n = int(max(300, min(N_CAND, rate * target_s)))
+        q, t, off, ln, c = cpu_sample(lengths, cands, n)
+        t0 = time.perf_counter()
+        oracle.dense_scores(q, t, off, ln, c, qdtype=oracle.F16, tdtype=oracle.F16)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    return n / dt, n, dt, threads or cores
 
 
 def run_reference(args, ws, rank):
@@ -286,7 +297,8 @@ def dense_workload(dtype, lengths, cands, device):
 
 
 def time_dense(w, steps, warmup, stream):
-    """Device-resident steps: (ms per step, dense-kernel ms per launch)."""
+    """Device-resident steps: (ms per step, dense-kernel ms per launch,
+    scores, per-step ms -- consecutive step-boundary events on the stream)."""
     import torch
     from paper_2606_26439_gb300 import tms
     out = torch.empty(len(w["flat"]), dtype=torch.float32, device=w["q"].device)
@@ -306,16 +318,17 @@ def time_dense(w, steps, warmup, stream):
             step()
     torch.cuda.synchronize()
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     with torch.cuda.stream(stream):
-        e0.record(stream)
         for i in range(steps):
+            sev[i].record(stream)
             step(kev[i])
-        e1.record(stream)
+        sev[steps].record(stream)
     torch.cuda.synchronize()
-    total = e0.elapsed_time(e1)
+    total = sev[0].elapsed_time(sev[steps])
     kern = [a.elapsed_time(b) for a, b in kev]
-    return total / steps, statistics.mean(kern), out
+    per_step = [sev[i].elapsed_time(sev[i + 1]) for i in range(steps)]
+    return total / steps, statistics.mean(kern), out, per_step
 
 
 def time_dense_e2e(w, steps, warmup, stream):
@@ -574,7 +587,7 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     dev = torch.device("cuda")
     for dtype, steps in (("bf16", 50), ("f32", 10)):
         w = dense_workload(dtype, lengths, cands, dev)
-        ms, kms, _ = time_dense(w, steps, 3, stream)
+        ms, kms, _, _ = time_dense(w, steps, 3, stream)
         elem = 2 if dtype == "bf16" else 4
         alg = iomodel.dense_alg_bytes(w["tokens"], len(w["flat"]), N_QUERIES, NQ, D, elem)
         rows[f"dense_{dtype}"] = {
@@ -585,7 +598,7 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     # the headline after the autotuner picked its launch configuration
     w = dense_workload("f16", lengths, cands, dev)
     _, n_cfg = tms.tune_dense(w["q"], w["tok"], w["off"], w["ln"], w["f"], w["c"], stream=stream)
-    ms, kms, _ = time_dense(w, 30, 3, stream)
+    ms, kms, _, _ = time_dense(w, 30, 3, stream)
     alg = iomodel.dense_alg_bytes(w["tokens"], len(w["flat"]), N_QUERIES, NQ, D, 2)
     rows["dense_f16_autotuned"] = {"docs_per_s": len(w["flat"]) / (ms * 1e-3), "ms_per_step": ms, "kernel_ms": kms,
                                    "configs_timed": n_cfg, "achieved_gbs": alg / (kms * 1e-3) / 1e9,
@@ -781,7 +794,7 @@ def run_tms(args, ws, rank, local):
     barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
-    ms, kms, out = time_dense(w, args.steps, args.warmup, stream)
+    ms, kms, out, per_step = time_dense(w, args.steps, args.warmup, stream)
     clk = clocks.stop()
     assert tms.device_error(stream) == 0, "device error flags raised during the benchmark"
     assert bool(torch.isfinite(out).all())
@@ -812,6 +825,8 @@ def run_tms(args, ws, rank, local):
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "docs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "step_ms": {"median": float(np.median(per_step)), "p10": float(np.percentile(per_step, 10)),
+                    "p90": float(np.percentile(per_step, 90)), "n": len(per_step)},
         "gpu_launches": 2 * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
@@ -819,8 +834,11 @@ def run_tms(args, ws, rank, local):
     torch.cuda.empty_cache()
     if ws == 1 and rank == 0 and args.workload == "headline":
         rate, n, dt, cores = time_oracle(lengths, cands, 15.0)
+        rate1, n1, dt1, _ = time_oracle(lengths, cands, 5.0, threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": "docs/s", "cores": cores, "kind": "oracle",
-                                "sample": f"first {n} candidates of query 0 ({dt:.1f} s, FP64, fp16 stored values)"}
+                                "sample": f"first {n} candidates of query 0 ({dt:.1f} s, FP64, fp16 stored values)",
+                                "one_thread": {"value": rate1, "unit": "docs/s",
+                                               "sample": f"first {n1} candidates of query 0 ({dt1:.1f} s)"}}
         if not args.no_rows:
             line["rows"] = secondary_rows(lengths, cands, stream, hbm_peak, clk["sm_mhz"])
     if rank == 0:
