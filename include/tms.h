@@ -349,6 +349,9 @@ typedef struct {
     int max_batch_requests;        /* requests per launch, 1..4096 (1 = no batching) */
     int64_t max_batch_candidates;  /* candidates per launch (all requests), >= 1 */
     int max_pending;               /* admitted but unfinished requests, >= 1 */
+    int64_t max_pending_bytes;     /* device bytes admitted but unfinished requests may claim in the
+                                      batch buffers -- query + 8 per candidate (id and score) --
+                                      0 = no byte limit */
     int inject_error_batch;        /* test hook: > 0 fails that batch (1-based) on the host, 0 = off */
 } tms_server_config;
 
@@ -367,10 +370,11 @@ tms_status tms_server_create(const tms_server_config *cfg, tms_server **out);
 /*
  * Submit one request (HOST pointers, copied): query [nq][d] of the dense
  * store's dtype, cand_ids [n_cand] document ids of `store` (the FP8 store
- * shares the dense store's ids).  *ticket receives its handle.  Returns
- * TMS_ERR_BUSY when max_pending requests are unfinished,
- * TMS_ERR_UNSUPPORTED when n_cand exceeds max_batch_candidates or the
- * store is absent.
+ * shares the dense store's ids).  *ticket receives its handle.  Admission:
+ * TMS_ERR_BUSY when max_pending requests are unfinished or their device
+ * bytes plus this one's would pass max_pending_bytes; TMS_ERR_UNSUPPORTED
+ * when n_cand exceeds max_batch_candidates, the request alone exceeds
+ * max_pending_bytes, or the store is absent.
  */
 tms_status tms_server_submit(tms_server *s, tms_store store, const void *query, const int32_t *cand_ids,
                              int64_t n_cand, uint64_t *ticket);

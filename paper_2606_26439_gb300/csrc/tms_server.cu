@@ -44,6 +44,7 @@ struct Request {
     std::vector<int32_t> cands;
     std::vector<float> scores;
     std::vector<int32_t> ids;
+    int64_t bytes = 0;  // device bytes claimed in the batch buffers (admission)
     tms_status status = TMS_OK;
     bool done = false;
     Clock::time_point t_submit, t_done;
@@ -99,6 +100,7 @@ struct tms_server {
     std::unordered_map<uint64_t, tms::server::RequestPtr> live;  // admitted, result not yet taken
     uint64_t next_ticket = 1;
     int unfinished = 0;
+    int64_t unfinished_bytes = 0;
     bool stop = false;
     uint64_t batch_ordinal = 0;
     tms_server_stats stats{};
@@ -304,6 +306,7 @@ void complete(tms_server* s, Slot& sl) {
             sl.status = TMS_ERR_CUDA;
     const Clock::time_point now = Clock::now();
     uint64_t n = 0, cands = 0;
+    int64_t bytes = 0;
     for (int st = 0; st < kStores; ++st) {
         const bool rescore = st == 2 && c.rescore_k > 0;
         for (size_t i = 0; i < sl.reqs[st].size(); ++i) {
@@ -326,6 +329,7 @@ void complete(tms_server* s, Slot& sl) {
             }
             r.t_done = now;
             cands += r.cands.size();
+            bytes += r.bytes;
             ++n;
         }
     }
@@ -334,6 +338,7 @@ void complete(tms_server* s, Slot& sl) {
         for (int st = 0; st < kStores; ++st)
             for (auto& r : sl.reqs[st]) r->done = true;
         s->unfinished -= static_cast<int>(n);
+        s->unfinished_bytes -= bytes;
         s->stats.requests += n;
         s->stats.candidates += cands;
     }
@@ -386,7 +391,8 @@ bool config_ok(const tms_server_config& c) {
     if (c.d < 8 || c.d > 1024 || c.d % 8 != 0) return false;
     if (c.nq < 1 || c.nq > 128 || c.topk < 1 || c.topk > 1024) return false;
     if (c.max_batch_requests < 1 || c.max_batch_requests > 4096 || c.max_batch_candidates < 1 ||
-        c.max_batch_candidates >= (int64_t(1) << 31) || c.max_pending < 1 || c.inject_error_batch < 0)
+        c.max_batch_candidates >= (int64_t(1) << 31) || c.max_pending < 1 || c.max_pending_bytes < 0 ||
+        c.inject_error_batch < 0)
         return false;
     if (c.pq_codes) {
         if (!c.pq_codebook || !c.pq_offsets || !c.pq_lengths || c.pq_n_docs < 1 || c.pq_n_tokens < 1) return false;
@@ -447,15 +453,19 @@ extern "C" tms_status tms_server_submit(tms_server* s, tms_store store, const vo
     if ((store == TMS_STORE_PQ && !s->cfg.pq_codes) || (store == TMS_STORE_FP8 && !s->cfg.fp8_codes))
         return TMS_ERR_UNSUPPORTED;
     if (n_cand > s->cfg.max_batch_candidates) return TMS_ERR_UNSUPPORTED;
+    const int64_t bytes = static_cast<int64_t>(s->qbytes) + 8 * n_cand;
+    if (s->cfg.max_pending_bytes > 0 && bytes > s->cfg.max_pending_bytes) return TMS_ERR_UNSUPPORTED;
     auto r = std::make_shared<Request>();
     r->store = store;
+    r->bytes = bytes;
     r->query.assign(static_cast<const uint8_t*>(query), static_cast<const uint8_t*>(query) + s->qbytes);
     r->cands.assign(cand_ids, cand_ids + n_cand);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return TMS_ERR_INVALID_ARG;
-        if (s->unfinished >= s->cfg.max_pending) {
+        if (s->unfinished >= s->cfg.max_pending ||
+            (s->cfg.max_pending_bytes > 0 && s->unfinished_bytes + bytes > s->cfg.max_pending_bytes)) {
             ++s->stats.rejected;
             return TMS_ERR_BUSY;
         }
@@ -463,6 +473,7 @@ extern "C" tms_status tms_server_submit(tms_server* s, tms_store store, const vo
         s->pending.push_back(r);
         s->live.emplace(r->ticket, r);
         ++s->unfinished;
+        s->unfinished_bytes += bytes;
         *ticket = r->ticket;
     }
     s->cv_work.notify_one();

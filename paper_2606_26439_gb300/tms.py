@@ -49,7 +49,7 @@ class ServerConfig(ctypes.Structure):
         ("pq_lengths", ctypes.c_void_p), ("pq_n_docs", ctypes.c_int64),
         ("fp8_codes", ctypes.c_void_p), ("fp8_scales", ctypes.c_void_p), ("rescore_k", ctypes.c_int),
         ("nq", ctypes.c_int), ("topk", ctypes.c_int), ("max_batch_requests", ctypes.c_int),
-        ("max_batch_candidates", ctypes.c_int64), ("max_pending", ctypes.c_int),
+        ("max_batch_candidates", ctypes.c_int64), ("max_pending", ctypes.c_int), ("max_pending_bytes", ctypes.c_int64),
         ("inject_error_batch", ctypes.c_int),
     ]
 
@@ -398,7 +398,8 @@ class Server:
     of each request's ``rescore_k`` best candidates (0: FP8 scores)."""
 
     def __init__(self, doc_tokens, doc_offsets, doc_lengths, nq, topk, max_batch_requests,
-                 max_batch_candidates, max_pending, pq=None, inject_error_batch=0, fp8=None, rescore_k=0):
+                 max_batch_candidates, max_pending, pq=None, inject_error_batch=0, fp8=None, rescore_k=0,
+                 max_pending_bytes=0):
         torch = _torch()
         cfg = ServerConfig()
         cfg.doc_tokens = _dev(doc_tokens)
@@ -426,6 +427,7 @@ class Server:
         cfg.max_batch_requests = max_batch_requests
         cfg.max_batch_candidates = max_batch_candidates
         cfg.max_pending = max_pending
+        cfg.max_pending_bytes = max_pending_bytes
         cfg.inject_error_batch = inject_error_batch
         self.topk = topk
         self.qshape = (nq, cfg.d)

@@ -102,7 +102,7 @@ def test_server_rejects_bad_config(lib):
     cfg.dtype, cfg.d, cfg.n_tokens, cfg.n_docs = tms.TMS_F16, 128, 100, 10
     cfg.nq, cfg.topk, cfg.max_batch_requests, cfg.max_batch_candidates, cfg.max_pending = 32, 10, 8, 1000, 16
     for field, bad in (("nq", 0), ("topk", 1025), ("max_batch_requests", 0), ("max_pending", 0), ("d", 12),
-                       ("dtype", tms.TMS_F32), ("inject_error_batch", -1)):
+                       ("dtype", tms.TMS_F32), ("inject_error_batch", -1), ("max_pending_bytes", -1)):
         good = getattr(cfg, field)
         setattr(cfg, field, bad)
         assert lib.tms_server_create(ctypes.byref(cfg), ctypes.byref(h)) == tms.TMS_ERR_INVALID_ARG, field

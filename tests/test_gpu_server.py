@@ -132,6 +132,34 @@ def test_admission_budget(stores):
     assert len(tickets) >= 2
 
 
+def test_admission_by_device_bytes(stores):
+    """A byte budget for admitted-but-unfinished requests (query + 8 bytes
+    per candidate): past it submit answers BUSY, a request larger than the
+    whole budget is refused outright, and admitted work still completes."""
+    from paper_2606_26439_gb300 import tms
+    q = synth.queries(1, NQ, D, "f16", 31)[0]
+    qbytes = NQ * D * 2
+    cands = np.random.default_rng(31).integers(0, 600, 500).astype(np.int32)
+    one = qbytes + 8 * len(cands)
+    with _server(stores, max_batch_requests=1, max_pending_bytes=3 * one) as srv:
+        with pytest.raises(tms.TmsError) as e:      # alone over the budget
+            srv.submit(q, np.zeros(3 * one // 8, np.int32))
+        assert e.value.status == tms.TMS_ERR_UNSUPPORTED
+        tickets, busy = [], 0
+        for _ in range(40):
+            try:
+                tickets.append(srv.submit(q, cands))
+            except tms.TmsError as err:
+                assert err.status == tms.TMS_ERR_BUSY
+                busy += 1
+        assert busy > 0 and len(tickets) >= 3
+        results = [srv.wait(t) for t in tickets]
+        assert all(np.array_equal(r[1], results[0][1]) for r in results)
+        st = srv.stats()
+        assert st["rejected"] == busy and st["requests"] == len(tickets)
+        srv.wait(srv.submit(q, cands))   # the budget is free again
+
+
 def test_injected_batch_failure_is_reported(stores):
     from paper_2606_26439_gb300 import tms
     reqs = _requests(6, 4)
