@@ -78,6 +78,34 @@ def test_pq_rejects_bad_shapes(lib, m, k):
     assert st in (tms.TMS_ERR_INVALID_ARG, tms.TMS_ERR_UNSUPPORTED)
 
 
+@pytest.mark.parametrize("m,k,want", [(4, 256, "unsupported"), (8, 256, "unsupported"), (16, 0, "invalid"),
+                                      (32, 256, "unsupported")])
+def test_pq_f16_rejects_before_any_device_call(lib, m, k, want):
+    """The fp16-table variant takes m in {16, 32} with m * k <= 4096."""
+    st = tms.tms_score_pq_f16(DUMMY, 1, 32, m, k, DUMMY, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL)
+    assert st == (tms.TMS_ERR_UNSUPPORTED if want == "unsupported" else tms.TMS_ERR_INVALID_ARG)
+
+
+@pytest.mark.parametrize("args,want", [
+    (dict(qdtype=7), "invalid"),                       # not a dtype
+    (dict(qdtype=tms.TMS_BF16), "unsupported"),       # fp16 queries only
+    (dict(nq=33), "unsupported"),                      # shared lists: nq <= 32
+    (dict(m=8, d=64), "unsupported"),                  # M = 16 only
+    (dict(d=100), "invalid"),                          # d % m != 0
+    (dict(k=257), "invalid"),
+    (dict(queries=DUMMY + 8), "invalid"),              # misaligned
+    (dict(n_cand=0, cand_ids=None, out=None), "ok"),   # nothing to launch
+])
+def test_pq_tc_shared_host_checks(lib, args, want):
+    a = dict(queries=DUMMY, qdtype=tms.TMS_F16, n_queries=4, nq=32, d=128, codebook=DUMMY, m=16, k=256,
+             codes=DUMMY, n_tokens=10, offsets=DUMMY, lengths=DUMMY, n_docs=1, cand_ids=DUMMY, n_cand=1, out=DUMMY)
+    a.update(args)
+    st = tms.tms_score_pq_tc_shared(a["queries"], a["qdtype"], a["n_queries"], a["nq"], a["d"], a["codebook"], a["m"],
+                                    a["k"], a["codes"], a["n_tokens"], a["offsets"], a["lengths"], a["n_docs"],
+                                    a["cand_ids"], a["n_cand"], a["out"], NULL)
+    assert st == {"invalid": tms.TMS_ERR_INVALID_ARG, "unsupported": tms.TMS_ERR_UNSUPPORTED, "ok": tms.TMS_OK}[want]
+
+
 def test_pq_lut_rejects_indivisible_d(lib):
     st = tms.tms_build_pq_lut(DUMMY, 0, 1, 32, 100, DUMMY, 16, 256, DUMMY, NULL)
     assert st == tms.TMS_ERR_INVALID_ARG
