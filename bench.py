@@ -524,7 +524,8 @@ def serve_poisson(srv, pool, rate, duration, store_of=None):
     st = srv.stats()
     lat = np.array(lat) * 1e3
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "docs_per_s": docs / wall, "requests": n_req, "batches": st["batches"]}
+            "docs_per_s": docs / wall, "requests": n_req, "batches": st["batches"],
+            "host_enqueue_us_per_batch": 1e6 * st["enqueue_s"] / max(1, st["batches"])}
 
 
 def serving_fp8_row(tok, off, ln):

@@ -360,6 +360,7 @@ typedef struct {
     uint64_t batches;      /* launches */
     uint64_t candidates;   /* scored */
     uint64_t rejected;     /* refused by admission */
+    double enqueue_s;      /* host time spent staging and enqueueing batches (seconds) */
 } tms_server_stats;
 
 /* Create the server and start its worker on the current device.  Returns

@@ -373,7 +373,13 @@ void worker_main(tms_server* s) {
             quit = batch.empty() && !busy && s->stop;
         }
         if (quit) break;
-        if (!batch.empty()) launch(s, s->slots[cur], batch);
+        if (!batch.empty()) {
+            const Clock::time_point t0 = Clock::now();
+            launch(s, s->slots[cur], batch);
+            const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stats.enqueue_s += dt;
+        }
         if (inflight[cur ^ 1]) {
             complete(s, s->slots[cur ^ 1]);
             inflight[cur ^ 1] = false;

@@ -56,7 +56,7 @@ class ServerConfig(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
-                ("rejected", ctypes.c_uint64)]
+                ("rejected", ctypes.c_uint64), ("enqueue_s", ctypes.c_double)]
 
 _lib = None
 _lock = threading.Lock()
@@ -462,7 +462,7 @@ class Server:
         st = ServerStats()
         _check("tms_server_get_stats", lib().tms_server_get_stats(self._h, ctypes.byref(st)))
         return {"requests": st.requests, "batches": st.batches, "candidates": st.candidates,
-                "rejected": st.rejected}
+                "rejected": st.rejected, "enqueue_s": st.enqueue_s}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -85,6 +85,7 @@ def test_server_parity_with_oracle(stores):
         results = [srv.wait(t) for t in tickets]
         st = srv.stats()
     assert st["requests"] == len(reqs) and st["rejected"] == 0
+    assert st["batches"] >= 1 and st["enqueue_s"] > 0.0
     for (store, q, cands), (sc, ids, lat) in zip(reqs, results):
         want = _oracle_scores(stores, store, q, cands)
         n_valid = min(TOPK, len(cands))
