@@ -62,7 +62,8 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
 #define TMS_DEVERR_BAD_ID 1u      /* candidate id outside [0, n_docs)          */
 #define TMS_DEVERR_BAD_RANGE 2u   /* negative length/offset or rows past n_tokens */
 #define TMS_DEVERR_TIMEOUT 4u     /* a pipeline wait exceeded its budget       */
-#define TMS_DEVERR_BAD_CSR 8u     /* cand_offsets[n_queries] != n_cand         */
+#define TMS_DEVERR_BAD_CSR 8u     /* cand_offsets[n_queries] != n_cand, or a list
+                                     with a negative start or a decreasing end */
 
 /*
  * Dense MaxSim (Eq. 1) of n_queries queries over their candidate lists.
@@ -287,6 +288,13 @@ tms_status tms_score_pq_tc_shared(const void *queries, tms_dtype qdtype, int n_q
  * Order: score descending; equal scores by ascending position; NaN after
  * every number (-inf included).  Lists shorter than topk are padded with
  * (-inf, -1).  Limits: 1 <= topk <= 1024, list length < 2^31.
+ *
+ * cand_offsets must be a valid CSR over the scores buffer: 0 <= [q] <=
+ * [q+1] and every list inside it (the library cannot see the buffer's
+ * length).  A negative start or a decreasing pair sets TMS_DEVERR_BAD_CSR
+ * and never reads below the start of `scores`: a negative start reads the
+ * list as empty, a decreasing end is clamped to its start.  An end past the
+ * buffer is not detectable here.
  */
 tms_status tms_topk(const float *scores, const int64_t *cand_offsets, int n_queries, int topk,
                     float *out_scores, int32_t *out_pos, cudaStream_t stream);
@@ -371,11 +379,15 @@ tms_status tms_server_create(const tms_server_config *cfg, tms_server **out);
 /*
  * Submit one request (HOST pointers, copied): query [nq][d] of the dense
  * store's dtype, cand_ids [n_cand] document ids of `store` (the FP8 store
- * shares the dense store's ids).  *ticket receives its handle.  Admission:
+ * shares the dense store's ids).  *ticket receives its handle.  Every id
+ * is checked on the host against the store's document count (pq_n_docs for
+ * the PQ store, n_docs otherwise): an id outside [0, count) returns
+ * TMS_ERR_INVALID_ARG and nothing is admitted.  Admission:
  * TMS_ERR_BUSY when max_pending requests are unfinished or their device
  * bytes plus this one's would pass max_pending_bytes; TMS_ERR_UNSUPPORTED
  * when n_cand exceeds max_batch_candidates, the request alone exceeds
- * max_pending_bytes, or the store is absent.
+ * max_pending_bytes, or the store is absent.  Safe to call from several
+ * threads, also while others wait.
  */
 tms_status tms_server_submit(tms_server *s, tms_store store, const void *query, const int32_t *cand_ids,
                              int64_t n_cand, uint64_t *ticket);
@@ -387,7 +399,8 @@ tms_status tms_server_submit(tms_server *s, tms_store store, const void *query, 
  * *latency_s (may be NULL) receives submit-to-completion time.  Returns the
  * request's status (TMS_ERR_CUDA if its batch failed), TMS_ERR_TIMEOUT if
  * it is not done in time (it stays waitable), TMS_ERR_INVALID_ARG for an
- * unknown ticket.
+ * unknown ticket or one whose result another waiter already took (a
+ * result is handed out once).  Safe to call from several threads.
  */
 tms_status tms_server_wait(tms_server *s, uint64_t ticket, double timeout_s, float *out_scores, int32_t *out_ids,
                            double *latency_s);
@@ -404,6 +417,27 @@ tms_status tms_server_destroy(tms_server *s);
  * synchronises `stream`.
  */
 tms_status tms_get_device_error(cudaStream_t stream, int *flags);
+
+/*
+ * Diagnostics: exercises the timeout path of the pipelined kernels; not
+ * needed in normal use.  Every wait between the roles of those kernels
+ * (tms_score_dense on the tensor cores, the FP8 and shared-list calls,
+ * tms_score_pq_tc_shared, and the staged fused-PQ kernel) is bounded by a
+ * budget of SM clock cycles (default 2e9, about one second at 2 GHz); when
+ * it runs out the kernel sets TMS_DEVERR_TIMEOUT, lets every copy and MMA
+ * it issued land, frees its tensor memory and returns, so the context stays
+ * usable.  tms_debug_set changes, for launches prepared after it returns
+ * (process-wide):
+ *   wait_budget_cycles  the budget (0 restores the default; drain waits at
+ *                       exit always keep the default);
+ *   fault               0, or TMS_FAULT_HOLD_ACCUMULATOR: in the tensor-core
+ *                       dense kernels, CTA 0 never signals its first
+ *                       accumulator as ready, so that CTA's epilogue wait
+ *                       runs out of budget (a flag nothing sets).
+ * Returns TMS_ERR_INVALID_ARG for a negative budget or an unknown fault.
+ */
+#define TMS_FAULT_HOLD_ACCUMULATOR 1
+tms_status tms_debug_set(int64_t wait_budget_cycles, int fault);
 
 /* Static English text for a status code. */
 const char *tms_status_string(tms_status s);

@@ -1,6 +1,7 @@
 // tms_api.cu -- status strings, the device error word and per-device state.
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "tms_internal.h"
@@ -12,6 +13,14 @@
 __device__ unsigned int g_tms_error_word = 0;
 
 namespace tms {
+
+namespace {
+std::atomic<long long> g_debug_budget{0};
+std::atomic<int> g_debug_fault{0};
+}  // namespace
+
+long long debug_wait_budget() { return g_debug_budget.load(std::memory_order_relaxed); }
+int debug_fault() { return g_debug_fault.load(std::memory_order_relaxed); }
 
 namespace {
 constexpr int kMaxDevices = 64;
@@ -119,6 +128,13 @@ tms_status tms_get_device_error(cudaStream_t stream, int* flags) {
     }
     *flags = static_cast<int>(v);
     return v ? TMS_ERR_DEVICE_FLAG : TMS_OK;
+}
+
+tms_status tms_debug_set(int64_t wait_budget_cycles, int fault) {
+    if (wait_budget_cycles < 0 || (fault != 0 && fault != TMS_FAULT_HOLD_ACCUMULATOR)) return TMS_ERR_INVALID_ARG;
+    tms::g_debug_budget.store(wait_budget_cycles, std::memory_order_relaxed);
+    tms::g_debug_fault.store(fault, std::memory_order_relaxed);
+    return TMS_OK;
 }
 
 const char* tms_status_string(tms_status s) {

@@ -19,6 +19,8 @@
 namespace tms {
 
 // ~1 s at 2 GHz: far above any legitimate pipeline wait (microseconds).
+// The default budget of every bounded wait; launches may pass a shorter
+// one (diagnostics: tms_debug_set).  Drain waits always use this one.
 constexpr long long kWaitBudgetCycles = 2000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -59,17 +61,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase of `bar` with parity `parity` to complete.  Returns
-// false (and raises the abort flag) on timeout, or when another role of
-// the CTA has already aborted.
+// false (and raises the abort flag) once `budget` SM cycles have passed
+// (<= 0: kWaitBudgetCycles), or when another role of the CTA has already
+// aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned int* err) {
+                                          unsigned int* err, long long budget) {
     if (mbar_try_wait(bar, parity)) return true;
+    const long long limit = budget > 0 ? budget : kWaitBudgetCycles;
     const long long t0 = clock64();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0u) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > kWaitBudgetCycles) {
+            if (clock64() - t0 > limit) {
                 atomicOr(err, TMS_DEVERR_TIMEOUT);
                 *abort_flag = 1;
                 return false;

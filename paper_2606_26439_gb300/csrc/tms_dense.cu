@@ -145,6 +145,8 @@ tms_status score_dense(const void* queries, tms_dtype dtype, int n_queries, int 
     a.cand_offsets = cand_offsets;
     a.out = out_scores;
     a.err = dev.err;
+    a.budget = debug_wait_budget();
+    a.fault = debug_fault();
     a.n_docs = n_docs;
     a.n_tokens = n_tokens;
     a.n_cand = n_cand;
@@ -230,6 +232,8 @@ extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtyp
     a.cand_offsets = nullptr;
     a.out = out_scores;
     a.err = dev.err;
+    a.budget = debug_wait_budget();
+    a.fault = debug_fault();
     a.n_docs = n_docs;
     a.n_tokens = n_tokens;
     a.n_cand = n_cand;

@@ -154,7 +154,14 @@ struct Args {
     const uint8_t* pq_codes;    // kPQ: [n_tokens][16] uint8
     const float* pq_codebook;   // kPQ: [16][pq_k][8] fp32
     int pq_k;                   // kPQ: centroids per subspace (codes >= pq_k read zeros)
+    long long budget;           // SM cycles a pipeline wait may last (<= 0: kWaitBudgetCycles)
+    int fault;                  // diagnostics: kFaultHoldAccumulator, else 0
 };
+
+// Diagnostics (tms_debug_set): the MMA thread of CTA 0 never signals its
+// first accumulator, so that CTA's epilogue wait runs out of budget and the
+// timeout path -- flag, abort, drain, tensor-memory release -- runs.
+constexpr int kFaultHoldAccumulator = TMS_FAULT_HOLD_ACCUMULATOR;
 
 struct Layout {
     int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, cb_off, code_off, st_off, bar_off, misc_off, total;
@@ -227,9 +234,9 @@ __device__ __forceinline__ int meta_status(const Args& a, int id, int64_t off, i
 // data written by other threads or ordering tensor-core work.  Returns
 // false on timeout / abort.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned int* err) {
+                                          unsigned int* err, long long budget) {
     int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err, budget) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();
     return ok != 0;
@@ -238,8 +245,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
 // Every lane waits (and so observes the phase itself): for barriers that
 // complete the TMA bytes the lanes then read.
 __device__ __forceinline__ bool warp_wait_all(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                              unsigned int* err) {
-    const bool ok = mbar_wait(bar, parity, abort_flag, err);
+                                              unsigned int* err, long long budget) {
+    const bool ok = mbar_wait(bar, parity, abort_flag, err, budget);
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
@@ -420,13 +427,13 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         auto close_st = [&]() -> bool {
             const bool has = lane < nseg;
             const int xs = tst % kStRing;
-            if (!warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err)) return false;
+            if (!warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err, a.budget)) return false;
             if (F8) {
                 // Every epilogue warp passes every tile's scale slot in
                 // order, so the slot of the last tile being free means all
                 // of this super-tile's slots are.
                 const int u = tseg + nseg - 1;
-                if (!warp_wait(&sempty[u % kScaleRing], ((u / kScaleRing) & 1) ^ 1, abort_flag, a.err)) return false;
+                if (!warp_wait(&sempty[u % kScaleRing], ((u / kScaleRing) & 1) ^ 1, abort_flag, a.err, a.budget)) return false;
                 if (has) {
                     // the tile's row scales, from the 16-byte boundary at or below its first row
                     const int ss = (tseg + lane) % kScaleRing;
@@ -463,7 +470,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             // once it sees the new query.
             if (st_q != cur_q) {
                 const int slot = qi % QS;
-                if (!warp_wait(&qempty[slot], ((qi / QS) & 1) ^ 1, abort_flag, a.err)) return false;
+                if (!warp_wait(&qempty[slot], ((qi / QS) & 1) ^ 1, abort_flag, a.err, a.budget)) return false;
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&qfull[slot], static_cast<uint32_t>(qslot_bytes));
                     uint8_t* qdst = q_base + slot * qslot_bytes;
@@ -579,7 +586,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         if (!aborted && nseg > 0 && !close_st()) aborted = true;
         if (!aborted) {
             const int xs = tst % kStRing;
-            if (warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err) && lane == 0) {
+            if (warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err, a.budget) && lane == 0) {
                 StHdr h;
                 h.q = 0;
                 h.n = 0;
@@ -598,7 +605,9 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 for (int i = 1; i <= ns; ++i)
                     drain_wait(&sfull[(tseg - i) % kScaleRing], ((tseg - i) / kScaleRing) & 1);
             }
-            if (qi > 0) drain_wait(&qfull[(qi - 1) % QS], ((qi - 1) / QS) & 1);
+            // every query slot whose load may still be in flight (QS of them)
+            const int nqs = qi < QS ? qi : QS;
+            for (int i = 1; i <= nqs; ++i) drain_wait(&qfull[(qi - i) % QS], ((qi - i) / QS) & 1);
         }
         __syncwarp();
     } else if (PQ && warp == kLoaderWarp) {
@@ -608,7 +617,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         int64_t issued = 0;
         for (int t = 0;; ++t) {
             const int xs = t % kStRing;
-            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr h = slots[xs].h;
             if (h.flags & kEnd) break;
             const bool has = lane < h.nseg;
@@ -625,7 +634,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             __syncwarp();
             if (lane == 0) mbar_arrive(&xempty[xs]);
             const int cs = t % kCodeRing;
-            if (!warp_wait(&codeempty[cs], ((t / kCodeRing) & 1) ^ 1, abort_flag, a.err)) break;
+            if (!warp_wait(&codeempty[cs], ((t / kCodeRing) & 1) ^ 1, abort_flag, a.err, a.budget)) break;
             if (has)  // valid rows of each 8-row group of this tile (a prefix of the group)
                 for (int g8 = 0; g8 < (r + 7) >> 3; ++g8)
                     gvalid[cs * (STR / 8) + (col >> 3) + g8] = static_cast<uint8_t>(min(8, r - 8 * g8));
@@ -652,7 +661,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         int64_t issued = 0;
         for (int t = 0;; ++t) {
             const int xs = t % kStRing;
-            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr h = slots[xs].h;
             if (h.flags & kEnd) break;
             const bool has = lane < h.nseg;
@@ -668,7 +677,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             const CUtensorMap* dmap = &maps.doc[(n8 >> 3) - 1];
             bool ok = true;
             for (int kc = 0; kc < NCH; ++kc) {
-                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err, a.budget)) {
                     ok = false;
                     break;
                 }
@@ -712,15 +721,15 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         uint32_t ph = 0;
         for (int t = 0;; ++t) {
             const int xs = t % kStRing;
-            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr h = slots[xs].h;
             if (h.flags & kEnd) break;
             const int cs = t % kCodeRing;
-            if (!warp_wait_all(&codefull[cs], (t / kCodeRing) & 1, abort_flag, a.err)) break;
+            if (!warp_wait_all(&codefull[cs], (t / kCodeRing) & 1, abort_flag, a.err, a.budget)) break;
             const uint8_t* crow = code_ring + cs * STR * kPqM;
             bool ok = true;
             for (int kc = 0; kc < NCH; ++kc) {
-                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                if (!warp_wait(&empty[s], ph ^ 1, abort_flag, a.err, a.budget)) {
                     ok = false;
                     break;
                 }
@@ -793,7 +802,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         int qi = 0, cur_q = -1;
         for (int t = 0;; ++t) {
             const int xs = t % kStRing;
-            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr h = slots[xs].h;
             if (h.flags & kEnd) break;
             __syncwarp();
@@ -801,14 +810,14 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             bool ok = true;
             if (h.q != cur_q) {
                 const int slot = qi % QS;
-                if (!warp_wait_all(&qfull[slot], (qi / QS) & 1, abort_flag, a.err)) break;
+                if (!warp_wait_all(&qfull[slot], (qi / QS) & 1, abort_flag, a.err, a.budget)) break;
                 split(q_base + slot * qslot_bytes, qlo_base + slot * qslot_bytes, qslot_bytes);
                 if (lane == 0) mbar_arrive(&qconv[slot]);
                 ++qi;
                 cur_q = h.q;
             }
             for (int kc = 0; kc < NCH; ++kc) {
-                if (!warp_wait_all(&full[s], ph, abort_flag, a.err)) {
+                if (!warp_wait_all(&full[s], ph, abort_flag, a.err, a.budget)) {
                     ok = false;
                     break;
                 }
@@ -833,19 +842,19 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             bool any = false;
             for (int t = 0;; ++t) {
                 const int xs = t % kStRing;
-                if (!mbar_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+                if (!mbar_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
                 const StHdr x = slots[xs].h;
                 if (x.flags & kEnd) break;
                 mbar_arrive(&xempty[xs]);
                 if (x.q != cur_q) {
                     if (cur_q >= 0) mma_commit(&qempty[qslot]);
                     qslot = qi % QS;
-                    if (!mbar_wait(TF ? &qconv[qslot] : &qfull[qslot], (qi / QS) & 1, abort_flag, a.err)) break;
+                    if (!mbar_wait(TF ? &qconv[qslot] : &qfull[qslot], (qi / QS) & 1, abort_flag, a.err, a.budget)) break;
                     ++qi;
                     cur_q = x.q;
                 }
                 const int ab = t % kAcc;
-                if (!mbar_wait(&tempty[ab], ((t / kAcc) & 1) ^ 1, abort_flag, a.err)) break;
+                if (!mbar_wait(&tempty[ab], ((t / kAcc) & 1) ^ 1, abort_flag, a.err, a.budget)) break;
                 tc_fence_after();
                 bool ok = true;
                 const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * H * STR);
@@ -853,7 +862,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 const uint64_t qlo_desc = desc_sw128(smem_u32(qlo_base + qslot * qslot_bytes));
                 const uint32_t idesc = a.idesc | (static_cast<uint32_t>(x.n >> 3) << 17);
                 for (int kc = 0; kc < NCH; ++kc) {
-                    if (!mbar_wait(TF ? &conv[s] : &full[s], ph, abort_flag, a.err)) {
+                    if (!mbar_wait(TF ? &conv[s] : &full[s], ph, abort_flag, a.err, a.budget)) {
                         ok = false;
                         break;
                     }
@@ -888,7 +897,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                     }
                 }
                 if (!ok) break;
-                mma_commit(&tfull[ab]);
+                if (a.fault != kFaultHoldAccumulator || blockIdx.x != 0 || t != 0) mma_commit(&tfull[ab]);
             }
             // Every MMA this thread issued must finish before TMEM is freed.
             if (any) {
@@ -922,11 +931,11 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         for (int h = 0; h < H; ++h) qsc[h] = 1.f;
         for (int t = 0; !aborted; ++t) {
             const int xs = t % kStRing;
-            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err)) break;
+            if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr xh = slots[xs].h;
             if (xh.flags & kEnd) break;
             const int ab = t % kAcc;
-            if (!warp_wait(&tfull[ab], (t / kAcc) & 1, abort_flag, a.err)) break;
+            if (!warp_wait(&tfull[ab], (t / kAcc) & 1, abort_flag, a.err, a.budget)) break;
             tc_fence_after();
             for (int i = 0; i < xh.nseg; ++i, ++tseg) {
                 const SegInfo si = slots[xs].seg[i];
@@ -955,7 +964,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 }
                 const float* scl = nullptr;  // scl[c]: scale of column c's document row
                 if (F8) {
-                    if (!warp_wait_all(&sfull[ss], (tseg / kScaleRing) & 1, abort_flag, a.err)) {
+                    if (!warp_wait_all(&sfull[ss], (tseg / kScaleRing) & 1, abort_flag, a.err, a.budget)) {
                         aborted = true;
                         break;
                     }
@@ -1009,7 +1018,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                             // the copy's warps add their block sums in block order
                             const int pb = copy * 2 + (mydocs & 1);
                             const uint32_t use = mydocs >> 1;
-                            if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err)) {
+                            if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err, a.budget)) {
                                 aborted = true;
                                 break;
                             }
@@ -1018,7 +1027,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                                 mbar_arrive(&pfull[pb]);
                             }
                             if (b == 0) {
-                                if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err)) {
+                                if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err, a.budget)) {
                                     aborted = true;
                                     break;
                                 }

@@ -107,6 +107,8 @@ tms_status prepare(const uint8_t* q_codes, const float* q_scales, int n_queries,
     a->q_scales = q_scales;
     a->t_scales = doc_scales;
     a->err = dev->err;
+    a->budget = debug_wait_budget();
+    a->fault = debug_fault();
     a->n_docs = n_docs;
     a->n_tokens = n_tokens;
     a->n_cand = n_cand;

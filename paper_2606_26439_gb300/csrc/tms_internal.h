@@ -33,6 +33,12 @@ tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const voi
 // box_elems x 1, no swizzle, zero fill outside; load with tma_load_2d(x, 0).
 tms_status encode_tmap_1d_f32(CUtensorMap* map, const void* base, uint64_t n, uint32_t box_elems);
 
+// Diagnostics set by tms_debug_set, read when a launch is prepared: the
+// bound of every pipeline wait in SM cycles (0 = the kernels' default) and
+// the fault to inject (0 = none).
+long long debug_wait_budget();
+int debug_fault();
+
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 inline tms_status launch_status(cudaError_t e) {

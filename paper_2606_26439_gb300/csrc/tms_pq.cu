@@ -77,6 +77,7 @@ struct Args {
     int n_queries;
     int nq;
     int K;
+    long long budget;  // SM cycles a wait may last (<= 0: kWaitBudgetCycles)
 };
 
 // Codes of one token as M/4 32-bit words (M bytes, 4-byte aligned rows).
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args
                         if (nf >= 0) issue(noff, 0, min(kPiece, nlen));
                     }
                     const int b = consumed & 1;
-                    const bool got = mbar_wait(&wbar[b], (consumed >> 1) & 1, &abort_flag, a.err);
+                    const bool got = mbar_wait(&wbar[b], (consumed >> 1) & 1, &abort_flag, a.err, a.budget);
                     ++consumed;
                     if (!__all_sync(0xffffffffu, got)) {
                         ok = false;
@@ -648,6 +649,7 @@ tms_status score(const float* lut, int n_queries, int nq, int m, int k, const ui
     a.cand_offsets = cand_offsets;
     a.out = out_scores;
     a.err = dev.err;
+    a.budget = debug_wait_budget();
     a.n_docs = n_docs;
     a.n_tokens = n_tokens;
     a.n_cand = n_cand;

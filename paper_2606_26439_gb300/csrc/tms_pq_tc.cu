@@ -42,6 +42,8 @@ extern "C" tms_status tms_score_pq_tc_shared(const void* queries, tms_dtype qdty
     a.cand_offsets = nullptr;
     a.out = out_scores;
     a.err = dev.err;
+    a.budget = debug_wait_budget();
+    a.fault = debug_fault();
     a.n_docs = n_docs;
     a.n_tokens = n_tokens;
     a.n_cand = n_cand;

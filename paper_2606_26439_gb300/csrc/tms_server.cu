@@ -459,6 +459,12 @@ extern "C" tms_status tms_server_submit(tms_server* s, tms_store store, const vo
     if ((store == TMS_STORE_PQ && !s->cfg.pq_codes) || (store == TMS_STORE_FP8 && !s->cfg.fp8_codes))
         return TMS_ERR_UNSUPPORTED;
     if (n_cand > s->cfg.max_batch_candidates) return TMS_ERR_UNSUPPORTED;
+    // Ids are checked here, next to the copy, so a bad id never reaches the
+    // device (where it would score NaN and set a bit of the process-wide
+    // device error word that another caller would then read as its own).
+    const int64_t n_ids = store == TMS_STORE_PQ ? s->cfg.pq_n_docs : s->cfg.n_docs;
+    for (int64_t i = 0; i < n_cand; ++i)
+        if (cand_ids[i] < 0 || cand_ids[i] >= n_ids) return TMS_ERR_INVALID_ARG;
     const int64_t bytes = static_cast<int64_t>(s->qbytes) + 8 * n_cand;
     if (s->cfg.max_pending_bytes > 0 && bytes > s->cfg.max_pending_bytes) return TMS_ERR_UNSUPPORTED;
     auto r = std::make_shared<Request>();
@@ -493,12 +499,15 @@ extern "C" tms_status tms_server_wait(tms_server* s, uint64_t ticket, double tim
     RequestPtr r;
     {
         std::unique_lock<std::mutex> lk(s->mu);
-        auto it = s->live.find(ticket);
+        const auto it = s->live.find(ticket);
         if (it == s->live.end()) return TMS_ERR_INVALID_ARG;
         r = it->second;
         const auto limit = std::chrono::duration<double>(timeout_s > 1e6 ? 1e6 : timeout_s);
         if (!s->cv_done.wait_for(lk, limit, [&] { return r->done; })) return TMS_ERR_TIMEOUT;
-        s->live.erase(it);
+        // The lock was released while waiting: submit may have rehashed the
+        // map (invalidating `it`) and another waiter on the same ticket may
+        // have taken the result.  Erase by key; only one waiter wins.
+        if (s->live.erase(ticket) == 0) return TMS_ERR_INVALID_ARG;
     }
     std::memcpy(out_scores, r->scores.data(), r->scores.size() * 4);
     std::memcpy(out_ids, r->ids.data(), r->ids.size() * 4);

@@ -62,7 +62,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* buf, int* total)
 
 __global__ void __launch_bounds__(kThreads, 1)
     topk_kernel(const float* __restrict__ scores, const int64_t* __restrict__ cand_offsets, int n_queries, int k,
-                float* __restrict__ out_scores, int32_t* __restrict__ out_pos) {
+                float* __restrict__ out_scores, int32_t* __restrict__ out_pos, unsigned int* err) {
     __shared__ uint32_t whist[kWarps][256];
     __shared__ uint32_t hist[256];
     __shared__ unsigned long long sel[kMaxK];
@@ -72,8 +72,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int s_count;
     const int q = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // A list must lie inside the scores buffer: a negative start or a
+    // decreasing pair is a CSR error -- flagged, and the list read as empty
+    // (a negative start) or clamped to its start (never read below it).
     int64_t c0 = cand_offsets[q], c1 = cand_offsets[q + 1];
-    if (c1 < c0) c1 = c0;
+    if (c0 < 0 || c1 < c0) {
+        if (threadIdx.x == 0) atomicOr(err, TMS_DEVERR_BAD_CSR);
+        if (c0 < 0) c0 = c1 = 0;
+        if (c1 < c0) c1 = c0;
+    }
     const int n = static_cast<int>((c1 - c0) > 0x7fffffff ? 0x7fffffff : (c1 - c0));
     const float* s = scores + c0;
 
@@ -193,6 +200,6 @@ extern "C" tms_status tms_topk(const float* scores, const int64_t* cand_offsets,
     tms_status st = current_device(&dev);
     if (st != TMS_OK) return st;
     topk::topk_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(scores, cand_offsets, n_queries,
-                                                                                        topk, out_scores, out_pos);
+                                                                                        topk, out_scores, out_pos, dev.err);
     return launch_status(cudaGetLastError());
 }

@@ -29,11 +29,14 @@ TMS_DEVERR_BAD_RANGE = 2
 TMS_DEVERR_TIMEOUT = 4
 TMS_DEVERR_BAD_CSR = 8
 
+TMS_FAULT_HOLD_ACCUMULATOR = 1
+
 #: every symbol include/tms.h declares
 EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
            "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
            "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait",
-           "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_status_string", "tms_version")
+           "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_status_string",
+           "tms_version")
 
 TMS_STORE_DENSE, TMS_STORE_PQ, TMS_STORE_FP8 = 0, 1, 2
 
@@ -103,13 +106,14 @@ def lib(build_if_missing: bool = True):
             L.tms_server_get_stats.argtypes = [_p, ctypes.POINTER(ServerStats)]
             L.tms_server_destroy.argtypes = [_p]
             L.tms_get_device_error.argtypes = [_p, ctypes.POINTER(ctypes.c_int)]
+            L.tms_debug_set.argtypes = [_i64, _i32]
             L.tms_status_string.argtypes = [_i32]
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
             for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
                          "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
                          "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
-                         "tms_server_destroy", "tms_get_device_error", "tms_version"):
+                         "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_version"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -185,6 +189,10 @@ def tms_get_device_error(stream=None):
     flags = ctypes.c_int(0)
     st = lib().tms_get_device_error(stream, ctypes.byref(flags))
     return st, flags.value
+
+
+def tms_debug_set(wait_budget_cycles: int, fault: int) -> int:
+    return lib().tms_debug_set(int(wait_budget_cycles), int(fault))
 
 
 def tms_version() -> int:

@@ -159,3 +159,12 @@ def test_tune_dense_rejects_like_score_dense(lib):
     st = lib.tms_tune_dense(DUMMY, 0, 1, 0, 128, DUMMY, 10, DUMMY, DUMMY, 1, DUMMY, DUMMY, 1, DUMMY, NULL,
                             ctypes.byref(n))
     assert st == tms.TMS_ERR_INVALID_ARG and n.value == 0
+
+
+def test_debug_set_checks_and_restores(lib):
+    """tms_debug_set refuses a negative budget and unknown faults; (0, 0)
+    restores the defaults (no device needed)."""
+    assert tms.tms_debug_set(-1, 0) == tms.TMS_ERR_INVALID_ARG
+    assert tms.tms_debug_set(0, 7) == tms.TMS_ERR_INVALID_ARG
+    assert tms.tms_debug_set(1000, tms.TMS_FAULT_HOLD_ACCUMULATOR) == tms.TMS_OK
+    assert tms.tms_debug_set(0, 0) == tms.TMS_OK

@@ -12,7 +12,10 @@ device-resident dense store, PQ store and FP8 copy of the dense store.
 * a request's result is bitwise the same alone (batches of one) and mixed
   with others in large batches;
 * admission by pending budget, a host-injected batch failure, bounded
-  waits and unknown tickets.
+  waits and unknown tickets;
+* candidate ids outside the store are refused at submit, on the host;
+* submit and wait from different threads at once (the ticket map grows and
+  rehashes meanwhile), and two waiters on one ticket: one gets the result.
 """
 from __future__ import annotations
 
@@ -62,8 +65,6 @@ def _requests(n, seed, n_stores=2):
         n_docs = 500 if store == 1 else 600
         size = int(g.choice([0, 1, 7, 10, 33, 250, n_docs]))
         cands = g.choice(n_docs, size, replace=False).astype(np.int32)
-        if size > 20 and i % 5 == 0:
-            cands[3] = n_docs + 5       # a bad id: scores NaN, sorts last
         q = synth.queries(1, NQ, D, "f16", seed * 1000 + i)[0]
         reqs.append((store, q, cands))
     return reqs
@@ -212,8 +213,6 @@ def test_server_fp8_store(stores, rescore):
     for i in range(30):
         size = int(g.choice([0, 1, 9, 10, 11, 40, 41, 300, 600]))
         cands = g.choice(600, size, replace=False).astype(np.int32)
-        if size > 20 and i % 4 == 0:
-            cands[5] = 600 + 3       # a bad id: scores NaN, sorts last
         reqs.append((synth.queries(1, NQ, D, "f16", 900 + i)[0], cands))
     with _server(stores, rescore_k=rescore) as srv:
         results = [srv.wait(srv.submit(q, c, tms.TMS_STORE_FP8)) for q, c in reqs]
@@ -244,3 +243,98 @@ def test_server_fp8_rescore_uses_fp16_scores(stores):
         sd, idd, _ = srv.wait(srv.submit(q, cands, tms.TMS_STORE_DENSE))
     assert np.array_equal(s8.view(np.uint32), sd.view(np.uint32))
     assert np.array_equal(i8, idd)
+
+
+def test_bad_ids_refused_on_host(stores):
+    """An id outside [0, n_docs) of the request's store is refused by submit
+    with TMS_ERR_INVALID_ARG: nothing is admitted, nothing reaches the
+    device, and the device error word stays clear."""
+    from paper_2606_26439_gb300 import tms
+    q = synth.queries(1, NQ, D, "f16", 41)[0]
+    tms.device_error()  # start from a clear word
+    with _server(stores) as srv:
+        for store, bad in ((tms.TMS_STORE_DENSE, 600), (tms.TMS_STORE_DENSE, -1), (tms.TMS_STORE_PQ, 500),
+                           (tms.TMS_STORE_PQ, -7), (tms.TMS_STORE_FP8, 600), (tms.TMS_STORE_FP8, 2 ** 31 - 1)):
+            cands = np.array([3, 4, bad, 5], np.int32)
+            with pytest.raises(tms.TmsError) as e:
+                srv.submit(q, cands, store)
+            assert e.value.status == tms.TMS_ERR_INVALID_ARG
+        # PQ ids up to 499 are valid on the PQ store, 500..599 only on the dense one
+        srv.wait(srv.submit(q, np.array([0, 499], np.int32), tms.TMS_STORE_PQ))
+        srv.wait(srv.submit(q, np.array([0, 599], np.int32), tms.TMS_STORE_DENSE))
+        st = srv.stats()
+    assert st["requests"] == 2 and st["rejected"] == 0
+    assert tms.device_error() == 0
+
+
+def test_submit_while_waiting(stores):
+    """One thread submits 600 requests while the main thread waits for each
+    ticket as soon as it exists: the server's ticket map grows (and rehashes)
+    while waiters hold their lookups.  Every result equals the same request
+    run alone."""
+    import threading
+    reqs = []
+    g = np.random.default_rng(43)
+    for i in range(600):
+        store = i % 3
+        n_docs = 500 if store == 1 else 600
+        cands = g.choice(n_docs, int(g.integers(1, 60)), replace=False).astype(np.int32)
+        reqs.append((store, synth.queries(1, NQ, D, "f16", 43_000 + i)[0], cands))
+    with _server(stores, max_batch_requests=1) as srv:
+        alone = [srv.wait(srv.submit(q, c, s))[:2] for s, q, c in reqs[:60]]
+    tickets = [None] * len(reqs)
+    ready = [threading.Event() for _ in reqs]
+    errors = []
+    with _server(stores, max_batch_requests=64, max_pending=1024) as srv:
+        def producer():
+            try:
+                for i, (s, q, c) in enumerate(reqs):
+                    tickets[i] = srv.submit(q, c, s)
+                    ready[i].set()
+            except Exception as e:  # surfaced below
+                errors.append(e)
+                for ev in ready:
+                    ev.set()
+        th = threading.Thread(target=producer)
+        th.start()
+        results = []
+        for i in range(len(reqs)):
+            assert ready[i].wait(60)
+            assert not errors, errors
+            results.append(srv.wait(tickets[i])[:2])
+        th.join()
+    assert not errors, errors
+    for (sa, ia), (sm, im) in zip(alone, results[:60]):
+        assert np.array_equal(sa.view(np.uint32), sm.view(np.uint32))
+        assert np.array_equal(ia, im)
+    for (s, q, c), (sm, im) in zip(reqs, results):
+        n_valid = min(TOPK, len(c))
+        assert np.all(np.isin(im[:n_valid], c)) and np.all(im[n_valid:] == -1)
+
+
+def test_two_waiters_one_ticket(stores):
+    """Two threads wait on the same ticket: one takes the result, the other
+    is told the ticket is no longer known (a result is handed out once)."""
+    import threading
+    from paper_2606_26439_gb300 import tms
+    q = synth.queries(1, NQ, D, "f16", 45)[0]
+    big = np.random.default_rng(45).integers(0, 600, 150_000).astype(np.int32)
+    with _server(stores) as srv:
+        blockers = [srv.submit(q, big) for _ in range(4)]   # keep the GPU busy for a while
+        t = srv.submit(q, np.arange(50, dtype=np.int32))
+        outcome = []
+
+        def waiter():
+            try:
+                srv.wait(t)
+                outcome.append("ok")
+            except tms.TmsError as e:
+                outcome.append(e.status)
+        ths = [threading.Thread(target=waiter) for _ in range(2)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        for b in blockers:
+            srv.wait(b)
+    assert sorted(outcome, key=str) == sorted(["ok", tms.TMS_ERR_INVALID_ARG], key=str)
