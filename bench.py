@@ -9,7 +9,10 @@ each scoring its own random 100,000-document candidate subset.  One step
 = one tms_score_dense launch over all 16 x 100,000 candidates plus one
 tms_topk launch (top-10 per query).  Metric: documents scored per second.
 
-Also reported (N = 1 only): the same workload in bf16, fp32 and on the
+Also reported (N = 1 only): config 1 (one query over 10,000 documents of
+128 tokens, three corpus copies rotated so that L2 holds none of the copy a
+launch reads), measured ceilings (shared-memory load and HBM read
+bandwidth), the same workload in bf16, fp32 and on the
 FP8 E4M3 store (per-token scales), dimension tiling at d = 64/256/512/768
 (200,000 docs, 32 queries over all of them, bf16, top-100; per-query and
 shared-candidate schedules), the FP8 store at 1,000,000 docs with 64
@@ -23,6 +26,15 @@ and the served FP8 form (batched, fp16 re-score of each request's top 100)
 against one fp16 request per launch, with top-10 overlap.  The headline
 line also carries the per-step time distribution (median, p10, p90 over
 the K steps) and the oracle's rate on all host cores and on one thread.
+
+The oracle leg of the secondary rows: for one query per configuration
+(config 1 in full; query 0's 100,000 candidates per dtype of config 2;
+query 0 over all 200,000 documents per d of config 3; query 0 over all
+1,000,000 documents for PQ and for the FP8 store) the FP64 oracle scores the
+whole list on the host cores.  Its time is reported (docs/s, cores), and
+the GPU's scores and top-k of that query are compared with it: relative
+error (max, mean) and top-k overlap -- for the FP8 store against the oracle
+of the fp16 corpus it was quantized from, i.e. the store's whole error.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tms|reference]
 
@@ -251,6 +263,72 @@ def time_oracle(lengths, cands, target_s, threads=None):
     return n / dt, n, dt, threads or cores
 
 
+def rows_of(off, lengths, ids):
+    """Token rows of documents ``ids`` in order, as one index array."""
+    lens = np.asarray(lengths, np.int64)[ids]
+    starts = np.asarray(off, np.int64)[ids]
+    before = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    return np.repeat(starts - before, lens) + np.arange(int(lens.sum()), dtype=np.int64)
+
+
+def host_docs(rows_d, off, lengths, ids):
+    """Host copy of documents ``ids`` of a device row array, repacked for the
+    oracle: (rows as numpy, offsets, lengths)."""
+    import torch
+    lens = np.asarray(lengths, np.int32)[ids]
+    if len(ids) == len(lengths) and np.array_equal(ids, np.arange(len(lengths))):
+        sub, sub_off = rows_d.cpu(), np.asarray(off, np.int64)
+    else:
+        sub = rows_d[torch.from_numpy(rows_of(off, lengths, ids)).to(rows_d.device)].cpu()
+        sub_off = synth.offsets_of(lens)
+    if sub.dtype in (torch.float16, torch.bfloat16):
+        sub = sub.view(torch.int16).numpy().view(np.uint16)
+    else:
+        sub = sub.numpy()
+    return sub, sub_off, lens
+
+
+def _odt(dtype):
+    import oracle
+    return {"f16": oracle.F16, "bf16": oracle.BF16, "f32": oracle.F32}[dtype]
+
+
+def oracle_dense_query(q, dtype, tok_d, off, lengths, ids):
+    """The oracle leg: FP64 Eq. 1 of one query (host tensor [nq][d]) over a
+    whole candidate list of a device corpus, on all host cores.  Returns
+    (scores, seconds of oracle arithmetic)."""
+    import oracle
+    import torch
+    sub, sub_off, lens = host_docs(tok_d, off, lengths, ids)
+    qh = q.contiguous()
+    qa = qh.view(torch.int16).numpy().view(np.uint16) if qh.dtype in (torch.float16, torch.bfloat16) else qh.numpy()
+    t0 = time.perf_counter()
+    want = oracle.dense_scores(qa, sub, sub_off, lens, np.arange(len(ids), dtype=np.int32),
+                               qdtype=_odt(dtype), tdtype=_odt(dtype))
+    return want, time.perf_counter() - t0
+
+
+def quality_vs_oracle(got, want, gpu_top, k):
+    """GPU scores of one query against the oracle's scores of the same list:
+    relative error (floor Nq 1e-3, the parity tests' rule), the overlap of the
+    GPU's top-k (positions from tms_topk) with the oracle's own top-k, and
+    how many ranks hold the same position."""
+    import oracle
+    got = np.asarray(got, np.float64)
+    fin = np.isfinite(want)
+    rel = np.abs(got[fin] - want[fin]) / np.maximum(np.abs(want[fin]), NQ * 1e-3)
+    _, wp = oracle.topk(want, k)
+    gp = np.asarray(gpu_top)[:k]
+    return {"rel_err_max": float(rel.max()), "rel_err_mean": float(rel.mean()),
+            f"top{k}_overlap": len(set(gp.tolist()) & set(wp.tolist())) / k,
+            f"top{k}_same_rank": int(np.sum(gp == wp))}
+
+
+def oracle_timing(n_docs, seconds):
+    import oracle
+    return {"docs": int(n_docs), "seconds": seconds, "docs_per_s": n_docs / seconds, "cores": oracle.max_threads()}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -383,7 +461,9 @@ def fp8_store_row(stream, hbm_peak):
     Throughput of the FP8 pass, and its quality against the fp16 tensor-core
     scorer on the same documents (itself within 1e-3 of FP64 in the parity
     tests): relative score error over all 64M scores, overlap of the top-10,
-    and the overlap after re-scoring the FP8 top-100 with the fp16 scorer."""
+    and the overlap after re-scoring the FP8 top-100 with the fp16 scorer.
+    Query 0 is also scored over all documents by the FP64 oracle: the FP8
+    scores' error and top-10 overlap against it (raw and re-scored)."""
     import torch
     from paper_2606_26439_gb300 import tms
     dev = torch.device("cuda")
@@ -433,8 +513,16 @@ def fp8_store_row(stream, hbm_peak):
     short_np = short.view(nQ, k_short).cpu().numpy()
     top10_rs = np.take_along_axis(short_np, rtp.cpu().numpy().astype(np.int64), axis=1)
     overlap_rs = float(np.mean([len(set(a) & set(b)) / TOPK for a, b in zip(top10_rs, top10_16)]))
+    # the oracle leg: query 0 over all 1,000,000 documents in FP64 on the fp16
+    # corpus the store was quantized from
+    want0, secs = oracle_dense_query(Q[0].cpu(), "f16", tok, synth.offsets_of(lens), lens, np.arange(n))
+    rescored = quality_vs_oracle(s16[0].cpu().numpy(), want0, top10_rs[0], TOPK)
+    vs_oracle = {"fp8": quality_vs_oracle(s8[0].cpu().numpy(), want0, top10_8[0], TOPK),
+                 "fp8_rescored_top100": {k: v for k, v in rescored.items() if k.startswith("top")},
+                 "fp16": quality_vs_oracle(s16[0].cpu().numpy(), want0, top10_16[0], TOPK)}
     fl = iomodel.dense_alg_flops(tok_total * nQ, NQ, D)
-    row = {"docs_per_s": nQ * n / (ms8 * 1e-3), "kernel_ms": ms8, "fp16_shared_kernel_ms": ms16,
+    row = {"vs_fp64_oracle_query0": vs_oracle, "oracle_query0": oracle_timing(n, secs),
+           "docs_per_s": nQ * n / (ms8 * 1e-3), "kernel_ms": ms8, "fp16_shared_kernel_ms": ms16,
            "speedup_vs_fp16": ms16 / ms8, "tflops": fl / (ms8 * 1e-3) / 1e12,
            "store_reads_gbs": tok_total * (D + 4) * (nQ // 8) / (ms8 * 1e-3) / 1e9,
            "rel_err_vs_fp16_mean": float(rel.mean()), "rel_err_vs_fp16_max": float(rel.max()),
@@ -442,6 +530,80 @@ def fp8_store_row(stream, hbm_peak):
     del tok, tc, tsc, s8, s16, rel
     torch.cuda.empty_cache()
     return row
+
+
+def config1_row(stream, hbm_peak):
+    """Config 1: one query (Nq=32, d=128, fp16) over 10,000 documents of
+    exactly 128 tokens (unit-normalised Gaussian, seed 0): every score and
+    the top-10.  328 MB of tokens, a few times the L2, so three identical
+    copies of the corpus are rotated between launches and the copy a launch
+    reads was last touched two launches (~650 MB of traffic) earlier.  Each
+    launch (tms_score_dense + tms_topk) is timed alone with events; median
+    and p10/p90 over 200 launches.  The oracle scores the same query in full
+    on the host cores (its timing and the GPU's parity against it)."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    dev = torch.device("cuda")
+    n, nd = 10_000, 128
+    lengths = synth.lengths_fixed(n, nd)
+    tok, off, ln = synth.dense_corpus(n, lengths, D, "f16", 0)
+    Q = synth.queries(1, NQ, D, "f16", 0)
+    copies = [tok.to(dev) for _ in range(3)]
+    off_d, ln_d, q_d = torch.from_numpy(off).to(dev), torch.from_numpy(ln).to(dev), Q.to(dev)
+    f = torch.arange(n, dtype=torch.int32, device=dev)
+    c = torch.tensor([0, n], dtype=torch.int64, device=dev)
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    ts = torch.empty((1, TOPK), dtype=torch.float32, device=dev)
+    tp = torch.empty((1, TOPK), dtype=torch.int32, device=dev)
+    reps = 200
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with torch.cuda.stream(stream):
+        for i in range(6):
+            tms.score_dense(q_d, copies[i % 3], off_d, ln_d, f, c, out=out, stream=stream)
+            tms.topk(out, c, TOPK, ts, tp, stream=stream)
+        for i in range(reps):
+            ev[i][0].record(stream)
+            tms.score_dense(q_d, copies[i % 3], off_d, ln_d, f, c, out=out, stream=stream)
+            ev[i][1].record(stream)
+            tms.topk(out, c, TOPK, ts, tp, stream=stream)
+            ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    assert tms.device_error(stream) == 0
+    step = np.array([a.elapsed_time(b2) for a, _, b2 in ev])
+    kern = np.array([a.elapsed_time(b) for a, b, _ in ev])
+    alg = iomodel.dense_alg_bytes(n * nd, n, 1, NQ, D, 2)
+    kmed = float(np.median(kern))
+    row = {"workload": "config 1: 1 query Nq=32, d=128, fp16, 10,000 docs x 128 tokens, every score + top-10",
+           "docs_per_s": n / (float(np.median(step)) * 1e-3),
+           "step_ms": {"median": float(np.median(step)), "p10": float(np.percentile(step, 10)),
+                       "p90": float(np.percentile(step, 90))},
+           "kernel_ms_median": kmed, "achieved_gbs": alg / (kmed * 1e-3) / 1e9,
+           "frac_hbm_measured": alg / (kmed * 1e-3) / 1e9 / hbm_peak,
+           "frac_hbm_nominal_8tbs": alg / (kmed * 1e-3) / 1e9 / 8000.0,
+           "l2": "3 corpus copies rotated (984 MB > 129 MB L2)"}
+    got = out.cpu().numpy()
+    gtop = tp.cpu().numpy()[0]
+    want, secs = oracle_dense_query(Q[0], "f16", tok, off, lengths, np.arange(n))
+    row["oracle"] = oracle_timing(n, secs)
+    row["vs_oracle"] = quality_vs_oracle(got, want, gtop, TOPK)
+    del copies
+    torch.cuda.empty_cache()
+    return row
+
+
+def peaks_row(stream):
+    """Measured ceilings: shared-memory load bandwidth (conflict-free 128-bit
+    loads, all SMs) and HBM streaming-read bandwidth (4 GB buffer)."""
+    import torch
+    from paper_2606_26439_gb300 import tms
+    lds = tms.peak_shared_load(20000, stream=stream)
+    buf = torch.empty(1 << 32, dtype=torch.uint8, device="cuda")
+    buf.fill_(1)
+    rd = tms.peak_hbm_read(buf, reps=5, stream=stream)
+    del buf
+    torch.cuda.empty_cache()
+    return {"lds_gbs": lds, "hbm_read_gbs": rd}
 
 
 def serving_row():
@@ -586,15 +748,30 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     from paper_2606_26439_gb300 import tms
     rows = {}
     dev = torch.device("cuda")
+    peaks = peaks_row(stream)
+    rows["measured_peaks"] = peaks
+    rows["config1"] = config1_row(stream, hbm_peak)
+    off0 = synth.offsets_of(lengths)
+
+    def vs_oracle_q0(w, dtype, out):
+        """Oracle leg for query 0 of a config-2 launch: its 100,000 scores and
+        top-10 against the FP64 oracle, and the oracle's own timing."""
+        _, tp = tms.topk(out, w["c"], TOPK)
+        want, secs = oracle_dense_query(w["Q"][0], dtype, w["tok"], off0, lengths, cands[0])
+        q = quality_vs_oracle(out[:N_CAND].cpu().numpy(), want, tp.cpu().numpy()[0], TOPK)
+        return want, {"oracle_query0": oracle_timing(N_CAND, secs), "vs_oracle_query0": q}
+
     for dtype, steps in (("bf16", 50), ("f32", 10)):
         w = dense_workload(dtype, lengths, cands, dev)
-        ms, kms, _, _ = time_dense(w, steps, 3, stream)
+        ms, kms, out, _ = time_dense(w, steps, 3, stream)
         elem = 2 if dtype == "bf16" else 4
         alg = iomodel.dense_alg_bytes(w["tokens"], len(w["flat"]), N_QUERIES, NQ, D, elem)
         rows[f"dense_{dtype}"] = {
             "docs_per_s": len(w["flat"]) / (ms * 1e-3), "ms_per_step": ms, "kernel_ms": kms,
-            "achieved_gbs": alg / (kms * 1e-3) / 1e9, "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak}
-        del w
+            "achieved_gbs": alg / (kms * 1e-3) / 1e9, "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak,
+            "frac_hbm_read_peak": alg / (kms * 1e-3) / 1e9 / peaks["hbm_read_gbs"]}
+        rows[f"dense_{dtype}"].update(vs_oracle_q0(w, dtype, out)[1])
+        del w, out
         torch.cuda.empty_cache()
     # the headline after the autotuner picked its launch configuration
     w = dense_workload("f16", lengths, cands, dev)
@@ -604,7 +781,12 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     rows["dense_f16_autotuned"] = {"docs_per_s": len(w["flat"]) / (ms * 1e-3), "ms_per_step": ms, "kernel_ms": kms,
                                    "configs_timed": n_cfg, "achieved_gbs": alg / (kms * 1e-3) / 1e9,
                                    "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak}
-    del w
+    # the headline's fp16 scores of query 0 against the oracle (the FP8 row reuses them)
+    out16 = tms.score_dense(w["q"], w["tok"], w["off"], w["ln"], w["f"], w["c"], stream=stream)
+    torch.cuda.synchronize()
+    want16, q16 = vs_oracle_q0(w, "f16", out16)
+    rows["dense_f16"] = q16
+    del w, out16
     torch.cuda.empty_cache()
     # FP8 E4M3 store of the headline workload (quantized on the device)
     w = dense_workload("f16", lengths, cands, dev)
@@ -635,29 +817,43 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     kms = e[0].elapsed_time(e[1]) / reps
     alg = iomodel.fp8_alg_bytes(w["tokens"], len(w["flat"]), N_QUERIES, NQ, D)
     qbytes = iomodel.quantize_alg_bytes(n_tok, D, 2)
+    _, tp8 = tms.topk(out, w["c"], TOPK)
     rows["fp8_e4m3"] = {"docs_per_s": len(w["flat"]) / (kms * 1e-3), "kernel_ms": kms,
                         "achieved_gbs": alg / (kms * 1e-3) / 1e9, "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak,
-                        "quantize_corpus_ms": quant_ms, "quantize_gbs": qbytes / (quant_ms * 1e-3) / 1e9}
+                        "quantize_corpus_ms": quant_ms, "quantize_gbs": qbytes / (quant_ms * 1e-3) / 1e9,
+                        # FP8 scores of query 0 against the FP64 oracle of the fp16 corpus they were
+                        # quantized from: quantization error included (the FP8 store's quality)
+                        "vs_fp64_oracle_query0": quality_vs_oracle(out[:N_CAND].cpu().numpy(), want16,
+                                                                   tp8.cpu().numpy()[0], TOPK)}
     del w, tc, tsc, qc, qsc, out
     torch.cuda.empty_cache()
     rows["fp8_e4m3_shared_1m"] = fp8_store_row(stream, hbm_peak)
+    del want16
     rows["serving_mix_1m_dense_1m_pq"], rows["serving_fp8_vs_fp16_1m"] = serving_row()
-    # dimension tiling: 200K docs, 32 queries over all docs, bf16, top-100
+    # dimension tiling: 200K docs, 32 queries over all docs, bf16, top-100, in
+    # the per-query schedule and the shared-list schedule; query 0 of each
+    # against the oracle (all 200,000 scores and the top-100)
     n3 = 200_000
     len3 = synth.lengths_uniform(n3, LO, HI, 2)
+    off3 = synth.offsets_of(len3)
+    tok3 = int(len3.astype(np.int64).sum())
     for d in (64, 256, 512, 768):
         tok, off, ln = synth.device_dense_corpus(len3, d, "bf16", 2, dev)
-        Q = synth.queries(32, NQ, d, "bf16", 2).to(dev)
+        Qh = synth.queries(32, NQ, d, "bf16", 2)
+        Q = Qh.to(dev)
         f = torch.arange(n3, dtype=torch.int32, device=dev).repeat(32)
         c = torch.arange(0, 33 * n3, n3, dtype=torch.int64, device=dev)
         out = torch.empty(32 * n3, dtype=torch.float32, device=dev)
+        out_sh = torch.empty((32, n3), dtype=torch.float32, device=dev)
         ts = torch.empty((32, 100), dtype=torch.float32, device=dev)
         tp = torch.empty((32, 100), dtype=torch.int32, device=dev)
+        ts_sh, tp_sh = torch.empty_like(ts), torch.empty_like(tp)
         with torch.cuda.stream(stream):
             for _ in range(3):
                 tms.score_dense(Q, tok, off, ln, f, c, out=out, stream=stream)
+                tms.score_dense_shared(Q, tok, off, ln, f[:n3], out=out_sh, stream=stream)
         torch.cuda.synchronize()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         with torch.cuda.stream(stream):
             e[0].record(stream)
             for _ in range(3):
@@ -665,45 +861,31 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
             e[1].record(stream)
             tms.topk(out, c, 100, ts, tp, stream=stream)
             e[2].record(stream)
+            for _ in range(5):
+                tms.score_dense_shared(Q, tok, off, ln, f[:n3], out=out_sh, stream=stream)
+            e[3].record(stream)
+            tms.topk(out_sh.view(-1), c, 100, ts_sh, tp_sh, stream=stream)
+            e[4].record(stream)
         torch.cuda.synchronize()
         kms = e[0].elapsed_time(e[1]) / 3
-        alg = iomodel.dense_alg_bytes(int(len3.astype(np.int64).sum()) * 32, 32 * n3, 32, NQ, d, 2)
+        kms_sh = e[2].elapsed_time(e[3]) / 5
+        alg = iomodel.dense_alg_bytes(tok3 * 32, 32 * n3, 32, NQ, d, 2)
+        fl = iomodel.dense_alg_flops(tok3 * 32, NQ, d)
+        want0, secs = oracle_dense_query(Qh[0], "bf16", tok, off3, len3, np.arange(n3))
         rows[f"dtile_bf16_d{d}"] = {"docs_per_s": 32 * n3 / (kms * 1e-3), "kernel_ms": kms,
                                    "topk100_ms": e[1].elapsed_time(e[2]),
                                    "achieved_gbs": alg / (kms * 1e-3) / 1e9,
-                                   "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak}
-        del tok, off, ln, Q, f, out
-        torch.cuda.empty_cache()
-    # the same workload in the shared-candidate schedule (queries stacked in N)
-    for d in (64, 256, 512, 768):
-        tok, off, ln = synth.device_dense_corpus(len3, d, "bf16", 2, dev)
-        Q = synth.queries(32, NQ, d, "bf16", 2).to(dev)
-        f = torch.arange(n3, dtype=torch.int32, device=dev)
-        c = torch.arange(0, 33 * n3, n3, dtype=torch.int64, device=dev)
-        out = torch.empty((32, n3), dtype=torch.float32, device=dev)
-        ts = torch.empty((32, 100), dtype=torch.float32, device=dev)
-        tp = torch.empty((32, 100), dtype=torch.int32, device=dev)
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                tms.score_dense_shared(Q, tok, off, ln, f, out=out, stream=stream)
-        torch.cuda.synchronize()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        with torch.cuda.stream(stream):
-            e[0].record(stream)
-            for _ in range(5):
-                tms.score_dense_shared(Q, tok, off, ln, f, out=out, stream=stream)
-            e[1].record(stream)
-            tms.topk(out.view(-1), c, 100, ts, tp, stream=stream)
-            e[2].record(stream)
-        torch.cuda.synchronize()
-        kms = e[0].elapsed_time(e[1]) / 5
-        tok3 = int(len3.astype(np.int64).sum())
-        fl = iomodel.dense_alg_flops(tok3 * 32, NQ, d)
-        rows[f"dtile_shared_bf16_d{d}"] = {"docs_per_s": 32 * n3 / (kms * 1e-3), "kernel_ms": kms,
-                                          "topk100_ms": e[1].elapsed_time(e[2]),
-                                          "tflops": fl / (kms * 1e-3) / 1e12,
-                                          "corpus_reads_gbs": tok3 * d * 2 / (kms * 1e-3) / 1e9}
-        del tok, off, ln, Q, f, out
+                                   "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak,
+                                   "vs_oracle_query0": quality_vs_oracle(out[:n3].cpu().numpy(), want0,
+                                                                         tp.cpu().numpy()[0], 100),
+                                   "oracle_query0": oracle_timing(n3, secs)}
+        rows[f"dtile_shared_bf16_d{d}"] = {"docs_per_s": 32 * n3 / (kms_sh * 1e-3), "kernel_ms": kms_sh,
+                                          "topk100_ms": e[3].elapsed_time(e[4]),
+                                          "tflops": fl / (kms_sh * 1e-3) / 1e12,
+                                          "corpus_reads_gbs": tok3 * d * 2 / (kms_sh * 1e-3) / 1e9,
+                                          "vs_oracle_query0": quality_vs_oracle(out_sh[0].cpu().numpy(), want0,
+                                                                                tp_sh.cpu().numpy()[0], 100)}
+        del tok, off, ln, Q, f, out, out_sh
         torch.cuda.empty_cache()
     # fused PQ: 1M docs, M=16, K=256, dsub=8, 64 fp16 queries over all docs
     n4, M, K, dsub, nQ4 = 1_000_000, 16, 256, 8, 64
@@ -742,12 +924,15 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     tok4 = int(len4.astype(np.int64).sum()) * nQ4
     alg = iomodel.pq_alg_bytes(tok4, nQ4 * n4, nQ4, NQ, M, K)
     lds = iomodel.pq_lut_reads_bytes(tok4, NQ, M)
-    lds_peak = 152 * 128 * (sm_mhz or 1900.0) * 1e6 / 1e9  # GB/s of shared-memory loads
+    lds_peak = peaks["lds_gbs"]  # measured: conflict-free 128-bit shared-memory loads, all SMs
+    lds_nominal = 152 * 128 * (sm_mhz or 1900.0) * 1e6 / 1e9
     rows["pq_m16_k256"] = {"docs_per_s": nQ4 * n4 / (pq_ms * 1e-3), "kernel_ms": pq_ms, "lut_ms": lut_ms,
                            "achieved_gbs": alg / (pq_ms * 1e-3) / 1e9,
                            "frac_hbm": alg / (pq_ms * 1e-3) / 1e9 / hbm_peak,
                            "lds_gbs": lds / (pq_ms * 1e-3) / 1e9, "lds_peak_gbs": lds_peak,
-                           "frac_lds": lds / (pq_ms * 1e-3) / 1e9 / lds_peak}
+                           "lds_peak_kind": "measured (tms_peak_shared_load)",
+                           "frac_lds": lds / (pq_ms * 1e-3) / 1e9 / lds_peak,
+                           "frac_lds_nominal": lds / (pq_ms * 1e-3) / 1e9 / lds_nominal}
     # the same queries with the codes decompressed in shared memory and scored
     # on the tensor cores (one shared list: every document)
     ids = torch.arange(n4, dtype=torch.int32, device=dev)
@@ -767,14 +952,34 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
                                        "max_rel_diff_vs_fp32_table": rel_tc,
                                        "tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
                                        "codes_reads_gbs": tok4 // nQ4 * M * ((nQ4 + 3) // 4) / (tc_ms * 1e-3) / 1e9}
+    out_tc_q0 = out_tc[0].clone()
     del out_tc
+    # the oracle leg: query 0 over all 1,000,000 documents, FP64 decompress-then-dot
+    import oracle
+    cb_h, codes_h = cb.cpu().numpy(), codes.cpu().numpy()
+    Qh = Q.cpu().contiguous()
+    t0 = time.perf_counter()
+    want0 = oracle.pq_decompress_scores(Qh[0].view(torch.int16).numpy().view(np.uint16), cb_h, codes_h,
+                                        synth.offsets_of(len4), len4, np.arange(n4, dtype=np.int32),
+                                        qdtype=oracle.F16)
+    pq_oracle_s = time.perf_counter() - t0
+    del codes_h
+    c1 = c[:2]
+    pq_vs = {}
+    for name, scores in (("fp32_table", out), ("fp16_table", out16), ("tensor_core", out_tc_q0)):
+        _, tpq = tms.topk(scores, c1, TOPK)
+        pq_vs[name] = quality_vs_oracle(scores[:n4].cpu().numpy(), want0, tpq.cpu().numpy()[0], TOPK)
+    rows["pq_m16_k256"]["vs_oracle_query0"] = pq_vs["fp32_table"]
+    rows["pq_m16_k256"]["oracle_query0"] = oracle_timing(n4, pq_oracle_s)
+    rows["pq_m16_k256_tensor_core"]["vs_oracle_query0"] = pq_vs["tensor_core"]
     # the same pass through the fp16 table: half the shared-memory bytes per lookup
     lds16 = lds // 2
     rows["pq_m16_k256_f16_table"] = {"docs_per_s": nQ4 * n4 / (pq16_ms * 1e-3), "kernel_ms": pq16_ms,
                                      "speedup_vs_fp32_table": pq_ms / pq16_ms,
                                      "max_rel_diff_vs_fp32_table": rel,
                                      "lds_gbs": lds16 / (pq16_ms * 1e-3) / 1e9, "lds_peak_gbs": lds_peak,
-                                     "frac_lds": lds16 / (pq16_ms * 1e-3) / 1e9 / lds_peak}
+                                     "frac_lds": lds16 / (pq16_ms * 1e-3) / 1e9 / lds_peak,
+                                     "vs_oracle_query0": pq_vs["fp16_table"]}
     return rows
 
 
@@ -841,7 +1046,12 @@ def run_tms(args, ws, rank, local):
                                 "one_thread": {"value": rate1, "unit": "docs/s",
                                                "sample": f"first {n1} candidates of query 0 ({dt1:.1f} s)"}}
         if not args.no_rows:
-            line["rows"] = secondary_rows(lengths, cands, stream, hbm_peak, clk["sm_mhz"])
+            try:
+                line["rows"] = secondary_rows(lengths, cands, stream, hbm_peak, clk["sm_mhz"])
+            except Exception as exc:  # the headline line is still printed
+                import traceback
+                line["rows_error"] = "".join(traceback.format_exception_only(type(exc), exc)).strip()
+                traceback.print_exc()
     if rank == 0:
         print(json.dumps(line), flush=True)
 

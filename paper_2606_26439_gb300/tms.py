@@ -36,7 +36,7 @@ EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_q
            "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
            "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait",
            "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_status_string",
-           "tms_version")
+           "tms_version", "tms_peak_shared_load", "tms_peak_hbm_read")
 
 TMS_STORE_DENSE, TMS_STORE_PQ, TMS_STORE_FP8 = 0, 1, 2
 
@@ -107,13 +107,16 @@ def lib(build_if_missing: bool = True):
             L.tms_server_destroy.argtypes = [_p]
             L.tms_get_device_error.argtypes = [_p, ctypes.POINTER(ctypes.c_int)]
             L.tms_debug_set.argtypes = [_i64, _i32]
+            L.tms_peak_shared_load.argtypes = [_i32, _p, ctypes.POINTER(ctypes.c_double)]
+            L.tms_peak_hbm_read.argtypes = [_p, _i64, _i32, _p, ctypes.POINTER(ctypes.c_double)]
             L.tms_status_string.argtypes = [_i32]
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
             for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
                          "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
                          "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
-                         "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_version"):
+                         "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_version",
+                         "tms_peak_shared_load", "tms_peak_hbm_read"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -193,6 +196,22 @@ def tms_get_device_error(stream=None):
 
 def tms_debug_set(wait_budget_cycles: int, fault: int) -> int:
     return lib().tms_debug_set(int(wait_budget_cycles), int(fault))
+
+
+def peak_shared_load(iters=20000, stream=None) -> float:
+    """Measured shared-memory load bandwidth of the device, GB/s (all SMs)."""
+    g = ctypes.c_double()
+    _check("tms_peak_shared_load", lib().tms_peak_shared_load(int(iters), _stream_ptr(stream), ctypes.byref(g)))
+    return g.value
+
+
+def peak_hbm_read(buf, reps=5, stream=None) -> float:
+    """Measured HBM streaming-read bandwidth over the device tensor ``buf``, GB/s."""
+    g = ctypes.c_double()
+    nbytes = buf.numel() * buf.element_size()
+    _check("tms_peak_hbm_read", lib().tms_peak_hbm_read(_dev(buf), nbytes - nbytes % 16, int(reps),
+                                                        _stream_ptr(stream), ctypes.byref(g)))
+    return g.value
 
 
 def tms_version() -> int:

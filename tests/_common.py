@@ -84,3 +84,68 @@ def assert_topk_consistent(got_s, got_p, scores_ref, k: int, tol_abs):
         mask = np.ones(n, bool)
         mask[valid] = False
         assert ref_nan_last[mask].max() <= chosen.min() + tol_abs
+
+
+def _tau(s, rtol, nq):
+    return rtol * np.maximum(np.abs(s), nq * 1e-3)
+
+
+def _tied(a, b, rtol, nq):
+    """Elementwise: a and b equal within the parity tolerance of each (both
+    NaN, or the same infinity, count as equal)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    both_nan = np.isnan(a) & np.isnan(b)
+    same_inf = np.isinf(a) & np.isinf(b) & (a == b)
+    fin = np.isfinite(a) & np.isfinite(b)
+    with np.errstate(invalid="ignore"):
+        close = fin & (np.abs(a - b) <= _tau(a, rtol, nq) + _tau(b, rtol, nq))
+    return both_nan | same_inf | close
+
+
+def assert_topk_matches_oracle(got_pos, want, k: int, dtype: str, nq: int) -> int:
+    """Top-k parity against the oracle's own scores, tolerance ties merged.
+
+    ``want`` holds the oracle's scores of the whole list (NaN for bad
+    candidates); ``got_pos`` the GPU's top-k positions.  With the oracle's
+    ranking o (score desc, position asc, NaN last) and tau(s) = rtol *
+    max(|s|, nq * 1e-3) (rtol of ``dtype``):
+      * got_pos holds min(k, n) distinct positions of the list, then -1;
+      * rank by rank, the GPU's pick and the oracle's candidate are tied
+        within tolerance (|s - o_r| <= tau(s) + tau(o_r)): inside a run of
+        tolerance-tied oracle scores the GPU may order differently, never
+        across runs;
+      * no candidate left out beats the weakest pick by more than the
+        tolerance (no run is cut except at its tied boundary).
+    Returns how many ranks hold exactly the oracle's position.
+    """
+    import oracle
+    rtol = RTOL[dtype]
+    want = np.asarray(want, np.float64)
+    got_pos = np.asarray(got_pos, np.int64)
+    n = len(want)
+    m = min(k, n)
+    assert got_pos.shape == (k,)
+    assert np.all(got_pos[m:] == -1), "padding past the list's length"
+    picks = got_pos[:m]
+    assert np.all((picks >= 0) & (picks < n)), "position out of range"
+    assert len(np.unique(picks)) == m, "repeated position"
+    _, opos = oracle.topk(want, k)
+    o = want[opos[:m]]
+    s = want[picks]
+    bad = np.nonzero(~_tied(s, o, rtol, nq))[0]
+    assert bad.size == 0, (f"rank {bad[0]}: GPU pick {picks[bad[0]]} (oracle score {s[bad[0]]!r}) is not tied "
+                           f"with the oracle's rank-{bad[0]} candidate {opos[bad[0]]} ({o[bad[0]]!r})")
+    if m < n:
+        rest = np.ones(n, bool)
+        rest[picks] = False
+        low = np.where(np.isnan(s), -np.inf, s)
+        weakest = low.min()
+        out = np.where(np.isnan(want[rest]), -np.inf, want[rest])
+        if np.isfinite(weakest):
+            with np.errstate(invalid="ignore"):
+                over = out - weakest - _tau(out, rtol, nq) - _tau(weakest, rtol, nq)
+            assert not np.any(over > 0), f"a left-out candidate beats the weakest pick by {over.max():.3e}"
+        else:
+            assert not np.any(out > weakest), "a left-out candidate beats a -inf / NaN pick"
+    return int(np.sum(picks == opos[:m]))

@@ -70,3 +70,33 @@ def edge_candidates(n_docs, n_queries, seed):
         n = 0 if qi == 2 else int(g.integers(1, n_docs))
         cands.append(synth.candidates(n_docs, n, seed, qi))
     return cands
+
+
+def rows_of(off, lengths, ids):
+    """Token rows of documents ``ids`` in order, as one index array."""
+    lens = np.asarray(lengths, np.int64)[ids]
+    starts = np.asarray(off, np.int64)[ids]
+    if lens.sum() == 0:
+        return np.zeros(0, np.int64)
+    before = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    return np.repeat(starts - before, lens) + np.arange(int(lens.sum()), dtype=np.int64)
+
+
+def gather_docs(rows_d, off, lengths, ids):
+    """Host copy of the rows of documents ``ids`` of a device array, repacked
+    (offsets, lengths) for the oracle.  ``ids`` = every document in order
+    copies the array as it is."""
+    import torch
+    lens = np.asarray(lengths, np.int32)[ids]
+    if len(ids) == len(lengths) and np.array_equal(ids, np.arange(len(lengths))):
+        return rows_d.cpu(), np.asarray(off, np.int64), lens
+    idx = torch.from_numpy(rows_of(off, lengths, ids)).to(rows_d.device)
+    return rows_d[idx].cpu(), synth.offsets_of(lens), lens
+
+
+def oracle_dense_list(q, tok_d, off, lengths, ids):
+    """FP64 Eq. 1 of one query over a whole candidate list of a device corpus."""
+    sub, sub_off, sub_len = gather_docs(tok_d, off, lengths, ids)
+    qa, qdt = oracle_view(q)
+    ta, tdt = oracle_view(sub)
+    return oracle.dense_scores(qa, ta, sub_off, sub_len, np.arange(len(ids), dtype=np.int32), qdtype=qdt, tdtype=tdt)

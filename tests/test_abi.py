@@ -13,13 +13,17 @@ from paper_2606_26439_gb300 import build as tms_build
 from paper_2606_26439_gb300 import tms
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "tms.h")
+INCLUDE = os.path.join(ROOT, "include")
 
 
 def _declared():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tms_[a-z0-9_]+)\s*\(", text)))
+    """Every function declared by the headers under include/."""
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(tms_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -168,3 +172,14 @@ def test_debug_set_checks_and_restores(lib):
     assert tms.tms_debug_set(0, 7) == tms.TMS_ERR_INVALID_ARG
     assert tms.tms_debug_set(1000, tms.TMS_FAULT_HOLD_ACCUMULATOR) == tms.TMS_OK
     assert tms.tms_debug_set(0, 0) == tms.TMS_OK
+
+
+def test_peak_probes_reject_bad_arguments(lib):
+    """The measurement calls check their arguments on the host."""
+    g = ctypes.c_double()
+    assert lib.tms_peak_shared_load(0, None, ctypes.byref(g)) == tms.TMS_ERR_INVALID_ARG
+    assert lib.tms_peak_shared_load(10, None, None) == tms.TMS_ERR_INVALID_ARG
+    assert lib.tms_peak_hbm_read(None, 1 << 20, 1, None, ctypes.byref(g)) == tms.TMS_ERR_INVALID_ARG
+    assert lib.tms_peak_hbm_read(DUMMY + 8, 1 << 20, 1, None, ctypes.byref(g)) == tms.TMS_ERR_INVALID_ARG
+    assert lib.tms_peak_hbm_read(DUMMY, 1000, 1, None, ctypes.byref(g)) == tms.TMS_ERR_INVALID_ARG
+    assert lib.tms_peak_hbm_read(DUMMY, 1 << 20, 0, None, ctypes.byref(g)) == tms.TMS_ERR_INVALID_ARG

@@ -12,7 +12,7 @@ import pytest
 import oracle
 import synth
 from tests import gpu_cases as gc
-from tests._common import assert_scores_close, assert_topk_consistent, oracle_view
+from tests._common import assert_scores_close, assert_topk_consistent, assert_topk_matches_oracle, oracle_view
 
 pytestmark = pytest.mark.gpu
 
@@ -121,14 +121,11 @@ def test_config1_full_parity_and_top10(cuda_lib):
     want = gc.oracle_dense_multi(Q, tok, off, ln, cands)
     assert_scores_close(got, want, "f16", nq)
     s_d, co_d = gc.to_dev(got, np.array([0, n_docs], np.int64))
-    ts, tp = tms.topk(s_d, co_d, 10)
-    torch.cuda.synchronize()
-    tol = 1e-3 * np.abs(want).max()
-    assert_topk_consistent(ts.cpu().numpy()[0], tp.cpu().numpy()[0], want, 10, 2 * tol)
-    ws, wp = oracle.topk(want, 10)
-    # identical ranking unless oracle scores are tied within the tolerance
-    if np.all(np.diff(ws) < -2 * tol):
-        assert np.array_equal(tp.cpu().numpy()[0], wp)
+    for k in (10, 100):
+        ts, tp = tms.topk(s_d, co_d, k)
+        torch.cuda.synchronize()
+        # the oracle's own top-k, runs of tolerance-tied scores merged
+        assert_topk_matches_oracle(tp.cpu().numpy()[0], want, k, "f16", nq)
 
 
 def _sampled_parity(tok_d, off, ln, Q, cands, flat_scores, dtype, n_sample, seed):
@@ -175,37 +172,57 @@ def test_config2_full_size_sampled(cuda_lib, dtype):
     assert tms.device_error() == 0
     scores = out.cpu().numpy()
     assert np.isfinite(scores).all()
-    _sampled_parity(tok_d, synth.offsets_of(lengths), lengths, Q, cands, scores, dtype, 1600, 1)
+    off = synth.offsets_of(lengths)
+    _sampled_parity(tok_d, off, lengths, Q, cands, scores, dtype, 1600, 1)
+    # query 0: every one of its 100,000 scores and its top-10 / top-100
+    # against the oracle's own scores of the whole list
+    want0 = gc.oracle_dense_list(Q[0], tok_d, off, lengths, cands[0])
+    assert_scores_close(scores[:n_cand], want0, dtype, nq)
+    for k in (10, 100):
+        ts, tp = tms.topk(out, c_d, k)
+        torch.cuda.synchronize()
+        assert_topk_matches_oracle(tp.cpu().numpy()[0], want0, k, dtype, nq)
     del tok_d
     torch.cuda.empty_cache()
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("d", [64, 256, 512, 768])
-def test_config3_dimension_tiling_sampled(cuda_lib, d):
+def test_config3_dimension_tiling_full_query(cuda_lib, d):
     """200,000 documents, Nd ~ U[32, 180], bf16, 32 queries each scoring all
-    documents: sampled parity and a consistent top-100 per query."""
+    documents, in both schedules (per-query lists: tms_score_dense; one
+    shared list: tms_score_dense_shared).  Query 0: all 200,000 scores and
+    the top-100 against the oracle's own scores (tolerance ties merged);
+    sampled parity on the other queries; each schedule's top-100 is exactly
+    the top-100 of its own scores."""
     import torch
     from paper_2606_26439_gb300 import tms
     n_docs, nq, n_queries = 200_000, 32, 32
     lengths = synth.lengths_uniform(n_docs, 32, 180, 2)
+    off = synth.offsets_of(lengths)
     tok_d, off_d, ln_d = synth.device_dense_corpus(lengths, d, "bf16", 2)
     Q = synth.queries(n_queries, nq, d, "bf16", 2)
     cands = [np.arange(n_docs, dtype=np.int32)] * n_queries
     flat, co = gc.csr(cands)
     q_d, f_d, c_d = gc.to_dev(Q, flat, co)
-    out = tms.score_dense(q_d, tok_d, off_d, ln_d, f_d, c_d)
-    ts, tp = tms.topk(out, c_d, 100)
+    per_query = tms.score_dense(q_d, tok_d, off_d, ln_d, f_d, c_d)
+    shared = tms.score_dense_shared(q_d, tok_d, off_d, ln_d, f_d[:n_docs]).view(-1)
+    tops = [tms.topk(x, c_d, 100) for x in (per_query, shared)]
     torch.cuda.synchronize()
     assert tms.device_error() == 0
-    scores = out.cpu().numpy()
-    _sampled_parity(tok_d, synth.offsets_of(lengths), lengths, Q, cands, scores, "bf16", 640, 3)
-    # the top-100 of each query is exactly the top-100 of its own scores
-    tsn, tpn = ts.cpu().numpy(), tp.cpu().numpy()
-    for qi in range(n_queries):
-        row = scores[qi * n_docs:(qi + 1) * n_docs]
-        ws, wp = oracle.topk(row.astype(np.float64), 100)
-        assert np.array_equal(tpn[qi], wp)
-        assert np.array_equal(tsn[qi], ws.astype(np.float32))
+    s_pq, s_sh = per_query.cpu().numpy(), shared.cpu().numpy()
+    _sampled_parity(tok_d, off, lengths, Q, cands, s_pq, "bf16", 640, 3)
+    _sampled_parity(tok_d, off, lengths, Q, cands, s_sh, "bf16", 640, 4)
+    want0 = gc.oracle_dense_list(Q[0], tok_d, off, lengths, cands[0])
+    assert_scores_close(s_pq[:n_docs], want0, "bf16", nq)
+    assert_scores_close(s_sh[:n_docs], want0, "bf16", nq)
+    for scores, (ts, tp) in zip((s_pq, s_sh), tops):
+        tsn, tpn = ts.cpu().numpy(), tp.cpu().numpy()
+        assert_topk_matches_oracle(tpn[0], want0, 100, "bf16", nq)
+        for qi in range(n_queries):
+            row = scores[qi * n_docs:(qi + 1) * n_docs]
+            ws, wp = oracle.topk(row.astype(np.float64), 100)
+            assert np.array_equal(tpn[qi], wp)
+            assert np.array_equal(tsn[qi], ws.astype(np.float32))
     del tok_d
     torch.cuda.empty_cache()

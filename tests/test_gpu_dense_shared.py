@@ -71,39 +71,3 @@ def test_shared_refuses_unsupported(cuda_lib, dtype, nq):
     with pytest.raises(tms.TmsError) as e:
         _run_shared(Q, tok, off, ln, np.array([0, 1, 2], np.int32))
     assert e.value.status == tms.TMS_ERR_UNSUPPORTED
-
-
-@pytest.mark.slow
-@pytest.mark.parametrize("d", [64, 768])
-def test_config3_shared_full_size_sampled(cuda_lib, d):
-    """200,000 documents, bf16, 32 queries over all documents in the shared
-    schedule: sampled parity and the exact top-100 of the GPU's own scores."""
-    import torch
-    from paper_2606_26439_gb300 import tms
-    n_docs, nq, n_queries = 200_000, 32, 32
-    lengths = synth.lengths_uniform(n_docs, 32, 180, 2)
-    tok_d, off_d, ln_d = synth.device_dense_corpus(lengths, d, "bf16", 2)
-    Q = synth.queries(n_queries, nq, d, "bf16", 2)
-    q_d = Q.cuda()
-    cand_d = torch.arange(n_docs, dtype=torch.int32, device="cuda")
-    out = tms.score_dense_shared(q_d, tok_d, off_d, ln_d, cand_d)
-    co = torch.arange(0, (n_queries + 1) * n_docs, n_docs, dtype=torch.int64, device="cuda")
-    ts, tp = tms.topk(out.view(-1), co, 100)
-    torch.cuda.synchronize()
-    assert tms.device_error() == 0
-    scores = out.cpu().numpy()
-    g = np.random.default_rng(7)
-    off = synth.offsets_of(lengths)
-    qa, qdt = oracle_view(Q)
-    for qi in g.choice(n_queries, 4, replace=False):
-        ids = np.sort(g.choice(n_docs, 96, replace=False)).astype(np.int32)
-        rows = np.concatenate([np.arange(off[i], off[i] + lengths[i]) for i in ids])
-        sub = tok_d[torch.from_numpy(rows).cuda()].cpu()
-        ta, tdt = oracle_view(sub)
-        want = oracle.dense_scores(qa[qi], ta, synth.offsets_of(lengths[ids]), lengths[ids],
-                                   np.arange(len(ids), dtype=np.int32), qdtype=qdt, tdtype=tdt)
-        assert_scores_close(scores[qi, ids], want, "bf16", nq)
-        ws, wp = oracle.topk(scores[qi].astype(np.float64), 100)
-        assert np.array_equal(tp.cpu().numpy()[qi], wp)
-    del tok_d
-    torch.cuda.empty_cache()

@@ -16,7 +16,7 @@ import pytest
 import oracle
 import synth
 from tests import gpu_cases as gc
-from tests._common import assert_scores_close, oracle_view
+from tests._common import assert_topk_matches_oracle, assert_scores_close, oracle_view
 
 pytestmark = pytest.mark.gpu
 
@@ -229,5 +229,16 @@ def test_fp8_full_size_sampled(cuda_lib, shared):
         want[sel] = oracle.dense_scores_scaled(qc[qi], qs[qi], sub_c, sub_s, sub_off, sub_len, sel.astype(np.int32),
                                                qdtype=oracle.E4M3, tdtype=oracle.E4M3)
     assert_scores_close(scores[pos], want, "e4m3", nq)
+    # query 0: its whole list of 100,000 scores and its top-10 against the
+    # oracle's own scores (tolerance ties merged)
+    sub_c, sub_off, sub_len = gc.gather_docs(tc_d, off, lengths, cands[0])
+    sub_s, _, _ = gc.gather_docs(ts_d, off, lengths, cands[0])
+    want0 = oracle.dense_scores_scaled(qc[0], qs[0], sub_c.numpy(), sub_s.numpy(), sub_off, sub_len,
+                                       np.arange(n_cand, dtype=np.int32), qdtype=oracle.E4M3, tdtype=oracle.E4M3)
+    assert_scores_close(scores[:n_cand], want0, "e4m3", nq)
+    co_d = torch.tensor([0, n_cand], dtype=torch.int64, device="cuda")
+    _, tp = tms.topk(out[:n_cand], co_d, 10)
+    torch.cuda.synchronize()
+    assert_topk_matches_oracle(tp.cpu().numpy()[0], want0, 10, "e4m3", nq)
     del tc_d
     torch.cuda.empty_cache()

@@ -19,7 +19,7 @@ import pytest
 import oracle
 import synth
 from tests import gpu_cases as gc
-from tests._common import assert_scores_close, oracle_view
+from tests._common import assert_scores_close, assert_topk_matches_oracle, oracle_view
 
 pytestmark = pytest.mark.gpu
 
@@ -151,45 +151,57 @@ def test_pq_bitwise_repeatable(cuda_lib, f16):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("f16", [False, True])
-def test_config4_pq_full_size_sampled(cuda_lib, f16):
+def test_config4_pq_full_size_all_forms(cuda_lib):
     """1,000,000 documents, Nd ~ U[32, 180], M = 16, K = 256, dsub = 8,
     Gaussian centroids + N(0, 0.05) noise, nearest-centroid codes; 64 fp16
-    queries each over all documents.  Sampled parity vs decompress-then-dot."""
+    queries each over all documents -- the benchmark's launches of the fused
+    PQ kernel with the fp32 table and the fp16 table, and of the tensor-core
+    PQ kernel (codes decompressed in shared memory).  For each: 512 sampled
+    scores across the 64 queries, and query 0's all 1,000,000 scores and
+    top-10 / top-100 against FP64 decompress-then-dot (tolerance ties merged)."""
     import torch
     from paper_2606_26439_gb300 import tms
     n_docs, M, K, dsub, nq, n_queries = 1_000_000, 16, 256, 8, 32, 64
     d = M * dsub
     lengths = synth.lengths_uniform(n_docs, 32, 180, 4)
+    off = synth.offsets_of(lengths)
     cb_d, codes_d, off_d, ln_d = synth.device_pq_corpus(lengths, M, K, dsub, 4)
     Q = synth.queries(n_queries, nq, d, "f16", 4)
     q_d = gc.to_dev(Q)[0]
     lut_d = tms.build_pq_lut(q_d, cb_d)
-    cands = [np.arange(n_docs, dtype=np.int32)] * n_queries
-    flat, co = gc.csr(cands)
+    ids = np.arange(n_docs, dtype=np.int32)
+    flat, co = gc.csr([ids] * n_queries)
     f_d, co_d = gc.to_dev(flat, co)
-    out = tms.score_pq(lut_d, codes_d, off_d, ln_d, f_d, co_d, f16_table=f16)
+    forms = {
+        "fp32 table": tms.score_pq(lut_d, codes_d, off_d, ln_d, f_d, co_d),
+        "fp16 table": tms.score_pq(lut_d, codes_d, off_d, ln_d, f_d, co_d, f16_table=True),
+        "tensor cores": tms.score_pq_tc_shared(q_d, cb_d, codes_d, off_d, ln_d, f_d[:n_docs]).view(-1),
+    }
+    tops = {name: [tms.topk(x, co_d[:2], k) for k in (10, 100)] for name, x in forms.items()}
     torch.cuda.synchronize()
     assert tms.device_error() == 0
-    scores = out.cpu().numpy()
-    assert np.isfinite(scores).all()
+    cb = cb_d.cpu().numpy()
+    codes = codes_d.cpu().numpy()
+    qa, qdt = oracle_view(Q)
+    want0 = oracle.pq_decompress_scores(qa[0], cb, codes, off, lengths, ids, qdtype=qdt)
     g = np.random.default_rng(5)
     pos = np.sort(g.choice(len(flat), 512, replace=False))
     qidx = pos // n_docs
-    ids = flat[pos]
-    off = synth.offsets_of(lengths)
-    rows = np.concatenate([np.arange(off[i], off[i] + lengths[i]) for i in ids])
-    sub_codes = codes_d[torch.from_numpy(rows).cuda()].cpu().numpy()
-    sub_len = lengths[ids]
-    sub_off = synth.offsets_of(sub_len)
-    cb = cb_d.cpu().numpy()
-    qa, qdt = oracle_view(Q)
+    di = flat[pos]
+    sub_len = lengths[di]
+    sub_codes = codes[gc.rows_of(off, lengths, di)]
     want = np.empty(len(pos))
     for qi in np.unique(qidx):
         sel = np.nonzero(qidx == qi)[0]
-        want[sel] = oracle.pq_decompress_scores(qa[qi], cb, sub_codes, sub_off, sub_len, sel.astype(np.int32),
-                                                qdtype=qdt)
-    assert_scores_close(scores[pos], want, "f16", nq)
+        want[sel] = oracle.pq_decompress_scores(qa[qi], cb, sub_codes, synth.offsets_of(sub_len), sub_len,
+                                                sel.astype(np.int32), qdtype=qdt)
+    for name, out in forms.items():
+        scores = out.cpu().numpy()
+        assert np.isfinite(scores).all(), name
+        assert_scores_close(scores[pos], want, "f16", nq)
+        assert_scores_close(scores[:n_docs], want0, "f16", nq)
+        for k, (ts, tp) in zip((10, 100), tops[name]):
+            assert_topk_matches_oracle(tp.cpu().numpy()[0], want0, k, "f16", nq)
 
 
 def _ragged_pq_case(M, K, nq, seed, n_queries=2):

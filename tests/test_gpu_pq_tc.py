@@ -121,39 +121,3 @@ def test_pq_tc_rejects_unsupported(cuda_lib):
     with pytest.raises(tms.TmsError) as e:   # bf16 queries
         tms.score_pq_tc_shared(q.to(torch.bfloat16), cb16, codes16, off, ln, f)
     assert e.value.status == tms.TMS_ERR_UNSUPPORTED
-
-
-@pytest.mark.slow
-def test_config4_pq_tc_full_size_sampled(cuda_lib):
-    """1,000,000 documents, Nd ~ U[32, 180], M = 16, K = 256, dsub = 8,
-    Gaussian centroids + N(0, 0.05) noise; 64 fp16 queries over all
-    documents.  Sampled parity vs FP64 decompress-then-dot at 1e-3."""
-    import torch
-    from paper_2606_26439_gb300 import tms
-    n_docs, K, nq, n_queries = 1_000_000, 256, 32, 64
-    lengths = synth.lengths_uniform(n_docs, 32, 180, 4)
-    cb_d, codes_d, off_d, ln_d = synth.device_pq_corpus(lengths, M, K, DSUB, 4)
-    Q = synth.queries(n_queries, nq, D, "f16", 4)
-    q_d = gc.to_dev(Q)[0]
-    ids = torch.arange(n_docs, dtype=torch.int32, device="cuda")
-    out = tms.score_pq_tc_shared(q_d, cb_d, codes_d, off_d, ln_d, ids)
-    torch.cuda.synchronize()
-    assert tms.device_error() == 0
-    scores = out.cpu().numpy()
-    assert np.isfinite(scores).all()
-    g = np.random.default_rng(6)
-    qi = g.integers(0, n_queries, 512)
-    di = g.integers(0, n_docs, 512)
-    off = synth.offsets_of(lengths)
-    rows = np.concatenate([np.arange(off[i], off[i] + lengths[i]) for i in di])
-    sub_codes = codes_d[torch.from_numpy(rows).cuda()].cpu().numpy()
-    sub_len = lengths[di]
-    sub_off = synth.offsets_of(sub_len)
-    cb = cb_d.cpu().numpy()
-    qa, qdt = oracle_view(Q)
-    want = np.empty(512)
-    for q in np.unique(qi):
-        sel = np.nonzero(qi == q)[0]
-        want[sel] = oracle.pq_decompress_scores(qa[q], cb, sub_codes, sub_off, sub_len, sel.astype(np.int32),
-                                                qdtype=qdt)
-    assert_scores_close(scores[qi, di], want, "f16", nq)
