@@ -300,6 +300,32 @@ tms_status tms_topk(const float *scores, const int64_t *cand_offsets, int n_quer
                     float *out_scores, int32_t *out_pos, cudaStream_t stream);
 
 /*
+ * tms_topk on the whole GPU: each query's list is cut into S contiguous
+ * slices, one CTA selects each slice's top-k into `workspace`, and one CTA
+ * per query selects the final top-k from its S x topk entries.  The result
+ * is bit-identical to tms_topk (same order, same ties, same padding); only
+ * the work is spread over S times more CTAs, which matters when there are
+ * few queries with long lists (e.g. 16 lists of 100,000 scores).
+ *
+ *   n_cand         cand_offsets[n_queries] (HOST value): fixes S with
+ *                  n_queries, topk and the device's SM count.
+ *   workspace      DEVICE scratch of workspace_bytes bytes, 16-byte
+ *                  aligned, owned by the caller; its contents on entry do
+ *                  not matter and are overwritten.  Calls that may run at
+ *                  the same time need separate workspaces.
+ *
+ * tms_topk_workspace_size gives the bytes needed on the current device
+ * (n_queries * S * topk * 8; 0 when S = 1, then workspace may be NULL and
+ * the call is tms_topk).  A smaller workspace returns TMS_ERR_INVALID_ARG
+ * before anything is enqueued.  Other arguments and limits as tms_topk.
+ */
+tms_status tms_topk_workspace_size(int n_queries, int topk, int64_t n_cand, int64_t *bytes);
+
+tms_status tms_topk_split(const float *scores, const int64_t *cand_offsets, int n_queries, int topk,
+                          int64_t n_cand, float *out_scores, int32_t *out_pos, void *workspace,
+                          int64_t workspace_bytes, cudaStream_t stream);
+
+/*
  * Serving loop: a device-resident corpus (a dense store and optionally a PQ
  * store and an FP8 copy of the dense store) and a worker thread that scores
  * requests -- one query of nq tokens

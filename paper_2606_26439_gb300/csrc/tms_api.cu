@@ -91,21 +91,6 @@ tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const voi
     return r == CUDA_SUCCESS ? TMS_OK : TMS_ERR_INVALID_ARG;
 }
 
-tms_status encode_tmap_1d_f32(CUtensorMap* map, const void* base, uint64_t n, uint32_t box_elems) {
-    if (!load_encoder()) return TMS_ERR_CUDA;
-    // Described as one row of n elements (a rank-2 map with a unit outer
-    // dimension); its row pitch is n * 4 rounded up to 16 bytes.
-    const uint64_t nn = n > 0 ? n : 1;
-    const cuuint64_t dims[2] = {nn, 1};
-    const cuuint64_t strides[1] = {(nn * 4 + 15) & ~uint64_t(15)};
-    const cuuint32_t box[2] = {box_elems, 1};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? TMS_OK : TMS_ERR_INVALID_ARG;
-}
-
 }  // namespace tms
 
 extern "C" {

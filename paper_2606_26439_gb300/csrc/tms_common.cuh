@@ -113,6 +113,21 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// 4-byte asynchronous copy global -> shared (non-bulk cp.async: any 4-byte
+// aligned addresses), tracked per thread.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Arrive on `bar` once every cp.async this thread issued so far has
+// completed; the arrival counts against the barrier's expected count.
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Wait until every cp.async this thread issued has completed.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -215,6 +230,39 @@ __device__ __forceinline__ float fold_max32(float m, const float (&v)[32]) {
     const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
     const float b3 = fmax3(a[9], a[10], m);
     return fmax3(fmaxf(b0, b1), b2, b3);
+}
+
+// max(m, v[lo..hi)) (0 <= lo < hi <= 32): the columns outside [lo, hi)
+// are dropped (-inf) before the three-input fold.
+__device__ __forceinline__ float fold_max32_range(float m, const float (&v)[32], int lo, int hi) {
+    float w[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) w[c] = (c >= lo && c < hi) ? v[c] : -INFINITY;
+    return fold_max32(m, w);
+}
+
+// (a, b) *= (x, y) in one packed instruction; each product is rounded as a
+// single fp32 multiply (round to nearest even).
+__device__ __forceinline__ void mul_f32x2(float& a, float& b, float x, float y) {
+    asm("{\n\t.reg .b64 p, q;\n\t"
+        "mov.b64 p, {%0, %1};\n\t"
+        "mov.b64 q, {%2, %3};\n\t"
+        "mul.rn.f32x2 p, p, q;\n\t"
+        "mov.b64 {%0, %1}, p;\n\t}"
+        : "+f"(a), "+f"(b)
+        : "f"(x), "f"(y));
+}
+
+// v[c] *= s[c] for 32 columns, two at a time; `s` 16-byte aligned in shared
+// memory, read as eight broadcast 128-bit loads.
+__device__ __forceinline__ void scale32(float (&v)[32], const float* s) {
+    const float4* s4 = reinterpret_cast<const float4*>(s);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 k = s4[i];
+        mul_f32x2(v[4 * i], v[4 * i + 1], k.x, k.y);
+        mul_f32x2(v[4 * i + 2], v[4 * i + 3], k.z, k.w);
+    }
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {

@@ -87,10 +87,10 @@ constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8
 // Super-tile records in flight: 8 with 256-row super-tiles (one CTA per
 // SM), 4 with 128-row ones (two CTAs per SM share the shared memory).
 __host__ __device__ constexpr int st_ring(int str) { return str == 256 ? 8 : 4; }
-constexpr int kScaleRing = 32;                // F8: tiles whose row scales are in flight or held
-constexpr int kScaleBox = 136;                // floats per scale load: 128 rows + up to 3 of 16-byte alignment
-constexpr int kScalePitch = 160;              // floats per scale slot (640 B, a multiple of 128 B)
 constexpr int kEpiWarps = 4;
+// Tiles per super-tile when the epilogue splits the columns among the
+// query-tile copies (their per-tile partial maxima meet in shared memory).
+constexpr int kMaxTilesSplit = 8;
 constexpr int kLoaderWarp = 2 + kEpiWarps;
 constexpr int kThreads = 32 * (kLoaderWarp + 1);  // planner, MMA, four epilogue warps, loader
 constexpr int kSplitWarps = 4;                    // TF: splitter warps after the loader; kPQ: decompressors
@@ -164,7 +164,8 @@ struct Args {
 constexpr int kFaultHoldAccumulator = TMS_FAULT_HOLD_ACCUMULATOR;
 
 struct Layout {
-    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, cb_off, code_off, st_off, bar_off, misc_off, total;
+    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, pm_off, cb_off, code_off, st_off, bar_off, misc_off,
+        total;
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
@@ -174,7 +175,10 @@ struct Layout {
 // accumulator rows that nothing reads.  A stage holds the full super-tile
 // of str rows, so the document operand (N <= str) never reads past it.
 // TF: the query region and every stage have a lo twin right after them.
-__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind) {
+// F8: per super-tile record slot, the row scale of every column.  csplit
+// (the column-split epilogue): two buffers of per-tile partial maxima.
+__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind,
+                                              bool csplit) {
     const bool f8 = kind == kE4M3;
     const int twin = kind == kTF32 ? 2 : 1;
     Layout L;
@@ -184,12 +188,13 @@ __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunk
     L.stage_stride = twin * str * 128;
     L.part_off = L.stage_off + stages * L.stage_stride;
     L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
-    L.cb_off = L.sc_off + (f8 ? kScaleRing * kScalePitch * 4 : 0);
+    L.pm_off = L.sc_off + (f8 ? st_ring(str) * str * 4 : 0);                        // F8: [st_ring][str] scales
+    L.cb_off = L.pm_off + (csplit ? 2 * kMaxTilesSplit * kEpiWarps * 32 * 4 : 0);  // [2][tiles][warps][32]
     L.code_off = L.cb_off + (kind == kPQ ? kPqCbBytes : 0);                        // kPQ: fp16 codebook
     // kPQ: code-row ring, then per slot the valid rows of each 8-row group
     L.st_off = L.code_off + (kind == kPQ ? kCodeRing * (str * kPqM + kMaxSeg * 4) : 0);
     L.bar_off = L.st_off + st_ring(str) * static_cast<int>(sizeof(StSlot));
-    const int nbar = 3 * stages + 2 * kAcc + 3 * qslots + 2 * st_ring(str) + 8 + 2 * kScaleRing + 1 + 2 * kCodeRing;
+    const int nbar = 3 * stages + 2 * kAcc + 3 * qslots + 3 * st_ring(str) + 8 + 2 + 1 + 2 * kCodeRing;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
@@ -269,12 +274,10 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 // Tensor maps of one launch.  doc[h] covers document rows with a box of
 // 8 (h + 1) rows x one 128-byte chunk, so a tile of r rows is always ONE
-// box per chunk (at most 7 rows of over-fetch).  scales (F8): the
-// [n_tokens] fp32 row scales, boxes of kScaleBox.
+// box per chunk (at most 7 rows of over-fetch).
 struct Maps {
     CUtensorMap q;
     CUtensorMap doc[kBoxKinds];
-    CUtensorMap scales;
 };
 
 // H: 128-row halves of the query tile (2 for a shared group of 8 queries).
@@ -304,14 +307,17 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     const int QS = a.qslots;
     const int NCH = a.nchunks;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND);
+    // the epilogue splits each super-tile's columns among the query-tile copies
+    const bool csplit = H == 1 && a.reps > 1;
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND, csplit);
     const int SSTRIDE = L.stage_stride;  // bytes between stages (TF: hi, then lo)
 
     uint8_t* q_base = smem + L.q_off;
     uint8_t* qlo_base = smem + L.qlo_off;  // TF: the lo twin of the query region
     uint8_t* stage_base = smem + L.stage_off;
     float* part = reinterpret_cast<float*>(smem + L.part_off);  // [copy][parity][block]
-    float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // [kScaleRing][kScalePitch]
+    float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // F8: [kStRing][STR] scale of each column
+    float* pm = reinterpret_cast<float*>(smem + L.pm_off);      // csplit: [2][kMaxTilesSplit][kEpiWarps][32]
     StSlot* slots = reinterpret_cast<StSlot*>(smem + L.st_off);
     uint8_t* cb = smem + L.cb_off;           // kPQ: fp16 codebook, entry (code, m) at (code * 16 + m) * 16
     uint8_t* code_ring = smem + L.code_off;  // kPQ: [kCodeRing][STR rows][16] code bytes
@@ -327,9 +333,9 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     uint64_t* xempty = xfull + kStRing;     // [kStRing]
     uint64_t* pfull = xempty + kStRing;     // [copy][parity]
     uint64_t* pempty = pfull + 4;           // [copy][parity]
-    uint64_t* sfull = pempty + 4;           // [kScaleRing]
-    uint64_t* sempty = sfull + kScaleRing;  // [kScaleRing]
-    uint64_t* mdone = sempty + kScaleRing;
+    uint64_t* scfull = pempty + 4;          // F8: [kStRing] a record slot's column scales landed
+    uint64_t* ebar = scfull + kStRing;      // csplit: [2] every epilogue warp's partials written
+    uint64_t* mdone = ebar + 2;
     uint64_t* conv = mdone + 1;   // TF: [S] stage split
     uint64_t* qconv = conv + S;   // TF: [QS] query tile split
     uint64_t* codefull = qconv + QS;            // kPQ: [kCodeRing] code rows landed
@@ -361,10 +367,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             mbar_init(&pfull[i], a.bpc);
             mbar_init(&pempty[i], 1);
         }
-        for (int i = 0; i < kScaleRing; ++i) {
-            mbar_init(&sfull[i], 1);
-            mbar_init(&sempty[i], kEpiWarps);
-        }
+        for (int i = 0; i < kStRing; ++i) mbar_init(&scfull[i], 32);  // one cp.async arrival per loader lane
+        for (int i = 0; i < 2; ++i) mbar_init(&ebar[i], kEpiWarps);
         mbar_init(mdone, 1);
         for (int i = 0; i < S; ++i) mbar_init(&conv[i], kSplitWarps);
         for (int i = 0; i < QS; ++i) mbar_init(&qconv[i], kSplitWarps);
@@ -378,10 +382,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     if (warp == kLoaderWarp) {
         if (lane < kBoxKinds) prefetch_tensormap(&maps.doc[lane]);
     }
-    if (warp == 0) {
-        if (lane == 0) prefetch_tensormap(&maps.q);
-        if (F8 && lane == 1) prefetch_tensormap(&maps.scales);
-    }
+    if (warp == 0 && lane == 0) prefetch_tensormap(&maps.q);
     if (warp == 1) {
         tmem_alloc(tmem_slot, TCOLS);
         tmem_relinquish();
@@ -412,35 +413,23 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
 
     if (warp == 0) {
         // ------------------------------------------------------- planner
-        const uint64_t pol_stream = policy_evict_first();
         const uint64_t pol_keep = policy_evict_last();
-        int tseg = 0;  // tiles published
         int tst = 0;   // super-tiles published
+        // tiles per super-tile: one per planner lane, and no more than the
+        // partials buffer holds when the epilogue splits the columns
+        const int max_tiles = csplit ? kMaxTilesSplit : STR / 8;
         int qi = 0, cur_q = -1;
         bool aborted = false;
         // The open super-tile: its tile i lives in lane i's registers.
         int nseg = 0, rows_used = 0, st_q = 0;
         int my_f = 0, my_r = 0, my_flags = 0, my_row0 = 0, my_col = 0;
 
-        // Publish the open super-tile: F8 row-scale loads, the record, and
-        // the query tile if the query changed.
+        // Publish the open super-tile: the record, and the query tile if the
+        // query changed.
         auto close_st = [&]() -> bool {
             const bool has = lane < nseg;
             const int xs = tst % kStRing;
             if (!warp_wait(&xempty[xs], ((tst / kStRing) & 1) ^ 1, abort_flag, a.err, a.budget)) return false;
-            if (F8) {
-                // Every epilogue warp passes every tile's scale slot in
-                // order, so the slot of the last tile being free means all
-                // of this super-tile's slots are.
-                const int u = tseg + nseg - 1;
-                if (!warp_wait(&sempty[u % kScaleRing], ((u / kScaleRing) & 1) ^ 1, abort_flag, a.err, a.budget)) return false;
-                if (has) {
-                    // the tile's row scales, from the 16-byte boundary at or below its first row
-                    const int ss = (tseg + lane) % kScaleRing;
-                    mbar_arrive_expect_tx(&sfull[ss], static_cast<uint32_t>(kScaleBox * 4));
-                    tma_load_2d(sc + ss * kScalePitch, &maps.scales, my_row0 & ~3, 0, &sfull[ss], pol_stream);
-                }
-            }
             StSlot* x = &slots[xs];
             if (has) {
                 SegInfo si;
@@ -464,7 +453,6 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             __syncwarp();
             if (lane == 0) mbar_arrive(&xfull[xs]);
             ++tst;
-            tseg += nseg;
             // A new query's rows go to the next query slot.  The record is
             // published first: the MMA thread releases the old slot only
             // once it sees the new query.
@@ -559,7 +547,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 for (int r0 = 0; r0 < len; r0 += kRows) {
                     const int r = min(kRows, len - r0);
                     const int n8 = (r + 7) & ~7;
-                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == STR / 8)) {
+                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == max_tiles)) {
                         if (!close_st()) {
                             aborted = true;
                             break;
@@ -600,11 +588,6 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         }
         // Let every copy this warp issued land before the CTA can exit.
         if (lane == 0) {
-            if (F8) {
-                const int ns = tseg < kScaleRing ? tseg : kScaleRing;
-                for (int i = 1; i <= ns; ++i)
-                    drain_wait(&sfull[(tseg - i) % kScaleRing], ((tseg - i) / kScaleRing) & 1);
-            }
             // every query slot whose load may still be in flight (QS of them)
             const int nqs = qi < QS ? qi : QS;
             for (int i = 1; i <= nqs; ++i) drain_wait(&qfull[(qi - i) % QS], ((qi - i) / QS) & 1);
@@ -659,21 +642,39 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         int s = 0;
         uint32_t ph = 0;
         int64_t issued = 0;
+        int sc_sts = 0;  // F8: super-tiles whose column scales were issued
         for (int t = 0;; ++t) {
             const int xs = t % kStRing;
             if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr h = slots[xs].h;
             if (h.flags & kEnd) break;
             const bool has = lane < h.nseg;
-            int n8 = 8, row0 = 0, col = 0;
+            int n8 = 8, row0 = 0, col = 0, rr = 0;
             if (has) {
                 const SegInfo si = slots[xs].seg[lane];
+                rr = si.r;
                 n8 = (si.r + 7) & ~7;
                 row0 = si.row0;
                 col = si.col;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&xempty[xs]);
+            if (F8) {
+                // Each tile's row scales to its columns of the record slot's
+                // scale array (4-byte copies: any row alignment; 32
+                // consecutive rows per warp step), completing on scfull[xs].
+                // The array is free: the slot was republished only after
+                // every epilogue warp had finished with its previous use.
+                float* dst = sc + xs * STR;
+                for (int i = 0; i < h.nseg; ++i) {
+                    const int ri = __shfl_sync(0xffffffffu, rr, i);
+                    const int rowi = __shfl_sync(0xffffffffu, row0, i);
+                    const int coli = __shfl_sync(0xffffffffu, col, i);
+                    for (int j = lane; j < ri; j += 32) cp_async4(dst + coli + j, a.t_scales + rowi + j);
+                }
+                cp_async_mbar_arrive(&scfull[xs]);
+                ++sc_sts;
+            }
             const CUtensorMap* dmap = &maps.doc[(n8 >> 3) - 1];
             bool ok = true;
             for (int kc = 0; kc < NCH; ++kc) {
@@ -693,6 +694,14 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             if (!ok) break;
         }
         // Let every copy still in flight land before the CTA can exit.
+        if (F8) {
+            cp_async_wait_all();
+            __syncwarp();
+            if (lane == 0) {
+                const int n = sc_sts < kStRing ? sc_sts : kStRing;
+                for (int i = 1; i <= n; ++i) drain_wait(&scfull[(sc_sts - i) % kStRing], ((sc_sts - i) / kStRing) & 1);
+            }
+        }
         if (lane == 0) {
             const int64_t n = issued < S ? issued : S;
             int ss = s;
@@ -910,16 +919,28 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         // ----------------------------------------------------- epilogue
         // Thread = query row 128 h + 32 qd + lane of half h (TMEM lane
         // 32 qd + lane).  Row block 4 h + qd is copy (4 h + qd) / bpc of
-        // block (4 h + qd) % bpc; the copy of this warp takes the documents
-        // whose ordinal is that copy mod reps, and rmax[h] is the running
-        // max of the row over the current document's columns.
+        // block (4 h + qd) % bpc.  The documents are dealt round-robin to
+        // the copies (ordinal mod reps): the warps of the owning copy finish
+        // a document -- sum its query tokens' maxima (times their scales,
+        // F8) and store the score.  rmax[h] is the owner's running max of
+        // its row over the current document's columns.
+        //
+        // With one copy (reps = 1) every warp reads all of its documents'
+        // columns.  With several copies (csplit) the columns of each
+        // super-tile are split among the copies instead -- each copy's
+        // warps read an equal share of 32-column groups from their own copy
+        // of the accumulator and leave, per tile, the max over their share
+        // in shared memory (pm); after one barrier the owners fold the
+        // partials of their documents' tiles.  The work per warp is then the
+        // same whatever the document lengths, and the accumulator goes back
+        // to the MMA as soon as it is read.
         const int qd = warp & 3;
         const int copy = qd / a.bpc;
+        const int blk = qd - copy * a.bpc;
         const bool active = copy < a.reps;
         float rmax[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-        int tseg = 0;          // tiles seen (all copies)
         uint32_t ord = 0;      // documents seen (all copies)
         uint32_t mydocs = 0;   // documents of this copy finished
         bool mine = false;
@@ -929,6 +950,67 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         int qsc_q = -1;
 #pragma unroll
         for (int h = 0; h < H; ++h) qsc[h] = 1.f;
+
+        // A document's first tile: its owner copy, and a fresh running max.
+        auto first_tile = [&](const StHdr& xh) {
+            mine = active && (ord & static_cast<uint32_t>(a.reps - 1)) == static_cast<uint32_t>(copy);
+            ++ord;
+#pragma unroll
+            for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
+            if (F8 && mine && xh.q != qsc_q) {
+                qsc_q = xh.q;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const int b = (4 * h + qd) % a.bpc;
+                    const int qq = SH ? xh.q * a.group + b : xh.q;
+                    const int tok = SH ? lane : b * 32 + lane;
+                    qsc[h] = (tok < a.nq && qq < a.n_queries) ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
+                                                              : 0.f;
+                }
+            }
+        };
+        // A document's last tile: its score(s).  False on abort.
+        auto finish = [&](const SegInfo& si, const StHdr& xh) -> bool {
+            if (SH) {
+                const int64_t fc = si.f;  // shared mode: position in the candidate list
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const int b = (4 * h + qd) % a.bpc;
+                    const int qq = xh.q * a.group + b;
+                    const float sum = warp_sum(lane < a.nq ? (F8 ? rmax[h] * qsc[h] : rmax[h]) : 0.f);
+                    if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
+                }
+            } else {
+                const int tok = blk * 32 + lane;
+                float v = 0.f;
+                if (tok < a.nq) v = F8 ? rmax[0] * qsc[0] : rmax[0];
+                const float sum = warp_sum(v);
+                if (a.bpc == 1) {
+                    if (lane == 0) a.out[si.f] = sum;
+                } else {
+                    // the copy's warps add their block sums in block order
+                    const int pb = copy * 2 + (mydocs & 1);
+                    const uint32_t use = mydocs >> 1;
+                    if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err, a.budget)) return false;
+                    if (lane == 0) {
+                        part[pb * 4 + blk] = sum;
+                        mbar_arrive(&pfull[pb]);
+                    }
+                    if (blk == 0) {
+                        if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err, a.budget)) return false;
+                        if (lane == 0) {
+                            float tot = part[pb * 4];
+                            for (int bb = 1; bb < a.bpc; ++bb) tot += part[pb * 4 + bb];
+                            a.out[si.f] = tot;
+                            mbar_arrive(&pempty[pb]);
+                        }
+                    }
+                }
+            }
+            ++mydocs;
+            return true;
+        };
+
         for (int t = 0; !aborted; ++t) {
             const int xs = t % kStRing;
             if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
@@ -937,118 +1019,120 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             const int ab = t % kAcc;
             if (!warp_wait(&tfull[ab], (t / kAcc) & 1, abort_flag, a.err, a.budget)) break;
             tc_fence_after();
-            for (int i = 0; i < xh.nseg; ++i, ++tseg) {
-                const SegInfo si = slots[xs].seg[i];
-                if (si.flags & kFirst) {
-                    mine = active && (ord & static_cast<uint32_t>(a.reps - 1)) == static_cast<uint32_t>(copy);
-                    ++ord;
-#pragma unroll
-                    for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-                    if (F8 && mine && xh.q != qsc_q) {
-                        qsc_q = xh.q;
-#pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            const int b = (4 * h + qd) % a.bpc;
-                            const int qq = SH ? xh.q * a.group + b : xh.q;
-                            const int tok = SH ? lane : b * 32 + lane;
-                            qsc[h] = (tok < a.nq && qq < a.n_queries)
-                                         ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
-                                         : 0.f;
+            const float* scol = sc + xs * STR;              // F8: scale of each column's document row
+            const uint32_t sc_par = (t / kStRing) & 1;
+            if (csplit) {
+                // ---- phase 1: this copy's share of the 32-column groups
+                const int par = t & 1;
+                const int G = (xh.rows + 31) >> 5;
+                const int gl = copy * G / a.reps, gh = (copy + 1) * G / a.reps;
+                if (active && gl < gh) {
+                    if (F8 && !warp_wait_all(&scfull[xs], sc_par, abort_flag, a.err, a.budget)) break;
+                    float* pmw = pm + (par * kMaxTilesSplit * kEpiWarps + qd) * 32 + lane;
+                    const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(ab * STR);
+                    int ti = 0;
+                    SegInfo cur = slots[xs].seg[0];
+                    while (ti + 1 < xh.nseg && cur.col + cur.r <= 32 * gl) cur = slots[xs].seg[++ti];
+                    float pacc = -INFINITY;
+                    int pt = -1;  // tile whose partial pacc holds
+                    for (int g = gl; g < gh; ++g) {
+                        const int c0 = 32 * g;
+                        float v[32];
+                        tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
+                        if (F8) scale32(v, scol + c0);
+                        // every tile with columns in [c0, c0 + 32)
+                        for (;;) {
+                            const int lo = max(cur.col - c0, 0), hi = min(cur.col + cur.r - c0, 32);
+                            if (lo < hi) {
+                                const float m = (lo == 0 && hi == 32) ? fold_max32(-INFINITY, v)
+                                                                      : fold_max32_range(-INFINITY, v, lo, hi);
+                                if (ti != pt) {
+                                    if (pt >= 0) pmw[pt * kEpiWarps * 32] = pacc;
+                                    pt = ti;
+                                    pacc = m;
+                                } else {
+                                    pacc = fmaxf(pacc, m);
+                                }
+                            }
+                            if (cur.col + cur.r > c0 + 32 || ti + 1 >= xh.nseg) break;
+                            cur = slots[xs].seg[++ti];
+                            if (cur.col >= c0 + 32) break;
                         }
                     }
+                    if (pt >= 0) pmw[pt * kEpiWarps * 32] = pacc;
                 }
-                const int ss = tseg % kScaleRing;
-                if (!mine) {
-                    if (F8 && lane == 0) mbar_arrive(&sempty[ss]);
-                    continue;
+                // the accumulator is read: back to the MMA; the partials are
+                // written: one arrival per warp on this parity's barrier
+                tc_fence_before();
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&tempty[ab]);
+                    mbar_arrive(&ebar[par]);
                 }
-                const float* scl = nullptr;  // scl[c]: scale of column c's document row
-                if (F8) {
-                    if (!warp_wait_all(&sfull[ss], (tseg / kScaleRing) & 1, abort_flag, a.err, a.budget)) {
+                if (!warp_wait(&ebar[par], (t >> 1) & 1, abort_flag, a.err, a.budget)) break;
+                // ---- phase 2: owners fold the partials of their documents' tiles
+                if (active) {
+                    for (int i = 0; i < xh.nseg; ++i) {
+                        const SegInfo si = slots[xs].seg[i];
+                        if (si.flags & kFirst) first_tile(xh);
+                        if (!mine) continue;
+                        const int glo = si.col >> 5, ghi = (si.col + si.r - 1) >> 5;
+                        const float* pmr = pm + ((par * kMaxTilesSplit + i) * kEpiWarps + blk) * 32 + lane;
+                        for (int c2 = 0; c2 < a.reps; ++c2) {
+                            const int l2 = c2 * G / a.reps, h2 = (c2 + 1) * G / a.reps;
+                            if (l2 < h2 && l2 <= ghi && h2 > glo) rmax[0] = fmaxf(rmax[0], pmr[c2 * a.bpc * 32]);
+                        }
+                        if ((si.flags & kLast) && !finish(si, xh)) {
+                            aborted = true;
+                            break;
+                        }
+                    }
+                    if (aborted) break;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xempty[xs]);
+            } else {
+                bool sc_ready = false;
+                for (int i = 0; i < xh.nseg; ++i) {
+                    const SegInfo si = slots[xs].seg[i];
+                    if (si.flags & kFirst) first_tile(xh);
+                    if (!mine) continue;
+                    if (F8 && !sc_ready) {
+                        if (!warp_wait_all(&scfull[xs], sc_par, abort_flag, a.err, a.budget)) {
+                            aborted = true;
+                            break;
+                        }
+                        sc_ready = true;
+                    }
+                    const int c_lo = si.col;
+                    const int c_hi = si.col + si.r;
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
+                                              static_cast<uint32_t>((ab * H + h) * STR);
+                        for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
+                            float v[32];
+                            tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
+                            if (F8) scale32(v, scol + c0);
+                            if (c0 < c_lo || c0 + 32 > c_hi)
+                                rmax[h] = fold_max32_range(rmax[h], v, max(c_lo - c0, 0), min(c_hi - c0, 32));
+                            else
+                                rmax[h] = fold_max32(rmax[h], v);
+                        }
+                    }
+                    if ((si.flags & kLast) && !finish(si, xh)) {
                         aborted = true;
                         break;
                     }
-                    scl = sc + ss * kScalePitch + (si.row0 & 3) - si.col;
                 }
-                const int c_lo = si.col;
-                const int c_hi = si.col + si.r;
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
-                                          static_cast<uint32_t>((ab * H + h) * STR);
-                    for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
-                        if (c0 < c_lo || c0 + 32 > c_hi) {
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) {
-                                const bool in = c0 + c >= c_lo && c0 + c < c_hi;
-                                v[c] = in ? (F8 ? v[c] * scl[c0 + c] : v[c]) : -INFINITY;
-                            }
-                        } else if (F8) {
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) v[c] *= scl[c0 + c];
-                        }
-                        rmax[h] = fold_max32(rmax[h], v);
-                    }
+                if (aborted) break;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&tempty[ab]);
+                    mbar_arrive(&xempty[xs]);
                 }
-                if (F8) {
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sempty[ss]);
-                }
-                if (si.flags & kLast) {
-                    if (SH) {
-                        const int64_t fc = si.f;  // shared mode: position in the candidate list
-#pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            const int b = (4 * h + qd) % a.bpc;
-                            const int qq = xh.q * a.group + b;
-                            const float sum = warp_sum(lane < a.nq ? (F8 ? rmax[h] * qsc[h] : rmax[h]) : 0.f);
-                            if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
-                        }
-                    } else {
-                        const int b = qd % a.bpc;
-                        const int tok = b * 32 + lane;
-                        float v = 0.f;
-                        if (tok < a.nq) v = F8 ? rmax[0] * qsc[0] : rmax[0];
-                        const float sum = warp_sum(v);
-                        if (a.bpc == 1) {
-                            if (lane == 0) a.out[si.f] = sum;
-                        } else {
-                            // the copy's warps add their block sums in block order
-                            const int pb = copy * 2 + (mydocs & 1);
-                            const uint32_t use = mydocs >> 1;
-                            if (!warp_wait(&pempty[pb], (use & 1) ^ 1, abort_flag, a.err, a.budget)) {
-                                aborted = true;
-                                break;
-                            }
-                            if (lane == 0) {
-                                part[pb * 4 + b] = sum;
-                                mbar_arrive(&pfull[pb]);
-                            }
-                            if (b == 0) {
-                                if (!warp_wait(&pfull[pb], use & 1, abort_flag, a.err, a.budget)) {
-                                    aborted = true;
-                                    break;
-                                }
-                                if (lane == 0) {
-                                    float tot = part[pb * 4];
-                                    for (int bb = 1; bb < a.bpc; ++bb) tot += part[pb * 4 + bb];
-                                    a.out[si.f] = tot;
-                                    mbar_arrive(&pempty[pb]);
-                                }
-                            }
-                        }
-                    }
-                    ++mydocs;
-                }
-            }
-            if (aborted) break;
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&tempty[ab]);
-                mbar_arrive(&xempty[xs]);
             }
         }
     }
@@ -1147,7 +1231,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
                                     : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
         int best = -1;
         for (int qs = 2; qs >= 1; --qs) {
-            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND);
+            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, H == 1 && rp > 1);
             const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
             if (sts > best) {
                 best = sts;
@@ -1207,18 +1291,11 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         st = encode_tmap_2d(&maps.doc[h], tdt, dbase, d, n_tokens, row_bytes, CE, static_cast<uint32_t>(8 * (h + 1)));
         if (st != TMS_OK) return st;
     }
-    if (F8) {
-        st = encode_tmap_1d_f32(&maps.scales, n_tokens > 0 ? static_cast<const void*>(a.t_scales) : queries,
-                                static_cast<uint64_t>(n_tokens), kScaleBox);
-        if (st != TMS_OK) return st;
-    } else {
-        maps.scales = maps.q;  // never used
-    }
     // format code 0 is f16 under kind::f16 and E4M3 under kind::f8f6f4; 2 is TF32
     a.idesc = make_idesc(128, 0, TF ? 2u : ((!F8 && dtype == TMS_BF16) ? 1u : 0u));
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND);
+    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND, H == 1 && reps > 1);
     const int smem = L.total + 1024;
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {

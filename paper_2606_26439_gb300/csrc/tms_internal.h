@@ -29,9 +29,6 @@ tms_status current_device(DeviceInfo* out);
 tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
                           uint64_t rows, uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows);
 
-// Encode a tensor map over `n` consecutive fp32 elements (one row), box of
-// box_elems x 1, no swizzle, zero fill outside; load with tma_load_2d(x, 0).
-tms_status encode_tmap_1d_f32(CUtensorMap* map, const void* base, uint64_t n, uint32_t box_elems);
 
 // Diagnostics set by tms_debug_set, read when a launch is prepared: the
 // bound of every pipeline wait in SM cycles (0 = the kernels' default) and

@@ -34,8 +34,8 @@ TMS_FAULT_HOLD_ACCUMULATOR = 1
 #: every symbol include/tms.h declares
 EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
            "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
-           "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait",
-           "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_status_string",
+           "tms_score_pq_tc_shared", "tms_topk", "tms_topk_workspace_size", "tms_topk_split", "tms_server_create",
+           "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_status_string",
            "tms_version", "tms_peak_shared_load", "tms_peak_hbm_read")
 
 TMS_STORE_DENSE, TMS_STORE_PQ, TMS_STORE_FP8 = 0, 1, 2
@@ -99,6 +99,8 @@ def lib(build_if_missing: bool = True):
             L.tms_score_pq_tc_shared.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _i64, _p, _p, _i64,
                                                  _p, _i64, _p, _p]
             L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
+            L.tms_topk_workspace_size.argtypes = [_i32, _i32, _i64, ctypes.POINTER(ctypes.c_int64)]
+            L.tms_topk_split.argtypes = [_p, _p, _i32, _i32, _i64, _p, _p, _p, _i64, _p]
             L.tms_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
             L.tms_server_submit.argtypes = [_p, _i32, _p, _p, _i64, ctypes.POINTER(ctypes.c_uint64)]
             L.tms_server_wait.argtypes = [_p, ctypes.c_uint64, ctypes.c_double, _p, _p,
@@ -114,7 +116,8 @@ def lib(build_if_missing: bool = True):
             L.tms_version.argtypes = []
             for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
                          "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
-                         "tms_score_pq_tc_shared", "tms_topk", "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
+                         "tms_score_pq_tc_shared", "tms_topk", "tms_topk_workspace_size", "tms_topk_split",
+                         "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
                          "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_version",
                          "tms_peak_shared_load", "tms_peak_hbm_read"):
                 getattr(L, name).restype = ctypes.c_int
@@ -402,6 +405,35 @@ def topk(scores, cand_offsets, k, out_scores=None, out_pos=None, stream=None):
     _check("tms_topk", tms_topk(_dev(scores, torch.float32), _dev(cand_offsets, torch.int64), nQ, k,
                                 _dev(out_scores, torch.float32), _dev(out_pos, torch.int32),
                                 _stream_ptr(stream)))
+    return out_scores, out_pos
+
+
+def topk_workspace_size(n_queries, k, n_cand) -> int:
+    """Bytes of device workspace tms_topk_split needs on the current device."""
+    b = ctypes.c_int64()
+    _check("tms_topk_workspace_size", lib().tms_topk_workspace_size(int(n_queries), int(k), int(n_cand),
+                                                                    ctypes.byref(b)))
+    return b.value
+
+
+def topk_split(scores, cand_offsets, k, n_cand=None, out_scores=None, out_pos=None, workspace=None, stream=None):
+    """tms_topk over slices of every list (same result as topk).  ``n_cand``:
+    the host value of cand_offsets[-1] (default: the length of ``scores``);
+    ``workspace``: a device tensor of at least topk_workspace_size bytes
+    (allocated here when None)."""
+    torch = _torch()
+    nQ = cand_offsets.shape[0] - 1
+    n_cand = scores.numel() if n_cand is None else int(n_cand)
+    if out_scores is None:
+        out_scores = torch.empty((nQ, k), dtype=torch.float32, device=scores.device)
+    if out_pos is None:
+        out_pos = torch.empty((nQ, k), dtype=torch.int32, device=scores.device)
+    if workspace is None:
+        workspace = torch.empty(max(16, topk_workspace_size(nQ, k, n_cand)), dtype=torch.uint8, device=scores.device)
+    nbytes = workspace.numel() * workspace.element_size()
+    _check("tms_topk_split", lib().tms_topk_split(_dev(scores, torch.float32), _dev(cand_offsets, torch.int64), nQ, k,
+                                                  n_cand, _dev(out_scores, torch.float32), _dev(out_pos, torch.int32),
+                                                  _dev(workspace), nbytes, _stream_ptr(stream)))
     return out_scores, out_pos
 
 
