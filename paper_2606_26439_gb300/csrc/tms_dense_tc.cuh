@@ -88,9 +88,6 @@ constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8
 // SM), 4 with 128-row ones (two CTAs per SM share the shared memory).
 __host__ __device__ constexpr int st_ring(int str) { return str == 256 ? 8 : 4; }
 constexpr int kEpiWarps = 4;
-// Tiles per super-tile when the epilogue splits the columns among the
-// query-tile copies (their per-tile partial maxima meet in shared memory).
-constexpr int kMaxTilesSplit = 8;
 constexpr int kLoaderWarp = 2 + kEpiWarps;
 constexpr int kThreads = 32 * (kLoaderWarp + 1);  // planner, MMA, four epilogue warps, loader
 constexpr int kSplitWarps = 4;                    // TF: splitter warps after the loader; kPQ: decompressors
@@ -119,7 +116,8 @@ struct StHdr {
     int nseg;   // tiles
     int flags;  // kEnd
     int rows;   // packed rows (sum of the tiles' rows rounded up to 8)
-    int pad[3];
+    int copy;   // the query-tile copy whose epilogue warps score it
+    int pad[2];
 };
 
 struct StSlot {
@@ -164,8 +162,7 @@ struct Args {
 constexpr int kFaultHoldAccumulator = TMS_FAULT_HOLD_ACCUMULATOR;
 
 struct Layout {
-    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, pm_off, cb_off, code_off, st_off, bar_off, misc_off,
-        total;
+    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, cb_off, code_off, st_off, bar_off, misc_off, total;
 };
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
@@ -175,10 +172,8 @@ struct Layout {
 // accumulator rows that nothing reads.  A stage holds the full super-tile
 // of str rows, so the document operand (N <= str) never reads past it.
 // TF: the query region and every stage have a lo twin right after them.
-// F8: per super-tile record slot, the row scale of every column.  csplit
-// (the column-split epilogue): two buffers of per-tile partial maxima.
-__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind,
-                                              bool csplit) {
+// F8: per super-tile record slot, the row scale of every column.
+__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind) {
     const bool f8 = kind == kE4M3;
     const int twin = kind == kTF32 ? 2 : 1;
     Layout L;
@@ -188,13 +183,12 @@ __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunk
     L.stage_stride = twin * str * 128;
     L.part_off = L.stage_off + stages * L.stage_stride;
     L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
-    L.pm_off = L.sc_off + (f8 ? st_ring(str) * str * 4 : 0);                        // F8: [st_ring][str] scales
-    L.cb_off = L.pm_off + (csplit ? 2 * kMaxTilesSplit * kEpiWarps * 32 * 4 : 0);  // [2][tiles][warps][32]
+    L.cb_off = L.sc_off + (f8 ? st_ring(str) * str * 4 : 0);  // F8: [st_ring][str] column scales
     L.code_off = L.cb_off + (kind == kPQ ? kPqCbBytes : 0);                        // kPQ: fp16 codebook
     // kPQ: code-row ring, then per slot the valid rows of each 8-row group
     L.st_off = L.code_off + (kind == kPQ ? kCodeRing * (str * kPqM + kMaxSeg * 4) : 0);
     L.bar_off = L.st_off + st_ring(str) * static_cast<int>(sizeof(StSlot));
-    const int nbar = 3 * stages + 2 * kAcc + 3 * qslots + 3 * st_ring(str) + 8 + 2 + 1 + 2 * kCodeRing;
+    const int nbar = 3 * stages + kAcc * (kEpiWarps + 1) + 3 * qslots + 3 * st_ring(str) + 8 + 1 + 2 * kCodeRing;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
@@ -307,9 +301,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     const int QS = a.qslots;
     const int NCH = a.nchunks;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    // the epilogue splits each super-tile's columns among the query-tile copies
-    const bool csplit = H == 1 && a.reps > 1;
-    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND, csplit);
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND);
     const int SSTRIDE = L.stage_stride;  // bytes between stages (TF: hi, then lo)
 
     uint8_t* q_base = smem + L.q_off;
@@ -317,7 +309,6 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     uint8_t* stage_base = smem + L.stage_off;
     float* part = reinterpret_cast<float*>(smem + L.part_off);  // [copy][parity][block]
     float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // F8: [kStRing][STR] scale of each column
-    float* pm = reinterpret_cast<float*>(smem + L.pm_off);      // csplit: [2][kMaxTilesSplit][kEpiWarps][32]
     StSlot* slots = reinterpret_cast<StSlot*>(smem + L.st_off);
     uint8_t* cb = smem + L.cb_off;           // kPQ: fp16 codebook, entry (code, m) at (code * 16 + m) * 16
     uint8_t* code_ring = smem + L.code_off;  // kPQ: [kCodeRing][STR rows][16] code bytes
@@ -325,8 +316,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;
     uint64_t* empty = full + S;
-    uint64_t* tfull = empty + S;
-    uint64_t* tempty = tfull + kAcc;
+    uint64_t* tfull = empty + S;              // [kAcc][kEpiWarps]: accumulator ready, per (accumulator, copy)
+    uint64_t* tempty = tfull + kAcc * kEpiWarps;
     uint64_t* qfull = tempty + kAcc;
     uint64_t* qempty = qfull + QS;
     uint64_t* xfull = qempty + QS;          // [kStRing]
@@ -334,8 +325,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     uint64_t* pfull = xempty + kStRing;     // [copy][parity]
     uint64_t* pempty = pfull + 4;           // [copy][parity]
     uint64_t* scfull = pempty + 4;          // F8: [kStRing] a record slot's column scales landed
-    uint64_t* ebar = scfull + kStRing;      // csplit: [2] every epilogue warp's partials written
-    uint64_t* mdone = ebar + 2;
+    uint64_t* mdone = scfull + kStRing;
     uint64_t* conv = mdone + 1;   // TF: [S] stage split
     uint64_t* qconv = conv + S;   // TF: [QS] query tile split
     uint64_t* codefull = qconv + QS;            // kPQ: [kCodeRing] code rows landed
@@ -351,10 +341,9 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             mbar_init(&full[i], PQ ? kSplitWarps : 1);  // kPQ: every decompressor warp wrote its rows
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < kAcc; ++i) {
-            mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], kEpiWarps);
-        }
+        for (int i = 0; i < kAcc * kEpiWarps; ++i) mbar_init(&tfull[i], 1);
+        // released by the warps of the copy that scored the super-tile
+        for (int i = 0; i < kAcc; ++i) mbar_init(&tempty[i], a.bpc < kEpiWarps ? a.bpc : kEpiWarps);
         for (int i = 0; i < QS; ++i) {
             mbar_init(&qfull[i], 1);
             mbar_init(&qempty[i], 1);
@@ -368,7 +357,6 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             mbar_init(&pempty[i], 1);
         }
         for (int i = 0; i < kStRing; ++i) mbar_init(&scfull[i], 32);  // one cp.async arrival per loader lane
-        for (int i = 0; i < 2; ++i) mbar_init(&ebar[i], kEpiWarps);
         mbar_init(mdone, 1);
         for (int i = 0; i < S; ++i) mbar_init(&conv[i], kSplitWarps);
         for (int i = 0; i < QS; ++i) mbar_init(&qconv[i], kSplitWarps);
@@ -415,9 +403,10 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         // ------------------------------------------------------- planner
         const uint64_t pol_keep = policy_evict_last();
         int tst = 0;   // super-tiles published
-        // tiles per super-tile: one per planner lane, and no more than the
-        // partials buffer holds when the epilogue splits the columns
-        const int max_tiles = csplit ? kMaxTilesSplit : STR / 8;
+        // Super-tiles are dealt to the query-tile copies in runs: a run is a
+        // maximal sequence of super-tiles joined by documents that continue
+        // from one into the next, so each document is scored by one copy.
+        int st_copy = 0;
         int qi = 0, cur_q = -1;
         bool aborted = false;
         // The open super-tile: its tile i lives in lane i's registers.
@@ -447,12 +436,16 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 h.nseg = nseg;
                 h.flags = 0;
                 h.rows = rows_used;
-                h.pad[0] = h.pad[1] = h.pad[2] = 0;
+                h.copy = st_copy;
+                h.pad[0] = h.pad[1] = 0;
                 x->h = h;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&xfull[xs]);
             ++tst;
+            // the next super-tile starts a new run unless this one ends inside a document
+            const int last_flags = __shfl_sync(0xffffffffu, my_flags, nseg - 1);
+            if (last_flags & kLast) st_copy = st_copy + 1 == a.reps ? 0 : st_copy + 1;
             // A new query's rows go to the next query slot.  The record is
             // published first: the MMA thread releases the old slot only
             // once it sees the new query.
@@ -544,10 +537,19 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 const int off = static_cast<int>(__shfl_sync(0xffffffffu, cur.off, i));
                 const int q = __shfl_sync(0xffffffffu, ql, i);
                 const int fi = static_cast<int>(__shfl_sync(0xffffffffu, SH ? pos : f, i));
+                // With several copies, a document that fits an empty
+                // super-tile is not split across two: the run ends here.
+                const int doc8 = (len / kRows) * kRows + (((len % kRows) + 7) & ~7);
+                if (a.reps > 1 && nseg > 0 && doc8 <= STR && rows_used + doc8 > STR) {
+                    if (!close_st()) {
+                        aborted = true;
+                        break;
+                    }
+                }
                 for (int r0 = 0; r0 < len; r0 += kRows) {
                     const int r = min(kRows, len - r0);
                     const int n8 = (r + 7) & ~7;
-                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == max_tiles)) {
+                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == STR / 8)) {
                         if (!close_st()) {
                             aborted = true;
                             break;
@@ -581,7 +583,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 h.nseg = 0;
                 h.flags = kEnd;
                 h.rows = 0;
-                h.pad[0] = h.pad[1] = h.pad[2] = 0;
+                h.copy = 0;
+                h.pad[0] = h.pad[1] = 0;
                 slots[xs].h = h;
                 mbar_arrive(&xfull[xs]);
             }
@@ -906,7 +909,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                     }
                 }
                 if (!ok) break;
-                if (a.fault != kFaultHoldAccumulator || blockIdx.x != 0 || t != 0) mma_commit(&tfull[ab]);
+                if (a.fault != kFaultHoldAccumulator || blockIdx.x != 0 || t != 0)
+                    mma_commit(&tfull[ab * kEpiWarps + x.copy]);
             }
             // Every MMA this thread issued must finish before TMEM is freed.
             if (any) {
@@ -919,21 +923,16 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         // ----------------------------------------------------- epilogue
         // Thread = query row 128 h + 32 qd + lane of half h (TMEM lane
         // 32 qd + lane).  Row block 4 h + qd is copy (4 h + qd) / bpc of
-        // block (4 h + qd) % bpc.  The documents are dealt round-robin to
-        // the copies (ordinal mod reps): the warps of the owning copy finish
-        // a document -- sum its query tokens' maxima (times their scales,
-        // F8) and store the score.  rmax[h] is the owner's running max of
-        // its row over the current document's columns.
-        //
-        // With one copy (reps = 1) every warp reads all of its documents'
-        // columns.  With several copies (csplit) the columns of each
-        // super-tile are split among the copies instead -- each copy's
-        // warps read an equal share of 32-column groups from their own copy
-        // of the accumulator and leave, per tile, the max over their share
-        // in shared memory (pm); after one barrier the owners fold the
-        // partials of their documents' tiles.  The work per warp is then the
-        // same whatever the document lengths, and the accumulator goes back
-        // to the MMA as soon as it is read.
+        // block (4 h + qd) % bpc.  Each super-tile is scored by the warps of
+        // one copy (the record's `copy`; the planner deals runs of
+        // super-tiles to the copies in turn, so a document never changes
+        // copy): they read every column of it from their own copy of the
+        // accumulator, keep rmax[h], the running max of their row over the
+        // current document, and at a document's last tile sum its query
+        // tokens' maxima (times their scales, F8) and store the score.  The
+        // warps of the other copies only pass the record on.  Each warp thus
+        // spends nothing on the super-tiles it does not score, and the
+        // super-tiles in flight are scored by different warps at once.
         const int qd = warp & 3;
         const int copy = qd / a.bpc;
         const int blk = qd - copy * a.bpc;
@@ -941,9 +940,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         float rmax[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-        uint32_t ord = 0;      // documents seen (all copies)
-        uint32_t mydocs = 0;   // documents of this copy finished
-        bool mine = false;
+        uint32_t mydocs = 0;      // documents this warp finished
+        uint32_t nacc[kAcc] = {};  // super-tiles of this copy scored in each accumulator
         bool aborted = false;
         // F8: this thread's query-token scale(s), reloaded when the query changes
         float qsc[H];
@@ -951,24 +949,6 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
 #pragma unroll
         for (int h = 0; h < H; ++h) qsc[h] = 1.f;
 
-        // A document's first tile: its owner copy, and a fresh running max.
-        auto first_tile = [&](const StHdr& xh) {
-            mine = active && (ord & static_cast<uint32_t>(a.reps - 1)) == static_cast<uint32_t>(copy);
-            ++ord;
-#pragma unroll
-            for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-            if (F8 && mine && xh.q != qsc_q) {
-                qsc_q = xh.q;
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const int b = (4 * h + qd) % a.bpc;
-                    const int qq = SH ? xh.q * a.group + b : xh.q;
-                    const int tok = SH ? lane : b * 32 + lane;
-                    qsc[h] = (tok < a.nq && qq < a.n_queries) ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
-                                                              : 0.f;
-                }
-            }
-        };
         // A document's last tile: its score(s).  False on abort.
         auto finish = [&](const SegInfo& si, const StHdr& xh) -> bool {
             if (SH) {
@@ -1016,123 +996,63 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr xh = slots[xs].h;
             if (xh.flags & kEnd) break;
+            if (!active || xh.copy != copy) {  // another copy scores it
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xempty[xs]);
+                continue;
+            }
             const int ab = t % kAcc;
-            if (!warp_wait(&tfull[ab], (t / kAcc) & 1, abort_flag, a.err, a.budget)) break;
+            // accumulator ab for this copy: its phases are this copy's super-tiles in ab, in order
+            if (!warp_wait(&tfull[ab * kEpiWarps + copy], nacc[ab] & 1, abort_flag, a.err, a.budget)) break;
+            ++nacc[ab];
             tc_fence_after();
-            const float* scol = sc + xs * STR;              // F8: scale of each column's document row
-            const uint32_t sc_par = (t / kStRing) & 1;
-            if (csplit) {
-                // ---- phase 1: this copy's share of the 32-column groups
-                const int par = t & 1;
-                const int G = (xh.rows + 31) >> 5;
-                const int gl = copy * G / a.reps, gh = (copy + 1) * G / a.reps;
-                if (active && gl < gh) {
-                    if (F8 && !warp_wait_all(&scfull[xs], sc_par, abort_flag, a.err, a.budget)) break;
-                    float* pmw = pm + (par * kMaxTilesSplit * kEpiWarps + qd) * 32 + lane;
-                    const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(ab * STR);
-                    int ti = 0;
-                    SegInfo cur = slots[xs].seg[0];
-                    while (ti + 1 < xh.nseg && cur.col + cur.r <= 32 * gl) cur = slots[xs].seg[++ti];
-                    float pacc = -INFINITY;
-                    int pt = -1;  // tile whose partial pacc holds
-                    for (int g = gl; g < gh; ++g) {
-                        const int c0 = 32 * g;
+            if (F8 && !warp_wait_all(&scfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
+            const float* scol = sc + xs * STR;  // F8: scale of each column's document row
+            for (int i = 0; i < xh.nseg; ++i) {
+                const SegInfo si = slots[xs].seg[i];
+                if (si.flags & kFirst) {
+#pragma unroll
+                    for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
+                    if (F8 && xh.q != qsc_q) {
+                        qsc_q = xh.q;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const int b = (4 * h + qd) % a.bpc;
+                            const int qq = SH ? xh.q * a.group + b : xh.q;
+                            const int tok = SH ? lane : b * 32 + lane;
+                            qsc[h] = (tok < a.nq && qq < a.n_queries)
+                                         ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
+                                         : 0.f;
+                        }
+                    }
+                }
+                const int c_lo = si.col;
+                const int c_hi = si.col + si.r;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
+                                          static_cast<uint32_t>((ab * H + h) * STR);
+                    for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
                         float v[32];
                         tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
                         if (F8) scale32(v, scol + c0);
-                        // every tile with columns in [c0, c0 + 32)
-                        for (;;) {
-                            const int lo = max(cur.col - c0, 0), hi = min(cur.col + cur.r - c0, 32);
-                            if (lo < hi) {
-                                const float m = (lo == 0 && hi == 32) ? fold_max32(-INFINITY, v)
-                                                                      : fold_max32_range(-INFINITY, v, lo, hi);
-                                if (ti != pt) {
-                                    if (pt >= 0) pmw[pt * kEpiWarps * 32] = pacc;
-                                    pt = ti;
-                                    pacc = m;
-                                } else {
-                                    pacc = fmaxf(pacc, m);
-                                }
-                            }
-                            if (cur.col + cur.r > c0 + 32 || ti + 1 >= xh.nseg) break;
-                            cur = slots[xs].seg[++ti];
-                            if (cur.col >= c0 + 32) break;
-                        }
-                    }
-                    if (pt >= 0) pmw[pt * kEpiWarps * 32] = pacc;
-                }
-                // the accumulator is read: back to the MMA; the partials are
-                // written: one arrival per warp on this parity's barrier
-                tc_fence_before();
-                __threadfence_block();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&tempty[ab]);
-                    mbar_arrive(&ebar[par]);
-                }
-                if (!warp_wait(&ebar[par], (t >> 1) & 1, abort_flag, a.err, a.budget)) break;
-                // ---- phase 2: owners fold the partials of their documents' tiles
-                if (active) {
-                    for (int i = 0; i < xh.nseg; ++i) {
-                        const SegInfo si = slots[xs].seg[i];
-                        if (si.flags & kFirst) first_tile(xh);
-                        if (!mine) continue;
-                        const int glo = si.col >> 5, ghi = (si.col + si.r - 1) >> 5;
-                        const float* pmr = pm + ((par * kMaxTilesSplit + i) * kEpiWarps + blk) * 32 + lane;
-                        for (int c2 = 0; c2 < a.reps; ++c2) {
-                            const int l2 = c2 * G / a.reps, h2 = (c2 + 1) * G / a.reps;
-                            if (l2 < h2 && l2 <= ghi && h2 > glo) rmax[0] = fmaxf(rmax[0], pmr[c2 * a.bpc * 32]);
-                        }
-                        if ((si.flags & kLast) && !finish(si, xh)) {
-                            aborted = true;
-                            break;
-                        }
-                    }
-                    if (aborted) break;
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&xempty[xs]);
-            } else {
-                bool sc_ready = false;
-                for (int i = 0; i < xh.nseg; ++i) {
-                    const SegInfo si = slots[xs].seg[i];
-                    if (si.flags & kFirst) first_tile(xh);
-                    if (!mine) continue;
-                    if (F8 && !sc_ready) {
-                        if (!warp_wait_all(&scfull[xs], sc_par, abort_flag, a.err, a.budget)) {
-                            aborted = true;
-                            break;
-                        }
-                        sc_ready = true;
-                    }
-                    const int c_lo = si.col;
-                    const int c_hi = si.col + si.r;
-#pragma unroll
-                    for (int h = 0; h < H; ++h) {
-                        const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
-                                              static_cast<uint32_t>((ab * H + h) * STR);
-                        for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
-                            float v[32];
-                            tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
-                            if (F8) scale32(v, scol + c0);
-                            if (c0 < c_lo || c0 + 32 > c_hi)
-                                rmax[h] = fold_max32_range(rmax[h], v, max(c_lo - c0, 0), min(c_hi - c0, 32));
-                            else
-                                rmax[h] = fold_max32(rmax[h], v);
-                        }
-                    }
-                    if ((si.flags & kLast) && !finish(si, xh)) {
-                        aborted = true;
-                        break;
+                        if (c0 < c_lo || c0 + 32 > c_hi)
+                            rmax[h] = fold_max32_range(rmax[h], v, max(c_lo - c0, 0), min(c_hi - c0, 32));
+                        else
+                            rmax[h] = fold_max32(rmax[h], v);
                     }
                 }
-                if (aborted) break;
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&tempty[ab]);
-                    mbar_arrive(&xempty[xs]);
+                if ((si.flags & kLast) && !finish(si, xh)) {
+                    aborted = true;
+                    break;
                 }
+            }
+            if (aborted) break;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&tempty[ab]);
+                mbar_arrive(&xempty[xs]);
             }
         }
     }
@@ -1231,7 +1151,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
                                     : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
         int best = -1;
         for (int qs = 2; qs >= 1; --qs) {
-            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, H == 1 && rp > 1);
+            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND);
             const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
             if (sts > best) {
                 best = sts;
@@ -1295,7 +1215,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.idesc = make_idesc(128, 0, TF ? 2u : ((!F8 && dtype == TMS_BF16) ? 1u : 0u));
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND, H == 1 && reps > 1);
+    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND);
     const int smem = L.total + 1024;
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {
