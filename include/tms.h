@@ -77,9 +77,9 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
  * Limits: 1 <= nq <= 128; 8 <= d <= 1024 with d % 8 == 0 (16-byte rows);
  * 1 <= n_queries <= 4096; n_tokens < 2^31; queries, doc_tokens and every
  * index array 16-byte aligned.  For fp16/bf16 the whole query tile stays
- * in one CTA's shared memory next to at least two 32 KB stages: with nq
+ * in one CTA's shared memory next to at least two 16 KB stages: with nq
  * rounded up to a multiple of 32 and d to a multiple of 64, nq * d * 2
- * bytes must not exceed 160,256 (nq > 96 at d > 576 and nq > 64 at d > 832
+ * bytes must not exceed 188,416 (nq > 96 at d > 704 and nq > 64 at d > 960
  * return TMS_ERR_UNSUPPORTED).  fp16/bf16 run on the tensor cores
  * (tcgen05, fp32 accumulation in tensor memory); fp32 runs split TF32 on
  * the tensor cores (x = hi + lo, hi = x rounded to TF32; hi.hi + hi.lo +

@@ -84,9 +84,11 @@ constexpr int kPqCbBytes = 256 * kPqM * 16;   // kPQ: fp16 codebook, all 256 cod
 constexpr int kCodeRing = 4;                  // kPQ: super-tiles whose code rows are in flight or held
 constexpr int kBoxKinds = kRows / 8;          // box heights 8, 16, ..., 128
 constexpr int kMaxSeg = 32;                   // tiles per super-tile (each >= 8 rows, one per planner lane)
-// Super-tile records in flight: 8 with 256-row super-tiles (one CTA per
-// SM), 4 with 128-row ones (two CTAs per SM share the shared memory).
-__host__ __device__ constexpr int st_ring(int str) { return str == 256 ? 8 : 4; }
+// Super-tile records in flight.  A record slot is republished only after
+// every role has passed it, so the ring also bounds how far the loader can
+// run ahead of the epilogue: with HBM latencies of a few microseconds under
+// load, the loads of many super-tiles must be in flight at once.
+__host__ __device__ constexpr int st_ring(int) { return 16; }
 constexpr int kEpiWarps = 4;
 constexpr int kLoaderWarp = 2 + kEpiWarps;
 constexpr int kThreads = 32 * (kLoaderWarp + 1);  // planner, MMA, four epilogue warps, loader
@@ -94,7 +96,13 @@ constexpr int kSplitWarps = 4;                    // TF: splitter warps after th
 __host__ __device__ constexpr int kernel_threads(int kind) {
     return kThreads + ((kind == kTF32 || kind == kPQ) ? 32 * kSplitWarps : 0);
 }
-constexpr int kAcc = 2;                       // accumulator buffers (each H x STR TMEM columns)
+// Accumulator buffers (each H x STR tensor-memory columns): as many as the
+// SM's 512 columns hold for the CTAs sharing it, at most one per epilogue
+// warp.
+__host__ __device__ constexpr int acc_count(int h, int str, int ctas) {
+    return 512 / (h * str * ctas) < kEpiWarps ? 512 / (h * str * ctas) : kEpiWarps;
+}
+constexpr int kMaxAcc = kEpiWarps;
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;            // 227 KB opt-in maximum per CTA
 
@@ -116,8 +124,7 @@ struct StHdr {
     int nseg;   // tiles
     int flags;  // kEnd
     int rows;   // packed rows (sum of the tiles' rows rounded up to 8)
-    int copy;   // the query-tile copy whose epilogue warps score it
-    int pad[2];
+    int pad[3];
 };
 
 struct StSlot {
@@ -173,7 +180,8 @@ struct Layout {
 // of str rows, so the document operand (N <= str) never reads past it.
 // TF: the query region and every stage have a lo twin right after them.
 // F8: per super-tile record slot, the row scale of every column.
-__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind) {
+__host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind,
+                                              int kacc) {
     const bool f8 = kind == kE4M3;
     const int twin = kind == kTF32 ? 2 : 1;
     Layout L;
@@ -188,7 +196,7 @@ __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunk
     // kPQ: code-row ring, then per slot the valid rows of each 8-row group
     L.st_off = L.code_off + (kind == kPQ ? kCodeRing * (str * kPqM + kMaxSeg * 4) : 0);
     L.bar_off = L.st_off + st_ring(str) * static_cast<int>(sizeof(StSlot));
-    const int nbar = 3 * stages + kAcc * (kEpiWarps + 1) + 3 * qslots + 3 * st_ring(str) + 8 + 1 + 2 * kCodeRing;
+    const int nbar = 3 * stages + 2 * kacc + 3 * qslots + 3 * st_ring(str) + 8 + 1 + 2 * kCodeRing;
     L.misc_off = L.bar_off + nbar * 8;
     L.total = L.misc_off + 16;
     return L;
@@ -266,6 +274,39 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
+// Maxima of the four 8-column sub-blocks of 32 accumulator columns.
+// Document tiles start on 8-column boundaries, so a tile covers whole
+// sub-blocks except, at a document's end, a last partial one.
+__device__ __forceinline__ void sub_maxima8(const float (&v)[32], float (&sb)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        sb[k] = fmax3(fmax3(v[8 * k], v[8 * k + 1], v[8 * k + 2]), fmax3(v[8 * k + 3], v[8 * k + 4], v[8 * k + 5]),
+                      fmaxf(v[8 * k + 6], v[8 * k + 7]));
+}
+
+// max(m, v[lo..hi)) for 0 <= lo < hi <= 32 with lo a multiple of 8: the
+// whole sub-blocks from their maxima sb, a partial last one (hi not a
+// multiple of 8) from its hi % 8 leading columns.
+__device__ __forceinline__ float fold_cols(float m, const float (&v)[32], const float (&sb)[4], int lo, int hi) {
+    const int kl = lo >> 3;
+    const int kf = hi >> 3;
+    float x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = (k >= kl && k < kf) ? sb[k] : -INFINITY;
+    m = fmax3(m, fmax3(x[0], x[1], x[2]), x[3]);
+    const int rem = hi & 7;
+    if (rem != 0) {  // sub-block kf < 4 holds rem columns of the tile
+        float y[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            const float c = kf == 0 ? v[j] : (kf == 1 ? v[8 + j] : (kf == 2 ? v[16 + j] : v[24 + j]));
+            y[j] = j < rem ? c : -INFINITY;
+        }
+        m = fmax3(m, fmax3(y[0], y[1], y[2]), fmax3(y[3], y[4], fmaxf(y[5], y[6])));
+    }
+    return m;
+}
+
 // Tensor maps of one launch.  doc[h] covers document rows with a box of
 // 8 (h + 1) rows x one 128-byte chunk, so a tile of r rows is always ONE
 // box per chunk (at most 7 rows of over-fetch).
@@ -275,8 +316,9 @@ struct Maps {
 };
 
 // H: 128-row halves of the query tile (2 for a shared group of 8 queries).
-// STR: rows per super-tile (MMA N at most): 256 with one CTA per SM, 128
-// with two (each CTA then holds kAcc x H x STR = 256 TMEM columns).
+// STR: rows per super-tile (MMA N at most), 256 or 128.  CTAS: CTAs per SM
+// (1 or 2); the CTA holds KACC = acc_count(H, STR, CTAS) accumulators of
+// H x STR tensor-memory columns.
 // SH (shared mode): the launch's queries all score one candidate list; a
 // "query" of the pipeline is then a group of up to 4 H queries stacked in
 // M, so each document tile is read once per group, and the epilogue
@@ -291,9 +333,10 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     constexpr bool PQ = KIND == kPQ;
     constexpr int CE = chunk_elems(KIND);
     constexpr int STAGE_BYTES = STR * 128;
-    constexpr uint32_t TCOLS = kAcc * H * STR;
+    constexpr int KACC = acc_count(H, STR, CTAS);
+    constexpr uint32_t TCOLS = KACC * H * STR;
     constexpr int kStRing = st_ring(STR);
-    static_assert(TCOLS * CTAS <= 512, "tensor memory of one SM");
+    static_assert(KACC >= 2 && TCOLS * CTAS <= 512, "tensor memory of one SM");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -301,7 +344,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     const int QS = a.qslots;
     const int NCH = a.nchunks;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND);
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND, KACC);
     const int SSTRIDE = L.stage_stride;  // bytes between stages (TF: hi, then lo)
 
     uint8_t* q_base = smem + L.q_off;
@@ -316,9 +359,9 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;
     uint64_t* empty = full + S;
-    uint64_t* tfull = empty + S;              // [kAcc][kEpiWarps]: accumulator ready, per (accumulator, copy)
-    uint64_t* tempty = tfull + kAcc * kEpiWarps;
-    uint64_t* qfull = tempty + kAcc;
+    uint64_t* tfull = empty + S;              // [KACC] accumulator ready
+    uint64_t* tempty = tfull + KACC;          // [KACC] accumulator read by every active epilogue warp
+    uint64_t* qfull = tempty + KACC;
     uint64_t* qempty = qfull + QS;
     uint64_t* xfull = qempty + QS;          // [kStRing]
     uint64_t* xempty = xfull + kStRing;     // [kStRing]
@@ -341,9 +384,11 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             mbar_init(&full[i], PQ ? kSplitWarps : 1);  // kPQ: every decompressor warp wrote its rows
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < kAcc * kEpiWarps; ++i) mbar_init(&tfull[i], 1);
-        // released by the warps of the copy that scored the super-tile
-        for (int i = 0; i < kAcc; ++i) mbar_init(&tempty[i], a.bpc < kEpiWarps ? a.bpc : kEpiWarps);
+        for (int i = 0; i < KACC; ++i) {
+            mbar_init(&tfull[i], 1);
+            // the active epilogue warps: those whose row block belongs to a copy
+            mbar_init(&tempty[i], a.reps * a.bpc < kEpiWarps ? a.reps * a.bpc : kEpiWarps);
+        }
         for (int i = 0; i < QS; ++i) {
             mbar_init(&qfull[i], 1);
             mbar_init(&qempty[i], 1);
@@ -403,10 +448,6 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         // ------------------------------------------------------- planner
         const uint64_t pol_keep = policy_evict_last();
         int tst = 0;   // super-tiles published
-        // Super-tiles are dealt to the query-tile copies in runs: a run is a
-        // maximal sequence of super-tiles joined by documents that continue
-        // from one into the next, so each document is scored by one copy.
-        int st_copy = 0;
         int qi = 0, cur_q = -1;
         bool aborted = false;
         // The open super-tile: its tile i lives in lane i's registers.
@@ -436,16 +477,12 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 h.nseg = nseg;
                 h.flags = 0;
                 h.rows = rows_used;
-                h.copy = st_copy;
-                h.pad[0] = h.pad[1] = 0;
+                h.pad[0] = h.pad[1] = h.pad[2] = 0;
                 x->h = h;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&xfull[xs]);
             ++tst;
-            // the next super-tile starts a new run unless this one ends inside a document
-            const int last_flags = __shfl_sync(0xffffffffu, my_flags, nseg - 1);
-            if (last_flags & kLast) st_copy = st_copy + 1 == a.reps ? 0 : st_copy + 1;
             // A new query's rows go to the next query slot.  The record is
             // published first: the MMA thread releases the old slot only
             // once it sees the new query.
@@ -537,34 +574,28 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 const int off = static_cast<int>(__shfl_sync(0xffffffffu, cur.off, i));
                 const int q = __shfl_sync(0xffffffffu, ql, i);
                 const int fi = static_cast<int>(__shfl_sync(0xffffffffu, SH ? pos : f, i));
-                // With several copies, a document that fits an empty
-                // super-tile is not split across two: the run ends here.
-                const int doc8 = (len / kRows) * kRows + (((len % kRows) + 7) & ~7);
-                if (a.reps > 1 && nseg > 0 && doc8 <= STR && rows_used + doc8 > STR) {
-                    if (!close_st()) {
-                        aborted = true;
-                        break;
-                    }
-                }
-                for (int r0 = 0; r0 < len; r0 += kRows) {
-                    const int r = min(kRows, len - r0);
-                    const int n8 = (r + 7) & ~7;
-                    if (nseg > 0 && (q != st_q || rows_used + n8 > STR || nseg == STR / 8)) {
+                // Tiles of at most kRows rows fill the open super-tile to its
+                // last 8-row group: a document that does not fit is cut at
+                // the super-tile's end and continues in the next one.
+                for (int r0 = 0; r0 < len;) {
+                    if (nseg > 0 && (q != st_q || rows_used == STR || nseg == STR / 8)) {
                         if (!close_st()) {
                             aborted = true;
                             break;
                         }
                     }
                     if (nseg == 0) st_q = q;
+                    const int r = min(min(kRows, len - r0), STR - rows_used);
                     if (lane == nseg) {
                         my_f = fi;
                         my_r = r;
-                        my_flags = (r0 == 0 ? kFirst : 0) | (r0 + kRows >= len ? kLast : 0);
+                        my_flags = (r0 == 0 ? kFirst : 0) | (r0 + r >= len ? kLast : 0);
                         my_row0 = off + r0;
                         my_col = rows_used;
                     }
-                    rows_used += n8;
+                    rows_used += (r + 7) & ~7;
                     ++nseg;
+                    r0 += r;
                 }
                 if (aborted) break;
             }
@@ -583,8 +614,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 h.nseg = 0;
                 h.flags = kEnd;
                 h.rows = 0;
-                h.copy = 0;
-                h.pad[0] = h.pad[1] = 0;
+                h.pad[0] = h.pad[1] = h.pad[2] = 0;
                 slots[xs].h = h;
                 mbar_arrive(&xfull[xs]);
             }
@@ -865,8 +895,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                     ++qi;
                     cur_q = x.q;
                 }
-                const int ab = t % kAcc;
-                if (!mbar_wait(&tempty[ab], ((t / kAcc) & 1) ^ 1, abort_flag, a.err, a.budget)) break;
+                const int ab = t % KACC;
+                if (!mbar_wait(&tempty[ab], ((t / KACC) & 1) ^ 1, abort_flag, a.err, a.budget)) break;
                 tc_fence_after();
                 bool ok = true;
                 const uint32_t d_tmem = tbase + static_cast<uint32_t>(ab * H * STR);
@@ -910,7 +940,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 }
                 if (!ok) break;
                 if (a.fault != kFaultHoldAccumulator || blockIdx.x != 0 || t != 0)
-                    mma_commit(&tfull[ab * kEpiWarps + x.copy]);
+                    mma_commit(&tfull[ab]);
             }
             // Every MMA this thread issued must finish before TMEM is freed.
             if (any) {
@@ -923,16 +953,13 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         // ----------------------------------------------------- epilogue
         // Thread = query row 128 h + 32 qd + lane of half h (TMEM lane
         // 32 qd + lane).  Row block 4 h + qd is copy (4 h + qd) / bpc of
-        // block (4 h + qd) % bpc.  Each super-tile is scored by the warps of
-        // one copy (the record's `copy`; the planner deals runs of
-        // super-tiles to the copies in turn, so a document never changes
-        // copy): they read every column of it from their own copy of the
-        // accumulator, keep rmax[h], the running max of their row over the
-        // current document, and at a document's last tile sum its query
-        // tokens' maxima (times their scales, F8) and store the score.  The
-        // warps of the other copies only pass the record on.  Each warp thus
-        // spends nothing on the super-tiles it does not score, and the
-        // super-tiles in flight are scored by different warps at once.
+        // block (4 h + qd) % bpc; the copies hold the same sums.  Documents
+        // are dealt round-robin to the copies (by their order in the
+        // records), so each warp owns whole documents: rmax[h] is the
+        // running max of its row over the current document's columns, kept
+        // in registers from one super-tile to the next when a document is
+        // cut at a super-tile's end.  Every active warp passes every
+        // super-tile and loads only the column groups of its documents.
         const int qd = warp & 3;
         const int copy = qd / a.bpc;
         const int blk = qd - copy * a.bpc;
@@ -940,8 +967,9 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         float rmax[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-        uint32_t mydocs = 0;      // documents this warp finished
-        uint32_t nacc[kAcc] = {};  // super-tiles of this copy scored in each accumulator
+        uint32_t ord = 0;     // documents begun (all copies)
+        uint32_t mydocs = 0;  // documents this warp finished
+        bool mine = false;
         bool aborted = false;
         // F8: this thread's query-token scale(s), reloaded when the query changes
         float qsc[H];
@@ -949,24 +977,23 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
 #pragma unroll
         for (int h = 0; h < H; ++h) qsc[h] = 1.f;
 
-        // A document's last tile: its score(s).  False on abort.
-        auto finish = [&](const SegInfo& si, const StHdr& xh) -> bool {
+        // A document's score(s) from its row maxima m.  False on abort.
+        auto finish = [&](int64_t f, int q, const float (&m)[H]) -> bool {
             if (SH) {
-                const int64_t fc = si.f;  // shared mode: position in the candidate list
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
                     const int b = (4 * h + qd) % a.bpc;
-                    const int qq = xh.q * a.group + b;
-                    const float sum = warp_sum(lane < a.nq ? (F8 ? rmax[h] * qsc[h] : rmax[h]) : 0.f);
-                    if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + fc] = sum;
+                    const int qq = q * a.group + b;
+                    const float sum = warp_sum(lane < a.nq ? (F8 ? m[h] * qsc[h] : m[h]) : 0.f);
+                    if (lane == 0 && qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + f] = sum;
                 }
             } else {
                 const int tok = blk * 32 + lane;
                 float v = 0.f;
-                if (tok < a.nq) v = F8 ? rmax[0] * qsc[0] : rmax[0];
+                if (tok < a.nq) v = F8 ? m[0] * qsc[0] : m[0];
                 const float sum = warp_sum(v);
                 if (a.bpc == 1) {
-                    if (lane == 0) a.out[si.f] = sum;
+                    if (lane == 0) a.out[f] = sum;
                 } else {
                     // the copy's warps add their block sums in block order
                     const int pb = copy * 2 + (mydocs & 1);
@@ -981,7 +1008,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                         if (lane == 0) {
                             float tot = part[pb * 4];
                             for (int bb = 1; bb < a.bpc; ++bb) tot += part[pb * 4 + bb];
-                            a.out[si.f] = tot;
+                            a.out[f] = tot;
                             mbar_arrive(&pempty[pb]);
                         }
                     }
@@ -990,59 +1017,84 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             ++mydocs;
             return true;
         };
+        // 32 accumulator columns of this warp's lanes; F8: each times its
+        // document row's scale (the scales are read from shared memory
+        // before the tensor-memory load so both latencies overlap).
+        auto load_group = [&](uint32_t taddr, const float* scales, float (&v)[32]) {
+            if constexpr (F8) {
+                float4 s4[8];
+                const float4* p4 = reinterpret_cast<const float4*>(scales);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) s4[i] = p4[i];
+                tmem_ld32(taddr, v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    mul_f32x2(v[4 * i], v[4 * i + 1], s4[i].x, s4[i].y);
+                    mul_f32x2(v[4 * i + 2], v[4 * i + 3], s4[i].z, s4[i].w);
+                }
+            } else {
+                tmem_ld32(taddr, v);
+            }
+        };
 
         for (int t = 0; !aborted; ++t) {
             const int xs = t % kStRing;
             if (!warp_wait(&xfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const StHdr xh = slots[xs].h;
             if (xh.flags & kEnd) break;
-            if (!active || xh.copy != copy) {  // another copy scores it
+            if (!active) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&xempty[xs]);
                 continue;
             }
-            const int ab = t % kAcc;
-            // accumulator ab for this copy: its phases are this copy's super-tiles in ab, in order
-            if (!warp_wait(&tfull[ab * kEpiWarps + copy], nacc[ab] & 1, abort_flag, a.err, a.budget)) break;
-            ++nacc[ab];
+            const int ab = t % KACC;
+            if (!warp_wait(&tfull[ab], (t / KACC) & 1, abort_flag, a.err, a.budget)) break;
             tc_fence_after();
+            if (F8 && xh.q != qsc_q) {
+                qsc_q = xh.q;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const int b = (4 * h + qd) % a.bpc;
+                    const int qq = SH ? xh.q * a.group + b : xh.q;
+                    const int tok = SH ? lane : b * 32 + lane;
+                    qsc[h] = (tok < a.nq && qq < a.n_queries)
+                                 ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
+                                 : 0.f;
+                }
+            }
             if (F8 && !warp_wait_all(&scfull[xs], (t / kStRing) & 1, abort_flag, a.err, a.budget)) break;
             const float* scol = sc + xs * STR;  // F8: scale of each column's document row
+            float v[H][32], sb[H][4];
+            int held = -1;  // the column group in v
             for (int i = 0; i < xh.nseg; ++i) {
                 const SegInfo si = slots[xs].seg[i];
                 if (si.flags & kFirst) {
+                    mine = static_cast<int>(ord & static_cast<uint32_t>(a.reps - 1)) == copy;
+                    ++ord;
+                    if (mine) {
 #pragma unroll
-                    for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
-                    if (F8 && xh.q != qsc_q) {
-                        qsc_q = xh.q;
+                        for (int h = 0; h < H; ++h) rmax[h] = -INFINITY;
+                    }
+                }
+                if (!mine) continue;
+                const int c_hi = si.col + si.r;
+                for (int g0 = si.col & ~31; g0 < c_hi; g0 += 32) {
+                    if (g0 != held) {
 #pragma unroll
                         for (int h = 0; h < H; ++h) {
-                            const int b = (4 * h + qd) % a.bpc;
-                            const int qq = SH ? xh.q * a.group + b : xh.q;
-                            const int tok = SH ? lane : b * 32 + lane;
-                            qsc[h] = (tok < a.nq && qq < a.n_queries)
-                                         ? __ldg(a.q_scales + static_cast<int64_t>(qq) * a.nq + tok)
-                                         : 0.f;
+                            load_group(tbase + (static_cast<uint32_t>(qd * 32) << 16) +
+                                           static_cast<uint32_t>((ab * H + h) * STR + g0),
+                                       scol + g0, v[h]);
+                            sub_maxima8(v[h], sb[h]);
                         }
+                        held = g0;
                     }
-                }
-                const int c_lo = si.col;
-                const int c_hi = si.col + si.r;
+                    const int lo = max(si.col - g0, 0);
+                    const int hi = min(c_hi - g0, 32);
 #pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const uint32_t tcol = tbase + (static_cast<uint32_t>(qd * 32) << 16) +
-                                          static_cast<uint32_t>((ab * H + h) * STR);
-                    for (int c0 = c_lo & ~31; c0 < c_hi; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tcol + static_cast<uint32_t>(c0), v);
-                        if (F8) scale32(v, scol + c0);
-                        if (c0 < c_lo || c0 + 32 > c_hi)
-                            rmax[h] = fold_max32_range(rmax[h], v, max(c_lo - c0, 0), min(c_hi - c0, 32));
-                        else
-                            rmax[h] = fold_max32(rmax[h], v);
-                    }
+                    for (int h = 0; h < H; ++h) rmax[h] = fold_cols(rmax[h], v[h], sb[h], lo, hi);
                 }
-                if ((si.flags & kLast) && !finish(si, xh)) {
+                if ((si.flags & kLast) && !finish(si.f, xh.q, rmax)) {
                     aborted = true;
                     break;
                 }
@@ -1105,8 +1157,9 @@ inline int config_shapes(Config* out) {
         return 1;
     }
     out[0] = {256, 1, 0};
-    out[1] = {128, 2, 0};
-    return 2;
+    out[1] = {128, 1, 0};
+    out[2] = {128, 2, 0};
+    return 3;
 }
 
 // Plan shared memory, encode the tensor maps and launch dense_tc_kernel.
@@ -1151,7 +1204,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
                                     : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
         int best = -1;
         for (int qs = 2; qs >= 1; --qs) {
-            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND);
+            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, acc_count(H, str, ctas));
             const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
             if (sts > best) {
                 best = sts;
@@ -1193,11 +1246,18 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
             if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
         } else if (H == 2 || TF) {
             if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
-        } else if (!SH && F8) {
+        } else if (!SH && a.nchunks == 1) {
+            // 128-byte rows (FP8 at d <= 128, fp16 / bf16 at d <= 64): a
+            // super-tile carries few bytes for its fixed pipeline costs, so
+            // two CTAs per SM run two pipelines side by side
             if (plan(128, 2, stages, qslots, reps)) str = 128, ctas = 2;
             else if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+            else if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
         } else {
+            // 256-row super-tiles unless the query tile leaves no room for
+            // their stages; then 128-row ones
             if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
+            else if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
         }
     }
     if (ctas == 0) return TMS_ERR_UNSUPPORTED;
@@ -1215,7 +1275,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.idesc = make_idesc(128, 0, TF ? 2u : ((!F8 && dtype == TMS_BF16) ? 1u : 0u));
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND);
+    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND, acc_count(H, str, ctas));
     const int smem = L.total + 1024;
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {
@@ -1225,7 +1285,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     } else if constexpr (TF) {
         kern = dense_tc_kernel<1, 128, 1, false, kTF32>;
     } else {
-        kern = str == 128 ? dense_tc_kernel<1, 128, 2, SH, KIND> : dense_tc_kernel<1, 256, 1, SH, KIND>;
+        kern = str == 256 ? dense_tc_kernel<1, 256, 1, SH, KIND>
+                          : (ctas == 2 ? dense_tc_kernel<1, 128, 2, SH, KIND> : dense_tc_kernel<1, 128, 1, SH, KIND>);
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
@@ -1241,7 +1302,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
 template <int H, bool SH, int KIND>
 tms_status tune_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
                    const void* doc_tokens, int64_t n_tokens, const Args& a, cudaStream_t stream, int* n_timed) {
-    Config shapes[2];
+    Config shapes[3];
     const int ns = config_shapes<H, SH, KIND>(shapes);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
