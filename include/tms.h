@@ -326,6 +326,35 @@ tms_status tms_topk_split(const float *scores, const int64_t *cand_offsets, int 
                           int64_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * tms_topk_split without a workspace argument, for callers that cannot
+ * allocate device memory: a plugin whose host application owns every
+ * device allocation through its own pool, or a serving path that must
+ * make no cudaMalloc after start-up because the call can synchronise the
+ * device and has no bounded latency.  The paper has no counterpart; this
+ * is an interface variant of the top-k step (Section 6.8), not a new
+ * operation.  Same arguments, order, ties, padding and limits as
+ * tms_topk_split, and bit-identical results.
+ *
+ * The slice entries live in one 4 MiB array of device memory inside the
+ * library (a file-scope __device__ array): every GPU that loads libtms
+ * holds those 4 MiB until the process exits, and the call itself
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and remembers it;
+ *     make that first call before any stream capture on the device.
+ *   - Every call on a device shares the one array and it keeps the last
+ *     call's contents.  Nothing in it needs clearing (each call writes
+ *     every entry it reads), but calls whose work may overlap on the GPU
+ *     (different streams with no ordering between them) race on it: order
+ *     them on one stream, or use tms_topk_split with separate workspaces.
+ *   - The entries needed are tms_topk_workspace_size's bytes
+ *     (n_queries * S * topk * 8); above 4,194,304 bytes the call returns
+ *     TMS_ERR_UNSUPPORTED before anything is enqueued.
+ */
+tms_status tms_topk_split_noalloc(const float *scores, const int64_t *cand_offsets, int n_queries, int topk,
+                                  int64_t n_cand, float *out_scores, int32_t *out_pos, cudaStream_t stream);
+
+/*
  * Serving loop: a device-resident corpus (a dense store and optionally a PQ
  * store and an FP8 copy of the dense store) and a worker thread that scores
  * requests -- one query of nq tokens

@@ -22,6 +22,8 @@
 // bit-identical to tms_topk.  Deterministic and exact: it depends only on
 // the scores.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "tms_common.cuh"
 #include "tms_internal.h"
@@ -336,6 +338,73 @@ extern "C" tms_status tms_topk_split(const float* scores, const int64_t* cand_of
     const int64_t need = static_cast<int64_t>(n_queries) * S * topk * 8;
     if (workspace == nullptr || !aligned16(workspace) || workspace_bytes < need) return TMS_ERR_INVALID_ARG;
     auto* ws = static_cast<unsigned long long*>(workspace);
+    topk::topk_slice_kernel<<<static_cast<unsigned>(n_queries * S), topk::kThreads, 0, stream>>>(
+        scores, cand_offsets, topk, S, ws, dev.err);
+    st = launch_status(cudaGetLastError());
+    if (st != TMS_OK) return st;
+    topk::topk_merge_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(
+        scores, cand_offsets, topk, S, ws, out_scores, out_pos);
+    return launch_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// tms_topk_split_noalloc: tms_topk_split for callers that cannot allocate
+// device memory.  The slice entries go to one fixed array in the library's
+// own device memory instead of a caller workspace; it exists once per GPU
+// that loads the library, for the life of the process.
+namespace tms {
+namespace topk {
+
+constexpr int64_t kNoAllocScratchBytes = int64_t(4) << 20;  // 4 MiB
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocScratchBytes / 8];
+
+// The device address of g_noalloc_scratch on the current device.  Host code
+// sees the array's name only as a host-side stand-in, so the address is
+// looked up with cudaGetSymbolAddress the first time a device asks (that
+// device current) and remembered per device ordinal.
+tms_status noalloc_scratch(int ordinal, unsigned long long** out) {
+    static std::mutex m;
+    static std::map<int, unsigned long long*> addr;
+    std::lock_guard<std::mutex> lk(m);
+    auto it = addr.find(ordinal);
+    if (it == addr.end()) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            return TMS_ERR_CUDA;
+        }
+        it = addr.emplace(ordinal, static_cast<unsigned long long*>(p)).first;
+    }
+    *out = it->second;
+    return TMS_OK;
+}
+
+}  // namespace topk
+}  // namespace tms
+
+extern "C" tms_status tms_topk_split_noalloc(const float* scores, const int64_t* cand_offsets, int n_queries,
+                                             int topk, int64_t n_cand, float* out_scores, int32_t* out_pos,
+                                             cudaStream_t stream) {
+    using namespace tms;
+    if (!topk::args_ok(scores, cand_offsets, n_queries, topk, out_scores, out_pos) || n_cand < 0)
+        return TMS_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    tms_status st = current_device(&dev);
+    if (st != TMS_OK) return st;
+    const int S = topk::slices(dev.sm_count, n_queries, topk, n_cand);
+    if (S == 1) {  // one CTA per query: no scratch at all
+        topk::topk_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(
+            scores, cand_offsets, topk, out_scores, out_pos, dev.err);
+        return launch_status(cudaGetLastError());
+    }
+    const int64_t need = static_cast<int64_t>(n_queries) * S * topk * 8;
+    if (need > topk::kNoAllocScratchBytes) return TMS_ERR_UNSUPPORTED;
+    unsigned long long* ws = nullptr;
+    st = topk::noalloc_scratch(dev.ordinal, &ws);
+    if (st != TMS_OK) return st;
+    // Every slice writes all k of its entries (padding included), so nothing
+    // from an earlier call is ever read.
     topk::topk_slice_kernel<<<static_cast<unsigned>(n_queries * S), topk::kThreads, 0, stream>>>(
         scores, cand_offsets, topk, S, ws, dev.err);
     st = launch_status(cudaGetLastError());

@@ -34,7 +34,7 @@ TMS_FAULT_HOLD_ACCUMULATOR = 1
 #: every symbol include/tms.h declares
 EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
            "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
-           "tms_score_pq_tc_shared", "tms_topk", "tms_topk_workspace_size", "tms_topk_split", "tms_server_create",
+           "tms_score_pq_tc_shared", "tms_topk", "tms_topk_workspace_size", "tms_topk_split", "tms_topk_split_noalloc", "tms_server_create",
            "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_status_string",
            "tms_version", "tms_peak_shared_load", "tms_peak_hbm_read")
 
@@ -101,6 +101,7 @@ def lib(build_if_missing: bool = True):
             L.tms_topk.argtypes = [_p, _p, _i32, _i32, _p, _p, _p]
             L.tms_topk_workspace_size.argtypes = [_i32, _i32, _i64, ctypes.POINTER(ctypes.c_int64)]
             L.tms_topk_split.argtypes = [_p, _p, _i32, _i32, _i64, _p, _p, _p, _i64, _p]
+            L.tms_topk_split_noalloc.argtypes = [_p, _p, _i32, _i32, _i64, _p, _p, _p]
             L.tms_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
             L.tms_server_submit.argtypes = [_p, _i32, _p, _p, _i64, ctypes.POINTER(ctypes.c_uint64)]
             L.tms_server_wait.argtypes = [_p, ctypes.c_uint64, ctypes.c_double, _p, _p,
@@ -117,6 +118,7 @@ def lib(build_if_missing: bool = True):
             for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
                          "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
                          "tms_score_pq_tc_shared", "tms_topk", "tms_topk_workspace_size", "tms_topk_split",
+                         "tms_topk_split_noalloc",
                          "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
                          "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_version",
                          "tms_peak_shared_load", "tms_peak_hbm_read"):
@@ -434,6 +436,24 @@ def topk_split(scores, cand_offsets, k, n_cand=None, out_scores=None, out_pos=No
     _check("tms_topk_split", lib().tms_topk_split(_dev(scores, torch.float32), _dev(cand_offsets, torch.int64), nQ, k,
                                                   n_cand, _dev(out_scores, torch.float32), _dev(out_pos, torch.int32),
                                                   _dev(workspace), nbytes, _stream_ptr(stream)))
+    return out_scores, out_pos
+
+
+def topk_split_noalloc(scores, cand_offsets, k, n_cand=None, out_scores=None, out_pos=None, stream=None):
+    """tms_topk_split with its scratch in the library's fixed device array
+    (no workspace, no device allocation by the library; the output tensors
+    are allocated here only when not given)."""
+    torch = _torch()
+    nQ = cand_offsets.shape[0] - 1
+    n_cand = scores.numel() if n_cand is None else int(n_cand)
+    if out_scores is None:
+        out_scores = torch.empty((nQ, k), dtype=torch.float32, device=scores.device)
+    if out_pos is None:
+        out_pos = torch.empty((nQ, k), dtype=torch.int32, device=scores.device)
+    _check("tms_topk_split_noalloc",
+           lib().tms_topk_split_noalloc(_dev(scores, torch.float32), _dev(cand_offsets, torch.int64), nQ, k, n_cand,
+                                        _dev(out_scores, torch.float32), _dev(out_pos, torch.int32),
+                                        _stream_ptr(stream)))
     return out_scores, out_pos
 
 
