@@ -169,8 +169,16 @@ struct Args {
 constexpr int kFaultHoldAccumulator = TMS_FAULT_HOLD_ACCUMULATOR;
 
 struct Layout {
-    int q_off, qlo_off, stage_off, stage_stride, part_off, sc_off, cb_off, code_off, st_off, bar_off, misc_off, total;
+    int q_off, qlo_off, stage_off, stage_stride, part_off, fin_off, sc_off, cb_off, code_off, st_off, bar_off, misc_off,
+        total;
 };
+
+// Finished documents waiting for their sum over query tokens, per epilogue
+// warp: kFinRows rows of 32 row maxima (one row per document and query
+// half), padded to 33 floats so that lane r reading row r walks distinct
+// banks, then each document's (candidate, query) pair.
+constexpr int kFinRows = 16;
+constexpr int kFinWarpBytes = kFinRows * 33 * 4 + kFinRows * 8;
 
 // Shared-memory carve-up; the same arithmetic runs on host and device.
 // The query region comes first: the MMA reads 128 (x H) rows from each
@@ -181,7 +189,7 @@ struct Layout {
 // TF: the query region and every stage have a lo twin right after them.
 // F8: per super-tile record slot, the row scale of every column.
 __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind,
-                                              int kacc) {
+                                              int kacc, bool fin) {
     const bool f8 = kind == kE4M3;
     const int twin = kind == kTF32 ? 2 : 1;
     Layout L;
@@ -190,7 +198,8 @@ __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunk
     L.stage_off = (twin * L.qlo_off + 1023) & ~1023;
     L.stage_stride = twin * str * 128;
     L.part_off = L.stage_off + stages * L.stage_stride;
-    L.sc_off = L.part_off + 128;  // [2 copies][2 parities][4 blocks] partial sums, 128-byte aligned
+    L.fin_off = L.part_off + 128;  // after [2 copies][2 parities][4 blocks] partial sums
+    L.sc_off = L.fin_off + (fin ? kEpiWarps * kFinWarpBytes : 0);  // 128-byte aligned
     L.cb_off = L.sc_off + (f8 ? st_ring(str) * str * 4 : 0);  // F8: [st_ring][str] column scales
     L.code_off = L.cb_off + (kind == kPQ ? kPqCbBytes : 0);                        // kPQ: fp16 codebook
     // kPQ: code-row ring, then per slot the valid rows of each 8-row group
@@ -344,13 +353,14 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     const int QS = a.qslots;
     const int NCH = a.nchunks;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND, KACC);
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND, KACC, SH || a.bpc == 1);
     const int SSTRIDE = L.stage_stride;  // bytes between stages (TF: hi, then lo)
 
     uint8_t* q_base = smem + L.q_off;
     uint8_t* qlo_base = smem + L.qlo_off;  // TF: the lo twin of the query region
     uint8_t* stage_base = smem + L.stage_off;
     float* part = reinterpret_cast<float*>(smem + L.part_off);  // [copy][parity][block]
+    uint8_t* fin_base = smem + L.fin_off;                       // [epilogue warp] finished-document rows
     float* sc = reinterpret_cast<float*>(smem + L.sc_off);      // F8: [kStRing][STR] scale of each column
     StSlot* slots = reinterpret_cast<StSlot*>(smem + L.st_off);
     uint8_t* cb = smem + L.cb_off;           // kPQ: fp16 codebook, entry (code, m) at (code * 16 + m) * 16
@@ -978,7 +988,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         for (int h = 0; h < H; ++h) qsc[h] = 1.f;
 
         // A document's score(s) from its row maxima m.  False on abort.
-        auto finish = [&](int64_t f, int q, const float (&m)[H]) -> bool {
+        auto finish_now = [&](int64_t f, int q, const float (&m)[H]) -> bool {
             if (SH) {
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
@@ -1015,6 +1025,52 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 }
             }
             ++mydocs;
+            return true;
+        };
+        // Documents are finished in batches, off the path that releases the
+        // accumulator: their 32 row maxima (times the query-token scales,
+        // F8; 0 past nq) go to this warp's rows in shared memory, and every
+        // kFinRows / 2 rows lane r sums row r in token order and stores the
+        // score -- the same fixed order for every document, wherever it
+        // sits in a batch.  With several 32-token blocks per query (nq > 32)
+        // the copy's warps combine block sums at once instead (finish_now).
+        const bool batched = SH || a.bpc == 1;
+        float* fin_rows = reinterpret_cast<float*>(fin_base + qd * kFinWarpBytes);
+        int* fin_ids = reinterpret_cast<int*>(fin_base + qd * kFinWarpBytes + kFinRows * 33 * 4);
+        int nfin = 0;  // rows in use
+        auto flush = [&]() {
+            __syncwarp();
+            if (lane < nfin) {
+                float sum = 0.f;
+#pragma unroll 8
+                for (int i = 0; i < 32; ++i) sum += fin_rows[lane * 33 + i];
+                const int doc = lane / H;
+                const int f = fin_ids[2 * doc];
+                const int q = fin_ids[2 * doc + 1];
+                if (SH) {
+                    const int b = (4 * (lane % H) + qd) % a.bpc;
+                    const int qq = q * a.group + b;
+                    if (qq < a.n_queries) a.out[static_cast<int64_t>(qq) * a.n_cand + f] = sum;
+                } else {
+                    a.out[f] = sum;
+                }
+            }
+            __syncwarp();
+            nfin = 0;
+        };
+        auto finish = [&](int64_t f, int q, const float (&m)[H]) -> bool {
+            if (!batched) return finish_now(f, q, m);
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const int tok = SH ? lane : blk * 32 + lane;
+                fin_rows[(nfin + h) * 33 + lane] = tok < a.nq ? (F8 ? m[h] * qsc[h] : m[h]) : 0.f;
+            }
+            if (lane == 0) {
+                fin_ids[2 * (nfin / H)] = static_cast<int>(f);
+                fin_ids[2 * (nfin / H) + 1] = q;
+            }
+            nfin += H;
+            if (nfin == kFinRows) flush();
             return true;
         };
         // 32 accumulator columns of this warp's lanes; F8: each times its
@@ -1106,7 +1162,9 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 mbar_arrive(&tempty[ab]);
                 mbar_arrive(&xempty[xs]);
             }
+            if (nfin >= kFinRows / 2) flush();
         }
+        if (!aborted && nfin > 0) flush();
     }
 
     tc_fence_before();
@@ -1204,7 +1262,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
                                     : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
         int best = -1;
         for (int qs = 2; qs >= 1; --qs) {
-            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, acc_count(H, str, ctas));
+            const Layout L0 =
+                make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, acc_count(H, str, ctas), SH || a.bpc == 1);
             const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
             if (sts > best) {
                 best = sts;
@@ -1275,7 +1334,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.idesc = make_idesc(128, 0, TF ? 2u : ((!F8 && dtype == TMS_BF16) ? 1u : 0u));
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND, acc_count(H, str, ctas));
+    const Layout L =
+        make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND, acc_count(H, str, ctas), SH || a.bpc == 1);
     const int smem = L.total + 1024;
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {
