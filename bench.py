@@ -80,7 +80,8 @@ def parse_args():
     p.add_argument("--no-rows", action="store_true", help="skip the secondary workloads")
     p.add_argument("--workload", choices=["headline", "small"], default="headline",
                    help="small: 100,000 docs, 1 query x 100,000 candidates (sized for ncu captures)")
-    p.add_argument("--profile-case", choices=["fp8_small", "pq_small", "pq16_small", "pqtc_small", "shared_small"],
+    p.add_argument("--profile-case", choices=["fp8_small", "f32_small", "d64_small", "pq_small", "pq16_small", "pqtc_small",
+                                              "shared_small", "shared64_small", "shared768_small"],
                    default=None,
                    help="run only one small secondary kernel (sized for ncu captures) and print its timing")
     args = p.parse_args()
@@ -1070,18 +1071,27 @@ def run_tms(args, ws, rank, local):
 
 def profile_case(args):
     """One secondary kernel on a small case (100,000 documents, a few GB):
-    fp8_small -- FP8 store, 1 query x 100,000 candidates; pq_small -- PQ
-    M=16 K=256, 8 queries over all documents (pq16_small: the same through
-    the fp16 table; pqtc_small: decompressed in shared memory, tensor
-    cores); shared_small -- bf16 d=256, 8 queries over all documents in the
-    shared schedule."""
+    fp8_small -- FP8 store, 1 query x 100,000 candidates; f32_small -- fp32
+    (split TF32), the same; d64_small -- bf16 d=64, the same; pq_small --
+    PQ M=16 K=256, 8 queries over all documents (pq16_small: the same
+    through the fp16 table; pqtc_small: decompressed in shared memory,
+    tensor cores); shared_small / shared64_small / shared768_small -- bf16
+    d=256 / 64 / 768, 8 queries over all documents in the shared schedule
+    (20,000 documents at d=768: 3.3 GB)."""
     import torch
     from paper_2606_26439_gb300 import tms
     dev = torch.device("cuda")
     n = 100_000
     lens = synth.lengths_uniform(n, LO, HI, 9)
     ids = torch.arange(n, dtype=torch.int32, device=dev)
-    if args.profile_case == "fp8_small":
+    if args.profile_case in ("f32_small", "d64_small"):
+        dt, d = ("f32", 128) if args.profile_case == "f32_small" else ("bf16", 64)
+        tok, off, ln = synth.device_dense_corpus(lens, d, dt, 9, dev)
+        q = synth.queries(1, NQ, d, dt, 9).to(dev)
+        co = torch.tensor([0, n], dtype=torch.int64, device=dev)
+        run = lambda: tms.score_dense(q, tok, off, ln, ids, co)  # noqa: E731
+        units = n
+    elif args.profile_case == "fp8_small":
         tok, off, ln = synth.device_dense_corpus(lens, D, "f16", 9, dev)
         tc, ts = tms.quantize_e4m3(tok)
         del tok
@@ -1102,8 +1112,13 @@ def profile_case(args):
             run = lambda: tms.score_pq(lut, codes, off, ln, f, co, f16_table=half)  # noqa: E731
         units = 8 * n
     else:
-        tok, off, ln = synth.device_dense_corpus(lens, 256, "bf16", 9, dev)
-        q = synth.queries(8, NQ, 256, "bf16", 9).to(dev)
+        d = {"shared_small": 256, "shared64_small": 64, "shared768_small": 768}[args.profile_case]
+        if d == 768:
+            n = 20_000
+            lens = lens[:n]
+            ids = ids[:n]
+        tok, off, ln = synth.device_dense_corpus(lens, d, "bf16", 9, dev)
+        q = synth.queries(8, NQ, d, "bf16", 9).to(dev)
         run = lambda: tms.score_dense_shared(q, tok, off, ln, ids)  # noqa: E731
         units = 8 * n
     for _ in range(args.warmup):

@@ -295,21 +295,28 @@ __device__ __forceinline__ void sub_maxima8(const float (&v)[32], float (&sb)[4]
 
 // max(m, v[lo..hi)) for 0 <= lo < hi <= 32 with lo a multiple of 8: the
 // whole sub-blocks from their maxima sb, a partial last one (hi not a
-// multiple of 8) from its hi % 8 leading columns.
+// multiple of 8) from its hi % 8 leading columns.  A tile covering the
+// whole group (the common case inside long documents) takes one branch
+// and two maxima.
 __device__ __forceinline__ float fold_cols(float m, const float (&v)[32], const float (&sb)[4], int lo, int hi) {
+    if (lo == 0 && hi == 32) return fmax3(m, fmax3(sb[0], sb[1], sb[2]), sb[3]);
     const int kl = lo >> 3;
     const int kf = hi >> 3;
+    // sub-blocks [kl, kf) as a 4-bit mask
+    const uint32_t whole = (0xfu >> (4 - kf)) & ~((1u << kl) - 1u);
     float x[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) x[k] = (k >= kl && k < kf) ? sb[k] : -INFINITY;
+    for (int k = 0; k < 4; ++k) x[k] = (whole >> k) & 1u ? sb[k] : -INFINITY;
     m = fmax3(m, fmax3(x[0], x[1], x[2]), x[3]);
     const int rem = hi & 7;
     if (rem != 0) {  // sub-block kf < 4 holds rem columns of the tile
+        // the sub-block's first 7 columns, picked by kf, then masked to rem
         float y[7];
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
-            const float c = kf == 0 ? v[j] : (kf == 1 ? v[8 + j] : (kf == 2 ? v[16 + j] : v[24 + j]));
-            y[j] = j < rem ? c : -INFINITY;
+            const float lo2 = (kf & 1) ? v[8 + j] : v[j];
+            const float hi2 = (kf & 1) ? v[24 + j] : v[16 + j];
+            y[j] = j < rem ? ((kf & 2) ? hi2 : lo2) : -INFINITY;
         }
         m = fmax3(m, fmax3(y[0], y[1], y[2]), fmax3(y[3], y[4], fmaxf(y[5], y[6])));
     }
