@@ -94,17 +94,20 @@ tms_status tms_score_dense(const void *queries, tms_dtype dtype, int n_queries, 
                            float *out_scores, cudaStream_t stream);
 
 /*
- * Autotuner for tms_score_dense: the same arguments and effect (out_scores
- * holds the scores when it returns), but first every tensor-core launch
- * configuration that fits this shape is timed on these inputs -- rows per
- * super-tile (256 / 128), CTAs per SM (1 / 2) and copies of the query
- * tile (4 / 2 / 1), stages derived -- and the fastest is remembered for
- * every later tms_score_dense call on this device with the same dtype
- * class (fp16/bf16 or fp32), ceil(nq / 32) and number of dimension
- * chunks.  Scores do not depend on the configuration (bitwise).  This call
- * synchronises `stream`.  *n_configs (HOST, may be NULL) receives the
- * number of configurations timed (0 when fp32 falls back to the CUDA-core
- * kernel, which has none).
+ * Autotuner for tms_score_dense (the tile-shape search of Section 6.9,
+ * Table tile_ablation, over this kernel's own tile parameters): the same
+ * arguments and effect (out_scores holds the scores when it returns), but
+ * first every distinct tensor-core launch configuration that fits this
+ * shape is timed on these inputs -- rows per super-tile (256 / 128: the
+ * documents of one MMA run), CTAs per SM (1 / 2), copies of the query tile
+ * (4 / 2 / 1: query tokens per epilogue warp), query-tile slots (1 / 2)
+ * and chunk stages (all that fit / at most 4) -- and the fastest is
+ * remembered for every later tms_score_dense call on this device with the
+ * same dtype class (fp16/bf16 or fp32), ceil(nq / 32) and number of
+ * dimension chunks.  Scores do not depend on the configuration (bitwise).
+ * This call synchronises `stream`.  *n_configs (HOST, may be NULL)
+ * receives the number of configurations timed (0 when fp32 falls back to
+ * the CUDA-core kernel, which has none).
  */
 tms_status tms_tune_dense(const void *queries, tms_dtype dtype, int n_queries, int nq, int d,
                           const void *doc_tokens, int64_t n_tokens,
@@ -134,6 +137,20 @@ tms_status tms_score_dense_shared(const void *queries, tms_dtype dtype, int n_qu
                                   const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
                                   const int32_t *cand_ids, int64_t n_cand, float *out_scores,
                                   cudaStream_t stream);
+
+/*
+ * Autotuner for tms_score_dense_shared: as tms_tune_dense, and the query
+ * group size (8 / 4 / 2 queries stacked in M, those the launch allows and
+ * shared memory holds) is searched too; the fastest group and its
+ * configuration are remembered for later tms_score_dense_shared calls on
+ * this device with the same dimension chunks and min(n_queries, 8).
+ * Scores are bitwise those of tms_score_dense_shared with any group.
+ */
+tms_status tms_tune_dense_shared(const void *queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                 const void *doc_tokens, int64_t n_tokens,
+                                 const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                                 const int32_t *cand_ids, int64_t n_cand, float *out_scores,
+                                 cudaStream_t stream, int *n_configs);
 
 /*
  * FP8 E4M3 token store (an extension of the paper's fp16/bf16 scoring;
@@ -190,6 +207,25 @@ tms_status tms_score_fp8_shared(const uint8_t *q_codes, const float *q_scales, i
                                 const uint8_t *doc_codes, const float *doc_scales, int64_t n_tokens,
                                 const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
                                 const int32_t *cand_ids, int64_t n_cand, float *out_scores, cudaStream_t stream);
+
+/*
+ * Autotuners for the FP8 store, as tms_tune_dense / tms_tune_dense_shared:
+ * same arguments and effect as tms_score_fp8 / tms_score_fp8_shared, the
+ * configurations (and, shared lists, the group size) timed first and the
+ * fastest remembered for later calls of the same shape on this device.
+ * These calls synchronise `stream`; *n_configs (HOST, may be NULL)
+ * receives the number of configurations timed.
+ */
+tms_status tms_tune_fp8(const uint8_t *q_codes, const float *q_scales, int n_queries, int nq, int d,
+                        const uint8_t *doc_codes, const float *doc_scales, int64_t n_tokens,
+                        const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                        const int32_t *cand_ids, const int64_t *cand_offsets, int64_t n_cand,
+                        float *out_scores, cudaStream_t stream, int *n_configs);
+tms_status tms_tune_fp8_shared(const uint8_t *q_codes, const float *q_scales, int n_queries, int nq, int d,
+                               const uint8_t *doc_codes, const float *doc_scales, int64_t n_tokens,
+                               const int64_t *doc_offsets, const int32_t *doc_lengths, int64_t n_docs,
+                               const int32_t *cand_ids, int64_t n_cand, float *out_scores, cudaStream_t stream,
+                               int *n_configs);
 
 /*
  * PQ distance table (Section 4.2, Phase 1):

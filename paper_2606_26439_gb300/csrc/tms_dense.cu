@@ -205,11 +205,14 @@ extern "C" tms_status tms_tune_dense(const void* queries, tms_dtype dtype, int n
                             cand_ids, cand_offsets, n_cand, out_scores, stream, true, n_configs);
 }
 
-extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
-                                             const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
-                                             const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
-                                             int64_t n_cand, float* out_scores, cudaStream_t stream) {
-    using namespace tms;
+namespace tms {
+namespace {
+
+tms_status score_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                              const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
+                              const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids, int64_t n_cand,
+                              float* out_scores, cudaStream_t stream, bool tune, int* n_configs) {
+    if (n_configs) *n_configs = 0;
     if (dtype != TMS_F16 && dtype != TMS_BF16 && dtype != TMS_F32) return TMS_ERR_INVALID_ARG;
     if (n_queries < 1 || n_queries > 4096 || nq < 1 || nq > 128 || d < 8 || d > 1024 || d % 8 != 0)
         return TMS_ERR_INVALID_ARG;
@@ -240,20 +243,25 @@ extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtyp
     a.n_queries = n_queries;
     a.nq = nq;
     a.nchunks = (d + dense::chunk_elems(dense::kF16) - 1) / dense::chunk_elems(dense::kF16);
-    // Queries per group (32 MMA columns each): up to 8; a smaller group when
-    // the stacked query tile would not fit shared memory at this d.
-    for (int group = n_queries >= 5 ? 8 : (n_queries >= 3 ? 4 : 2); group >= 2; group /= 2) {
-        const int64_t n_groups = (n_queries + group - 1) / group;
-        if (n_groups * n_cand >= (int64_t(1) << 31)) return TMS_ERR_UNSUPPORTED;
-        a.n_flat = n_groups * n_cand;
-        a.group = group;
-        a.bpc = group;
-        a.qbox = 32;
-        st = group == 8 ? dense::launch_tc<2, true, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
-                                                          stream)
-                        : dense::launch_tc<1, true, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
-                                                          stream);
-        if (st != TMS_ERR_UNSUPPORTED) return st;
-    }
-    return TMS_ERR_UNSUPPORTED;
+    return dense::shared_run<dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream, tune,
+                                          n_configs);
+}
+
+}  // namespace
+}  // namespace tms
+
+extern "C" tms_status tms_score_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                             const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
+                                             const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
+                                             int64_t n_cand, float* out_scores, cudaStream_t stream) {
+    return tms::score_dense_shared(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets, doc_lengths,
+                                   n_docs, cand_ids, n_cand, out_scores, stream, false, nullptr);
+}
+
+extern "C" tms_status tms_tune_dense_shared(const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                                            const void* doc_tokens, int64_t n_tokens, const int64_t* doc_offsets,
+                                            const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids,
+                                            int64_t n_cand, float* out_scores, cudaStream_t stream, int* n_configs) {
+    return tms::score_dense_shared(queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, doc_offsets, doc_lengths,
+                                   n_docs, cand_ids, n_cand, out_scores, stream, true, n_configs);
 }

@@ -1182,12 +1182,18 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     }
 }
 
-// A launch configuration: rows per super-tile, CTAs per SM, copies of the
-// query blocks stacked in M.
+// A launch configuration -- the kernel's counterpart of the paper's tile
+// shape (Section 6.9, Table tile_ablation): rows per super-tile (documents
+// per MMA run) and CTAs per SM, copies of the query blocks stacked in M
+// (query tokens per epilogue warp), at most `stages` chunk stages (0: as
+// many as fit) and `qslots` query-tile slots (0: whichever gives more
+// stages).
 struct Config {
     int str;
     int ctas;
     int reps;
+    int stages;
+    int qslots;
 };
 
 // Configurations chosen by the autotuner, per device and launch shape.
@@ -1209,21 +1215,30 @@ inline std::map<TuneKey, Config>& tune_table() {
     static std::map<TuneKey, Config> t;
     return t;
 }
+// Shared candidate lists: the query group size the autotuner chose, per
+// device, row type, dimension chunks and queries per launch (capped at 8).
+inline std::map<TuneKey, int>& group_table() {
+    static std::map<TuneKey, int> t;
+    return t;
+}
+inline TuneKey group_key(int device, int kind, int nchunks, int n_queries) {
+    return TuneKey{device, kind, 0, 1, nchunks, n_queries < 8 ? n_queries : 8};
+}
 
 // The configurations an instantiation has kernels for.
 template <int H, bool SH, int KIND>
 inline int config_shapes(Config* out) {
     if (H == 2 || KIND == kTF32) {
-        out[0] = {128, 1, 0};
+        out[0] = {128, 1, 0, 0, 0};
         return 1;
     }
     if (KIND == kPQ) {  // one query half
-        out[0] = {256, 1, 0};
+        out[0] = {256, 1, 0, 0, 0};
         return 1;
     }
-    out[0] = {256, 1, 0};
-    out[1] = {128, 1, 0};
-    out[2] = {128, 2, 0};
+    out[0] = {256, 1, 0, 0, 0};
+    out[1] = {128, 1, 0, 0, 0};
+    out[2] = {128, 2, 0, 0, 0};
     return 3;
 }
 
@@ -1239,39 +1254,38 @@ inline int config_shapes(Config* out) {
 // and a.bpc / a.qbox: per-query ceil(nq / 32) and 32 bpc, shared mode the
 // group size and 32.  `force` (the autotuner's) overrides the choice;
 // TMS_ERR_UNSUPPORTED when it does not fit.
+// The resolved launch configuration: every field of Config set.
+struct Plan {
+    int str, ctas, reps, stages, qslots;
+    bool operator==(const Plan& o) const {
+        return str == o.str && ctas == o.ctas && reps == o.reps && stages == o.stages && qslots == o.qslots;
+    }
+};
+
+// The configuration a launch of this instantiation takes: `force` if it
+// fits (else TMS_ERR_UNSUPPORTED), else the autotuner's for this shape if
+// one fits, else the default below.
 template <int H, bool SH, int KIND>
-tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
-                     const void* doc_tokens, int64_t n_tokens, Args a, cudaStream_t stream,
-                     const Config* force = nullptr) {
+tms_status plan_tc(const DeviceInfo& dev, const Args& a, const Config* force, Plan* out) {
     constexpr bool F8 = KIND == kE4M3;
     constexpr bool TF = KIND == kTF32;
     constexpr bool PQ = KIND == kPQ;
-    constexpr int CE = chunk_elems(KIND);
-    const CUtensorMapDataType tdt = F8   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
-                                  : TF ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                  : dtype == TMS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const uint64_t row_bytes = static_cast<uint64_t>(d) * (F8 ? 1 : (TF ? 4 : 2));
-    // With no document rows nothing is ever loaded through the document
-    // maps; describe the query buffer so that they still encode.
-    const void* dbase = n_tokens > 0 ? doc_tokens : queries;
-    Maps maps;
-    tms_status st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes,
-                                   CE, static_cast<uint32_t>(a.qbox));
-    if (st != TMS_OK) return st;
+    (void)F8;
     // Shared-memory plan for (rows per super-tile, CTAs per SM, copies):
     // the query-slot count (2, else 1) that gives the most stages; the
     // plan fits with at least 4 chunk stages (2 with one CTA per SM).
     const int max_reps = H == 2 ? 1 : (a.bpc == 3 ? 1 : 4 / a.bpc);
-    auto fits = [&](int str, int ctas, int rp, int need, int& stages, int& qslots) {
+    auto fits = [&](int str, int ctas, int rp, int need, int& stages, int& qslots, int cap = 0, int want_qs = 0) {
         if (rp < 1 || rp > max_reps) return false;
         const int limit = ctas == 2 ? dev.smem_per_sm / 2 - dev.smem_reserved - 1024
                                     : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
         int best = -1;
         for (int qs = 2; qs >= 1; --qs) {
+            if (want_qs && qs != want_qs) continue;
             const Layout L0 =
                 make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, acc_count(H, str, ctas), SH || a.bpc == 1);
-            const int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
+            int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
+            if (cap > 0 && sts > cap) sts = cap;
             if (sts > best) {
                 best = sts;
                 stages = sts;
@@ -1291,7 +1305,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         return false;
     };
     int stages = 0, qslots = 1, reps = 0, str = 0, ctas = 0;
-    Config tuned{0, 0, 0};
+    Config tuned{0, 0, 0, 0, 0};
     if (!force) {
         std::lock_guard<std::mutex> lk(tune_mutex());
         const auto it = tune_table().find(TuneKey{dev.ordinal, KIND, H, SH ? 1 : 0, a.nchunks, a.bpc});
@@ -1299,7 +1313,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     }
     const Config* want = force ? force : (tuned.ctas ? &tuned : nullptr);
     if (want) {
-        if (fits(want->str, want->ctas, want->reps, 2, stages, qslots)) {
+        if (fits(want->str, want->ctas, want->reps, 2, stages, qslots, want->stages, want->qslots)) {
             str = want->str;
             ctas = want->ctas;
             reps = want->reps;
@@ -1327,6 +1341,34 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         }
     }
     if (ctas == 0) return TMS_ERR_UNSUPPORTED;
+    *out = Plan{str, ctas, reps, stages, qslots};
+    return TMS_OK;
+}
+
+template <int H, bool SH, int KIND>
+tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                     const void* doc_tokens, int64_t n_tokens, Args a, cudaStream_t stream,
+                     const Config* force = nullptr) {
+    constexpr bool F8 = KIND == kE4M3;
+    constexpr bool TF = KIND == kTF32;
+    constexpr bool PQ = KIND == kPQ;
+    constexpr int CE = chunk_elems(KIND);
+    Plan p;
+    tms_status st = plan_tc<H, SH, KIND>(dev, a, force, &p);
+    if (st != TMS_OK) return st;
+    const int str = p.str, ctas = p.ctas, reps = p.reps, stages = p.stages, qslots = p.qslots;
+    const CUtensorMapDataType tdt = F8   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                  : TF ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : dtype == TMS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const uint64_t row_bytes = static_cast<uint64_t>(d) * (F8 ? 1 : (TF ? 4 : 2));
+    // With no document rows nothing is ever loaded through the document
+    // maps; describe the query buffer so that they still encode.
+    const void* dbase = n_tokens > 0 ? doc_tokens : queries;
+    Maps maps;
+    st = encode_tmap_2d(&maps.q, tdt, queries, d, static_cast<uint64_t>(n_queries) * nq, row_bytes, CE,
+                        static_cast<uint32_t>(a.qbox));
+    if (st != TMS_OK) return st;
     a.reps = reps;
     a.rows_alloc = 32 * a.bpc * reps;
     for (int h = 0; h < kBoxKinds; ++h) {
@@ -1363,12 +1405,16 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
 }
 
 // Autotuner: time every configuration this instantiation has kernels for
-// that fits the launch (3 timed launches after one warm-up each, CUDA
-// events on `stream`), remember the fastest for the launch shape, and
-// report how many were timed.  Each launch writes the scores.
+// that fits the launch -- super-tile shape x copies x query slots (1 / 2) x
+// stage cap (all that fit / 4), skipping caps that change nothing -- with 3
+// timed launches after one warm-up each (CUDA events on `stream`), remember
+// the fastest for the launch shape, and report how many were timed and the
+// best mean time per launch.  Each launch writes the scores, so the last
+// (the chosen configuration, launched again) leaves them in place.
 template <int H, bool SH, int KIND>
 tms_status tune_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
-                   const void* doc_tokens, int64_t n_tokens, const Args& a, cudaStream_t stream, int* n_timed) {
+                   const void* doc_tokens, int64_t n_tokens, const Args& a, cudaStream_t stream, int* n_timed,
+                   float* best_ms_out = nullptr, bool relaunch = true) {
     Config shapes[3];
     const int ns = config_shapes<H, SH, KIND>(shapes);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1378,32 +1424,46 @@ tms_status tune_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, 
         return TMS_ERR_CUDA;
     }
     float best_ms = 0.f;
-    Config best{0, 0, 0};
+    Config best{0, 0, 0, 0, 0};
     int timed = 0;
     tms_status st = TMS_OK;
+    Plan seen[64];
+    int nseen = 0;
     for (int i = 0; i < ns && st == TMS_OK; ++i) {
-        for (int rp = 4; rp >= 1; rp /= 2) {
-            const Config c{shapes[i].str, shapes[i].ctas, rp};
-            tms_status r = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
-                                                  stream, &c);
-            if (r == TMS_ERR_UNSUPPORTED) continue;
-            if (r != TMS_OK) {
-                st = r;
-                break;
-            }
-            cudaEventRecord(e0, stream);
-            for (int k = 0; k < 3 && r == TMS_OK; ++k)
-                r = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream, &c);
-            cudaEventRecord(e1, stream);
-            float ms = 0.f;
-            if (r != TMS_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                st = r != TMS_OK ? r : TMS_ERR_CUDA;
-                break;
-            }
-            ++timed;
-            if (best.ctas == 0 || ms < best_ms) {
-                best_ms = ms;
-                best = c;
+        for (int rp = 4; rp >= 1 && st == TMS_OK; rp /= 2) {
+            for (int qs = 1; qs <= 2 && st == TMS_OK; ++qs) {
+                for (int cap = 0; cap <= 4 && st == TMS_OK; cap += 4) {
+                    const Config c{shapes[i].str, shapes[i].ctas, rp, cap, qs};
+                    Plan pl;
+                    if (plan_tc<H, SH, KIND>(dev, a, &c, &pl) != TMS_OK) continue;
+                    bool dup = false;
+                    for (int j = 0; j < nseen; ++j) dup = dup || seen[j] == pl;
+                    if (dup || nseen == 64) continue;
+                    seen[nseen++] = pl;
+                    tms_status r = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens,
+                                                          a, stream, &c);
+                    if (r == TMS_ERR_UNSUPPORTED) continue;
+                    if (r != TMS_OK) {
+                        st = r;
+                        break;
+                    }
+                    cudaEventRecord(e0, stream);
+                    for (int k = 0; k < 3 && r == TMS_OK; ++k)
+                        r = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                   stream, &c);
+                    cudaEventRecord(e1, stream);
+                    float ms = 0.f;
+                    if (r != TMS_OK || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        st = r != TMS_OK ? r : TMS_ERR_CUDA;
+                        break;
+                    }
+                    ++timed;
+                    if (best.ctas == 0 || ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
+                }
             }
         }
     }
@@ -1416,10 +1476,91 @@ tms_status tune_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, 
         std::lock_guard<std::mutex> lk(tune_mutex());
         tune_table()[TuneKey{dev.ordinal, KIND, H, SH ? 1 : 0, a.nchunks, a.bpc}] = best;
     }
-    // leave the scores of the chosen configuration in place
-    st = launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream, &best);
     if (n_timed) *n_timed = timed;
-    return st;
+    if (best_ms_out) *best_ms_out = best_ms / 3.f;
+    // leave the scores of the chosen configuration in place
+    return relaunch ? launch_tc<H, SH, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream,
+                                             &best)
+                    : TMS_OK;
+}
+
+// Shared candidate lists in groups of `group` queries stacked in M (group
+// 8: two 128-row halves): launch, or (tune) time the configurations of
+// that group size first.  a.nchunks and the list fields are set by the
+// caller.
+template <int KIND>
+inline tms_status shared_group_launch(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq,
+                               int d, const void* doc_tokens, int64_t n_tokens, Args a, int group,
+                               cudaStream_t stream, bool tune, int* n_timed, float* ms) {
+    const int64_t n_groups = (n_queries + group - 1) / group;
+    if (n_groups * a.n_cand >= (int64_t(1) << 31)) return TMS_ERR_UNSUPPORTED;
+    a.n_flat = n_groups * a.n_cand;
+    a.group = group;
+    a.bpc = group;
+    a.qbox = 32;
+    if (tune)
+        return group == 8 ? tune_tc<2, true, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                    stream, n_timed, ms, false)
+                          : tune_tc<1, true, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                    stream, n_timed, ms, false);
+    return group == 8 ? launch_tc<2, true, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream)
+                      : launch_tc<1, true, KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, stream);
+}
+
+// Group sizes tried, largest first: up to 8 queries, no more than the
+// launch has (rounded up to a power of two), at least 2.
+inline int first_group(int n_queries) { return n_queries >= 5 ? 8 : (n_queries >= 3 ? 4 : 2); }
+
+// Score (or tune, then score) shared candidate lists: the autotuner's group
+// size for this shape if it has one and it fits, else the largest group
+// whose stacked query tile fits shared memory.  Tuning times every group
+// size's configurations and keeps the fastest group and configuration.
+template <int KIND>
+inline tms_status shared_run(const DeviceInfo& dev, const void* queries, tms_dtype dtype, int n_queries, int nq, int d,
+                      const void* doc_tokens, int64_t n_tokens, const Args& a, cudaStream_t stream, bool tune,
+                      int* n_configs) {
+    const TuneKey gk = group_key(dev.ordinal, KIND, a.nchunks, n_queries);
+    if (tune) {
+        int best_group = 0, total = 0;
+        float best_ms = 0.f;
+        for (int group = first_group(n_queries); group >= 2; group /= 2) {
+            int n = 0;
+            float ms = 0.f;
+            const tms_status st =
+                shared_group_launch<KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a, group, stream,
+                                          true, &n, &ms);
+            if (st == TMS_ERR_UNSUPPORTED) continue;
+            if (st != TMS_OK) return st;
+            total += n;
+            if (best_group == 0 || ms < best_ms) {
+                best_group = group;
+                best_ms = ms;
+            }
+        }
+        if (best_group == 0) return TMS_ERR_UNSUPPORTED;
+        {
+            std::lock_guard<std::mutex> lk(tune_mutex());
+            group_table()[gk] = best_group;
+        }
+        if (n_configs) *n_configs = total;
+    }
+    int tuned_group = 0;
+    {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        const auto it = group_table().find(gk);
+        if (it != group_table().end()) tuned_group = it->second;
+    }
+    if (tuned_group) {
+        const tms_status st = shared_group_launch<KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens,
+                                                        a, tuned_group, stream, false, nullptr, nullptr);
+        if (st != TMS_ERR_UNSUPPORTED) return st;
+    }
+    for (int group = first_group(n_queries); group >= 2; group /= 2) {
+        const tms_status st = shared_group_launch<KIND>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,
+                                                        group, stream, false, nullptr, nullptr);
+        if (st != TMS_ERR_UNSUPPORTED) return st;
+    }
+    return TMS_ERR_UNSUPPORTED;
 }
 
 }  // namespace dense

@@ -144,24 +144,71 @@ extern "C" tms_status tms_quantize_e4m3(const void* x, tms_dtype dtype, int64_t 
     return launch_status(cudaGetLastError());
 }
 
-extern "C" tms_status tms_score_fp8(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq, int d,
-                                    const uint8_t* doc_codes, const float* doc_scales, int64_t n_tokens,
-                                    const int64_t* doc_offsets, const int32_t* doc_lengths, int64_t n_docs,
-                                    const int32_t* cand_ids, const int64_t* cand_offsets, int64_t n_cand,
-                                    float* out_scores, cudaStream_t stream) {
-    using namespace tms;
+namespace tms {
+namespace fp8 {
+
+// tms_score_fp8 / tms_tune_fp8: the same checks, then launch (or tune).
+tms_status score(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq, int d,
+                 const uint8_t* doc_codes, const float* doc_scales, int64_t n_tokens, const int64_t* doc_offsets,
+                 const int32_t* doc_lengths, int64_t n_docs, const int32_t* cand_ids, const int64_t* cand_offsets,
+                 int64_t n_cand, float* out_scores, cudaStream_t stream, bool tune, int* n_configs) {
+    if (n_configs) *n_configs = 0;
     if (!cand_offsets || !aligned16(cand_offsets)) return TMS_ERR_INVALID_ARG;
     DeviceInfo dev;
     dense::Args a;
-    tms_status st = fp8::prepare(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
-                                 doc_lengths, n_docs, cand_ids, n_cand, out_scores, &dev, &a);
+    tms_status st = prepare(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                            doc_lengths, n_docs, cand_ids, n_cand, out_scores, &dev, &a);
     if (st != TMS_OK || n_cand == 0) return st;
     a.cand_offsets = cand_offsets;
     a.n_flat = n_cand;
     a.group = 0;
     a.bpc = (nq + 31) / 32;
     a.qbox = 32 * a.bpc;
-    return dense::launch_tc<1, false, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream);
+    if (tune)
+        return dense::tune_tc<1, false, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
+                                                      stream, n_configs);
+    return dense::launch_tc<1, false, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
+                                                    stream);
+}
+
+// tms_score_fp8_shared / tms_tune_fp8_shared.
+tms_status score_shared(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq, int d,
+                        const uint8_t* doc_codes, const float* doc_scales, int64_t n_tokens,
+                        const int64_t* doc_offsets, const int32_t* doc_lengths, int64_t n_docs,
+                        const int32_t* cand_ids, int64_t n_cand, float* out_scores, cudaStream_t stream, bool tune,
+                        int* n_configs) {
+    if (n_configs) *n_configs = 0;
+    DeviceInfo dev;
+    dense::Args a;
+    tms_status st = prepare(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                            doc_lengths, n_docs, cand_ids, n_cand, out_scores, &dev, &a);
+    if (st != TMS_OK) return st;
+    if (nq > 32) return TMS_ERR_UNSUPPORTED;
+    if (n_cand == 0) return TMS_OK;
+    a.cand_offsets = nullptr;
+    return dense::shared_run<dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a, stream,
+                                           tune, n_configs);
+}
+
+}  // namespace fp8
+}  // namespace tms
+
+extern "C" tms_status tms_score_fp8(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq, int d,
+                                    const uint8_t* doc_codes, const float* doc_scales, int64_t n_tokens,
+                                    const int64_t* doc_offsets, const int32_t* doc_lengths, int64_t n_docs,
+                                    const int32_t* cand_ids, const int64_t* cand_offsets, int64_t n_cand,
+                                    float* out_scores, cudaStream_t stream) {
+    return tms::fp8::score(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                           doc_lengths, n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream, false, nullptr);
+}
+
+extern "C" tms_status tms_tune_fp8(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq, int d,
+                                   const uint8_t* doc_codes, const float* doc_scales, int64_t n_tokens,
+                                   const int64_t* doc_offsets, const int32_t* doc_lengths, int64_t n_docs,
+                                   const int32_t* cand_ids, const int64_t* cand_offsets, int64_t n_cand,
+                                   float* out_scores, cudaStream_t stream, int* n_configs) {
+    return tms::fp8::score(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                           doc_lengths, n_docs, cand_ids, cand_offsets, n_cand, out_scores, stream, true, n_configs);
 }
 
 extern "C" tms_status tms_score_fp8_shared(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq,
@@ -169,27 +216,15 @@ extern "C" tms_status tms_score_fp8_shared(const uint8_t* q_codes, const float* 
                                            int64_t n_tokens, const int64_t* doc_offsets, const int32_t* doc_lengths,
                                            int64_t n_docs, const int32_t* cand_ids, int64_t n_cand,
                                            float* out_scores, cudaStream_t stream) {
-    using namespace tms;
-    DeviceInfo dev;
-    dense::Args a;
-    tms_status st = fp8::prepare(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
-                                 doc_lengths, n_docs, cand_ids, n_cand, out_scores, &dev, &a);
-    if (st != TMS_OK) return st;
-    if (nq > 32) return TMS_ERR_UNSUPPORTED;
-    if (n_cand == 0) return TMS_OK;
-    a.cand_offsets = nullptr;
-    for (int group = n_queries >= 5 ? 8 : (n_queries >= 3 ? 4 : 2); group >= 2; group /= 2) {
-        const int64_t n_groups = (n_queries + group - 1) / group;
-        if (n_groups * n_cand >= (int64_t(1) << 31)) return TMS_ERR_UNSUPPORTED;
-        a.n_flat = n_groups * n_cand;
-        a.group = group;
-        a.bpc = group;
-        a.qbox = 32;
-        st = group == 8 ? dense::launch_tc<2, true, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
-                                                         stream)
-                        : dense::launch_tc<1, true, dense::kE4M3>(dev, q_codes, TMS_F16, n_queries, nq, d, doc_codes, n_tokens, a,
-                                                         stream);
-        if (st != TMS_ERR_UNSUPPORTED) return st;
-    }
-    return TMS_ERR_UNSUPPORTED;
+    return tms::fp8::score_shared(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                                  doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream, false, nullptr);
+}
+
+extern "C" tms_status tms_tune_fp8_shared(const uint8_t* q_codes, const float* q_scales, int n_queries, int nq,
+                                          int d, const uint8_t* doc_codes, const float* doc_scales,
+                                          int64_t n_tokens, const int64_t* doc_offsets, const int32_t* doc_lengths,
+                                          int64_t n_docs, const int32_t* cand_ids, int64_t n_cand,
+                                          float* out_scores, cudaStream_t stream, int* n_configs) {
+    return tms::fp8::score_shared(q_codes, q_scales, n_queries, nq, d, doc_codes, doc_scales, n_tokens, doc_offsets,
+                                  doc_lengths, n_docs, cand_ids, n_cand, out_scores, stream, true, n_configs);
 }

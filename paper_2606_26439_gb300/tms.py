@@ -32,8 +32,8 @@ TMS_DEVERR_BAD_CSR = 8
 TMS_FAULT_HOLD_ACCUMULATOR = 1
 
 #: every symbol include/tms.h declares
-EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
-           "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
+EXPORTS = ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_tune_dense_shared",
+           "tms_quantize_e4m3", "tms_score_fp8", "tms_tune_fp8", "tms_score_fp8_shared", "tms_tune_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
            "tms_score_pq_tc_shared", "tms_topk", "tms_topk_workspace_size", "tms_topk_split", "tms_topk_split_noalloc", "tms_server_create",
            "tms_server_submit", "tms_server_wait", "tms_server_get_stats", "tms_server_destroy", "tms_get_device_error", "tms_debug_set", "tms_status_string",
            "tms_version", "tms_peak_shared_load", "tms_peak_hbm_read")
@@ -90,9 +90,15 @@ def lib(build_if_missing: bool = True):
             L.tms_tune_dense.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p,
                                          ctypes.POINTER(ctypes.c_int)]
             L.tms_score_dense_shared.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p]
+            L.tms_tune_dense_shared.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p,
+                                                ctypes.POINTER(ctypes.c_int)]
             L.tms_quantize_e4m3.argtypes = [_p, _i32, _i64, _i32, _p, _p, _p]
             L.tms_score_fp8.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
+            L.tms_tune_fp8.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p,
+                                       ctypes.POINTER(ctypes.c_int)]
             L.tms_score_fp8_shared.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p]
+            L.tms_tune_fp8_shared.argtypes = [_p, _p, _i32, _i32, _i32, _p, _p, _i64, _p, _p, _i64, _p, _i64, _p, _p,
+                                              ctypes.POINTER(ctypes.c_int)]
             L.tms_build_pq_lut.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i32, _i32, _p, _p]
             L.tms_score_pq.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
             L.tms_score_pq_f16.argtypes = [_p, _i32, _i32, _i32, _i32, _p, _i64, _p, _p, _i64, _p, _p, _i64, _p, _p]
@@ -115,8 +121,9 @@ def lib(build_if_missing: bool = True):
             L.tms_status_string.argtypes = [_i32]
             L.tms_status_string.restype = ctypes.c_char_p
             L.tms_version.argtypes = []
-            for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_quantize_e4m3", "tms_score_fp8",
-                         "tms_score_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
+            for name in ("tms_score_dense", "tms_tune_dense", "tms_score_dense_shared", "tms_tune_dense_shared",
+                         "tms_quantize_e4m3", "tms_score_fp8", "tms_tune_fp8", "tms_score_fp8_shared",
+                         "tms_tune_fp8_shared", "tms_build_pq_lut", "tms_score_pq", "tms_score_pq_f16",
                          "tms_score_pq_tc_shared", "tms_topk", "tms_topk_workspace_size", "tms_topk_split",
                          "tms_topk_split_noalloc",
                          "tms_server_create", "tms_server_submit", "tms_server_wait", "tms_server_get_stats",
@@ -298,6 +305,22 @@ def score_dense_shared(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, 
     return out
 
 
+def tune_dense_shared(queries, doc_tokens, doc_offsets, doc_lengths, cand_ids, out=None, stream=None):
+    """tms_tune_dense_shared: score_dense_shared after timing the group sizes
+    and launch configurations; returns (scores, configurations timed)."""
+    torch = _torch()
+    nQ, nq, d = queries.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty((nQ, n_cand), dtype=torch.float32, device=queries.device)
+    n = ctypes.c_int(0)
+    _check("tms_tune_dense_shared", lib().tms_tune_dense_shared(
+        _dev(queries), _dtype_code(queries), nQ, nq, d, _dev(doc_tokens, queries.dtype), doc_tokens.shape[0],
+        _dev(doc_offsets, torch.int64), _dev(doc_lengths, torch.int32), doc_offsets.shape[0],
+        _dev(cand_ids, torch.int32), n_cand, _dev(out, torch.float32), _stream_ptr(stream), ctypes.byref(n)))
+    return out, n.value
+
+
 def quantize_e4m3(x, codes=None, scales=None, stream=None):
     """Per-row E4M3 codes (uint8, x's shape) and fp32 scales (x.shape[:-1])
     of a CUDA tensor x [..., d] (fp16 / bf16 / fp32)."""
@@ -328,6 +351,42 @@ def score_fp8(q_codes, q_scales, doc_codes, doc_scales, doc_offsets, doc_lengths
         _dev(doc_lengths, torch.int32), doc_offsets.shape[0], _dev(cand_ids, torch.int32),
         _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32), _stream_ptr(stream)))
     return out
+
+
+def tune_fp8(q_codes, q_scales, doc_codes, doc_scales, doc_offsets, doc_lengths, cand_ids, cand_offsets,
+             out=None, stream=None):
+    """tms_tune_fp8: score_fp8 after timing the launch configurations;
+    returns (scores, configurations timed)."""
+    torch = _torch()
+    nQ, nq, d = q_codes.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty(n_cand, dtype=torch.float32, device=q_codes.device)
+    n = ctypes.c_int(0)
+    _check("tms_tune_fp8", lib().tms_tune_fp8(
+        _dev(q_codes, torch.uint8), _dev(q_scales, torch.float32), nQ, nq, d, _dev(doc_codes, torch.uint8),
+        _dev(doc_scales, torch.float32), doc_codes.shape[0], _dev(doc_offsets, torch.int64),
+        _dev(doc_lengths, torch.int32), doc_offsets.shape[0], _dev(cand_ids, torch.int32),
+        _dev(cand_offsets, torch.int64), n_cand, _dev(out, torch.float32), _stream_ptr(stream), ctypes.byref(n)))
+    return out, n.value
+
+
+def tune_fp8_shared(q_codes, q_scales, doc_codes, doc_scales, doc_offsets, doc_lengths, cand_ids, out=None,
+                    stream=None):
+    """tms_tune_fp8_shared: score_fp8_shared after timing the group sizes and
+    launch configurations; returns (scores, configurations timed)."""
+    torch = _torch()
+    nQ, nq, d = q_codes.shape
+    n_cand = cand_ids.shape[0]
+    if out is None:
+        out = torch.empty((nQ, n_cand), dtype=torch.float32, device=q_codes.device)
+    n = ctypes.c_int(0)
+    _check("tms_tune_fp8_shared", lib().tms_tune_fp8_shared(
+        _dev(q_codes, torch.uint8), _dev(q_scales, torch.float32), nQ, nq, d, _dev(doc_codes, torch.uint8),
+        _dev(doc_scales, torch.float32), doc_codes.shape[0], _dev(doc_offsets, torch.int64),
+        _dev(doc_lengths, torch.int32), doc_offsets.shape[0], _dev(cand_ids, torch.int32), n_cand,
+        _dev(out, torch.float32), _stream_ptr(stream), ctypes.byref(n)))
+    return out, n.value
 
 
 def score_fp8_shared(q_codes, q_scales, doc_codes, doc_scales, doc_offsets, doc_lengths, cand_ids, out=None,
