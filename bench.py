@@ -468,6 +468,23 @@ def time_dense_e2e(w, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps, h2d, d2h
 
 
+def time_launch(fn, stream, reps, warmup=2):
+    """Mean CUDA-event time (ms) of `fn` launched `reps` times on `stream`."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def fp8_store_row(stream, hbm_peak):
     """1,000,000 docs (Nd~U[32,180], d=128) quantized to the FP8 store; 64
     fp16 queries, each over every document, in the shared schedule.
@@ -831,9 +848,16 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
     alg = iomodel.fp8_alg_bytes(w["tokens"], len(w["flat"]), N_QUERIES, NQ, D)
     qbytes = iomodel.quantize_alg_bytes(n_tok, D, 2)
     _, tp8 = tms.topk(out, w["c"], TOPK)
+    # the same launch after tms_tune_fp8 chose its configuration
+    _, n_cfg8 = tms.tune_fp8(qc, qsc, tc, tsc, w["off"], w["ln"], w["f"], w["c"], out=out, stream=stream)
+    tuned_ms = time_launch(lambda: tms.score_fp8(qc, qsc, tc, tsc, w["off"], w["ln"], w["f"], w["c"], out=out,
+                                                 stream=stream), stream, reps)
     rows["fp8_e4m3"] = {"docs_per_s": len(w["flat"]) / (kms * 1e-3), "kernel_ms": kms,
                         "achieved_gbs": alg / (kms * 1e-3) / 1e9, "frac_hbm": alg / (kms * 1e-3) / 1e9 / hbm_peak,
                         "quantize_corpus_ms": quant_ms, "quantize_gbs": qbytes / (quant_ms * 1e-3) / 1e9,
+                        "autotuned": {"kernel_ms": tuned_ms, "configs_timed": n_cfg8,
+                                      "frac_hbm": alg / (tuned_ms * 1e-3) / 1e9 / hbm_peak,
+                                      "speedup_vs_default": kms / tuned_ms},
                         # FP8 scores of query 0 against the FP64 oracle of the fp16 corpus they were
                         # quantized from: quantization error included (the FP8 store's quality)
                         "vs_fp64_oracle_query0": quality_vs_oracle(out[:N_CAND].cpu().numpy(), want16,
@@ -892,12 +916,29 @@ def secondary_rows(lengths, cands, stream, hbm_peak, sm_mhz):
                                    "vs_oracle_query0": quality_vs_oracle(out[:n3].cpu().numpy(), want0,
                                                                          tp.cpu().numpy()[0], 100),
                                    "oracle_query0": oracle_timing(n3, secs)}
+        if d in (64, 768):
+            # the same launches after the autotuner chose their configuration
+            # (the shared-list tuner also chooses the query group size)
+            if d == 64:
+                _, n_cfg = tms.tune_dense(Q, tok, off, ln, f, c, out=out, stream=stream)
+                t_ms = time_launch(lambda: tms.score_dense(Q, tok, off, ln, f, c, out=out, stream=stream), stream, 3)
+                rows_tuned = {"kernel_ms": t_ms, "configs_timed": n_cfg, "speedup_vs_default": kms / t_ms,
+                              "frac_hbm": alg / (t_ms * 1e-3) / 1e9 / hbm_peak}
+            _, n_cfg_sh = tms.tune_dense_shared(Q, tok, off, ln, f[:n3], out=out_sh, stream=stream)
+            t_sh = time_launch(lambda: tms.score_dense_shared(Q, tok, off, ln, f[:n3], out=out_sh, stream=stream),
+                               stream, 5)
+            rows_tuned_sh = {"kernel_ms": t_sh, "configs_timed": n_cfg_sh, "speedup_vs_default": kms_sh / t_sh,
+                             "tflops": fl / (t_sh * 1e-3) / 1e12}
         rows[f"dtile_shared_bf16_d{d}"] = {"docs_per_s": 32 * n3 / (kms_sh * 1e-3), "kernel_ms": kms_sh,
                                           "topk100_ms": e[3].elapsed_time(e[4]),
                                           "tflops": fl / (kms_sh * 1e-3) / 1e12,
                                           "corpus_reads_gbs": tok3 * d * 2 / (kms_sh * 1e-3) / 1e9,
                                           "vs_oracle_query0": quality_vs_oracle(out_sh[0].cpu().numpy(), want0,
                                                                                 tp_sh.cpu().numpy()[0], 100)}
+        if d in (64, 768):
+            rows[f"dtile_shared_bf16_d{d}"]["autotuned"] = rows_tuned_sh
+            if d == 64:
+                rows[f"dtile_bf16_d{d}"]["autotuned"] = rows_tuned
         del tok, off, ln, Q, f, out, out_sh
         torch.cuda.empty_cache()
     # fused PQ: 1M docs, M=16, K=256, dsub=8, 64 fp16 queries over all docs

@@ -75,7 +75,6 @@ struct Slot {
     float* d_rts = nullptr;
     int32_t* d_rtp = nullptr;
     int32_t* h_rtp = nullptr;
-    int64_t* h_cor = nullptr;
     int64_t* d_cor = nullptr;
     int32_t* d_cr = nullptr;
     float* d_scr = nullptr;
@@ -151,7 +150,6 @@ bool alloc_slot(tms_server* s, Slot& sl) {
             !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_rts), nb * rk * 4)) ||
             !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_rtp), nb * rk * 4)) ||
             !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_rtp), nb * rk * 4)) ||
-            !cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&sl.h_cor), (nb + 1) * 8)) ||
             !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_cor), (nb + 1) * 8)) ||
             !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_cr), nb * rk * 4)) ||
             !cuda_ok(cudaMalloc(reinterpret_cast<void**>(&sl.d_scr), nb * rk * 4)))
@@ -182,13 +180,57 @@ void free_slot(Slot& sl) {
     cudaFree(sl.d_rts);
     cudaFree(sl.d_rtp);
     cudaFreeHost(sl.h_rtp);
-    cudaFreeHost(sl.h_cor);
     cudaFree(sl.d_cor);
     cudaFree(sl.d_cr);
     cudaFree(sl.d_scr);
     for (int st = 0; st < kStores; ++st)
         if (sl.done[st]) cudaEventDestroy(sl.done[st]);
     (void)cudaGetLastError();
+}
+
+// FP8 requests: the CSR offsets of the shortlists, cor[i] = sum over
+// requests j < i of min(list length, rk), computed on the device from the
+// batch's own offsets (one CTA, nb <= 4096: four requests per thread, a
+// warp scan, then a scan of the warp totals).
+constexpr int kCsrThreads = 1024;
+__global__ void __launch_bounds__(kCsrThreads) shortlist_csr(const int64_t* __restrict__ co, int nb, int rk,
+                                                             int64_t* __restrict__ cor) {
+    __shared__ int64_t warp_tot[kCsrThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int64_t v[4], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * t + j;
+        const int64_t n = i < nb ? co[i + 1] - co[i] : 0;
+        v[j] = n < rk ? n : rk;
+        sum += v[j];
+    }
+    int64_t incl = sum;  // inclusive scan of the per-thread sums within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t x = warp_tot[lane], y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        warp_tot[lane] = y - x;  // exclusive: everything before warp `lane`
+    }
+    __syncthreads();
+    int64_t run = warp_tot[w] + incl - sum;  // everything before this thread's first request
+    if (t == 0) cor[0] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * t + j;
+        run += v[j];
+        if (i < nb) cor[i + 1] = run;
+    }
 }
 
 // FP8 requests: the ids of request i's shortlist -- the first cor[i+1] -
@@ -254,15 +296,17 @@ void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
                 // scored again on the dense store
                 const int rk = c.rescore_k;
                 rc = tms_topk(sl.d_sc[st], sl.d_co[st], nb, rk, sl.d_rts, sl.d_rtp, s->stream[st]);
-                sl.h_cor[0] = 0;
+                // the shortlists' CSR is built on the device; the host keeps
+                // only their total (the re-score call's n_cand)
+                int64_t total_r = 0;
                 for (int i = 0; i < nb; ++i) {
                     const int64_t n = static_cast<int64_t>(sl.reqs[st][i]->cands.size());
-                    sl.h_cor[i + 1] = sl.h_cor[i] + (n < rk ? n : rk);
+                    total_r += n < rk ? n : rk;
                 }
-                const int64_t total_r = sl.h_cor[nb];
-                if (rc == TMS_OK &&
-                    !cuda_ok(cudaMemcpyAsync(sl.d_cor, sl.h_cor, (nb + 1) * 8, cudaMemcpyHostToDevice, s->stream[st])))
-                    rc = TMS_ERR_CUDA;
+                if (rc == TMS_OK) {
+                    shortlist_csr<<<1, kCsrThreads, 0, s->stream[st]>>>(sl.d_co[st], nb, rk, sl.d_cor);
+                    if (!cuda_ok(cudaGetLastError())) rc = TMS_ERR_CUDA;
+                }
                 if (rc == TMS_OK) {
                     const int64_t n = static_cast<int64_t>(nb) * rk;
                     shortlist_ids<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s->stream[st]>>>(
