@@ -76,11 +76,12 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
  *
  * Limits: 1 <= nq <= 128; 8 <= d <= 1024 with d % 8 == 0 (16-byte rows);
  * 1 <= n_queries <= 4096; n_tokens < 2^31; queries, doc_tokens and every
- * index array 16-byte aligned.  For fp16/bf16 the whole query tile stays
- * in one CTA's shared memory next to at least two 16 KB stages: with nq
- * rounded up to a multiple of 32 and d to a multiple of 64, nq * d * 2
- * bytes must not exceed 188,416 (nq > 96 at d > 704 and nq > 64 at d > 960
- * return TMS_ERR_UNSUPPORTED).  fp16/bf16 run on the tensor cores
+ * index array 16-byte aligned.  For fp16/bf16 the query tile stays in
+ * shared memory when it fits beside the document stages (nq * d * 2 bytes,
+ * nq rounded up to 32 and d to 64, up to 188,416) and is otherwise streamed
+ * from L2 with each 128-byte dimension chunk of the documents (Section 3's
+ * dimension tiling applied to the query as well), so every nq and d above
+ * is supported.  fp16/bf16 run on the tensor cores
  * (tcgen05, fp32 accumulation in tensor memory); fp32 runs split TF32 on
  * the tensor cores (x = hi + lo, hi = x rounded to TF32; hi.hi + hi.lo +
  * lo.hi, FP32-level accuracy) when its doubled query tile fits, else an
@@ -129,8 +130,10 @@ tms_status tms_tune_dense(const void *queries, tms_dtype dtype, int n_queries, i
  *   other arguments as for tms_score_dense.
  *
  * Limits: fp16 / bf16 only, 1 <= nq <= 32, n_queries / group * n_cand
- * < 2^31; larger d uses smaller groups (down to 2) so the stacked query tile
- * fits shared memory.  fp32 or nq > 32 return TMS_ERR_UNSUPPORTED.
+ * < 2^31.  The stacked query tile of a group stays in shared memory when
+ * it fits and is otherwise streamed with each dimension chunk (groups of 8
+ * at every d); tms_tune_dense_shared may choose a smaller resident group
+ * instead.  fp32 or nq > 32 return TMS_ERR_UNSUPPORTED.
  */
 tms_status tms_score_dense_shared(const void *queries, tms_dtype dtype, int n_queries, int nq, int d,
                                   const void *doc_tokens, int64_t n_tokens,

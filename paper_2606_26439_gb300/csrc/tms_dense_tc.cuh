@@ -150,7 +150,7 @@ struct Args {
     int nq;
     int nchunks;     // ceil(d / chunk_elems)
     int stages;      // chunk stages in the ring
-    int qslots;
+    int qslots;      // resident query-tile slots; 0: the query is streamed with each chunk stage
     int bpc;         // 32-row query blocks per copy: ceil(nq / 32) token blocks, or the group's queries
     int reps;        // copies of the blocks stacked in M (1, 2 or 4); documents are dealt round-robin to them
     int rows_alloc;  // query rows held per dimension chunk: 32 * bpc * reps
@@ -188,15 +188,18 @@ constexpr int kFinWarpBytes = kFinRows * 33 * 4 + kFinRows * 8;
 // of str rows, so the document operand (N <= str) never reads past it.
 // TF: the query region and every stage have a lo twin right after them.
 // F8: per super-tile record slot, the row scale of every column.
+// Streamed query (qslots = 0, qrows = 128 H): no resident query region;
+// each chunk stage holds the str document rows, then the qrows query rows
+// of the same dimension chunk.
 __host__ __device__ inline Layout make_layout(int stages, int qslots, int nchunks, int rows_alloc, int str, int kind,
-                                              int kacc, bool fin) {
+                                              int kacc, bool fin, int qrows) {
     const bool f8 = kind == kE4M3;
     const int twin = kind == kTF32 ? 2 : 1;
     Layout L;
     L.q_off = 0;
     L.qlo_off = qslots * nchunks * rows_alloc * 128;
     L.stage_off = (twin * L.qlo_off + 1023) & ~1023;
-    L.stage_stride = twin * str * 128;
+    L.stage_stride = twin * (str + qrows) * 128;
     L.part_off = L.stage_off + stages * L.stage_stride;
     L.fin_off = L.part_off + 128;  // after [2 copies][2 parities][4 blocks] partial sums
     L.sc_off = L.fin_off + (fin ? kEpiWarps * kFinWarpBytes : 0);  // 128-byte aligned
@@ -360,7 +363,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     const int QS = a.qslots;
     const int NCH = a.nchunks;
     const int qslot_bytes = NCH * a.rows_alloc * 128;
-    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND, KACC, SH || a.bpc == 1);
+    const bool QSTREAM = QS == 0;  // the query rows come with every chunk stage
+    const Layout L = make_layout(S, QS, NCH, a.rows_alloc, STR, KIND, KACC, SH || a.bpc == 1, QSTREAM ? 128 * H : 0);
     const int SSTRIDE = L.stage_stride;  // bytes between stages (TF: hi, then lo)
 
     uint8_t* q_base = smem + L.q_off;
@@ -503,7 +507,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             // A new query's rows go to the next query slot.  The record is
             // published first: the MMA thread releases the old slot only
             // once it sees the new query.
-            if (st_q != cur_q) {
+            if (!QSTREAM && st_q != cur_q) {
                 const int slot = qi % QS;
                 if (!warp_wait(&qempty[slot], ((qi / QS) & 1) ^ 1, abort_flag, a.err, a.budget)) return false;
                 if (lane == 0) {
@@ -689,6 +693,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
     } else if (warp == kLoaderWarp) {
         // -------------------------------------------------------- loader
         const uint64_t pol_stream = policy_evict_first();
+        const uint64_t pol_keep = policy_evict_last();
         int s = 0;
         uint32_t ph = 0;
         int64_t issued = 0;
@@ -732,7 +737,23 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                     ok = false;
                     break;
                 }
-                if (lane == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(h.rows * 128));
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>((h.rows + (QSTREAM ? a.rows_alloc : 0)) * 128));
+                    if (QSTREAM) {
+                        // the query (group) rows of this chunk, laid out as one
+                        // chunk of the resident query region
+                        uint8_t* qdst = stage_base + s * SSTRIDE + STR * 128;
+                        for (int rp = 0; rp < a.reps; ++rp) {
+                            if (SH) {
+                                for (int g = 0; g < a.bpc; ++g)
+                                    tma_load_2d(qdst + (rp * a.bpc + g) * 32 * 128, &maps.q, kc * CE,
+                                                (h.q * a.group + g) * a.nq, &full[s], pol_keep);
+                            } else {
+                                tma_load_2d(qdst + rp * a.qbox * 128, &maps.q, kc * CE, h.q * a.nq, &full[s], pol_keep);
+                            }
+                        }
+                    }
+                }
                 __syncwarp();
                 if (has) tma_load_2d(stage_base + s * SSTRIDE + col * 128, dmap, kc * CE, row0, &full[s], pol_stream);
                 ++issued;
@@ -905,7 +926,7 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                 const StHdr x = slots[xs].h;
                 if (x.flags & kEnd) break;
                 mbar_arrive(&xempty[xs]);
-                if (x.q != cur_q) {
+                if (!QSTREAM && x.q != cur_q) {
                     if (cur_q >= 0) mma_commit(&qempty[qslot]);
                     qslot = qi % QS;
                     if (!mbar_wait(TF ? &qconv[qslot] : &qfull[qslot], (qi / QS) & 1, abort_flag, a.err, a.budget)) break;
@@ -930,8 +951,11 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
                     const uint64_t blo_desc = desc_sw128(smem_u32(stage_base + s * SSTRIDE + STAGE_BYTES));
 #pragma unroll
                     for (int h = 0; h < H; ++h) {
-                        const uint64_t qoff = static_cast<uint64_t>(((kc * a.rows_alloc + h * 128) * 128) >> 4);
-                        const uint64_t a_desc = q_desc + qoff;
+                        const uint64_t qoff =
+                            QSTREAM ? 0 : static_cast<uint64_t>(((kc * a.rows_alloc + h * 128) * 128) >> 4);
+                        const uint64_t a_desc =
+                            QSTREAM ? desc_sw128(smem_u32(stage_base + s * SSTRIDE + (STR + h * 128) * 128))
+                                    : q_desc + qoff;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint32_t accumulate = (kc > 0 || kk > 0) ? 1u : 0u;
@@ -1186,14 +1210,17 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
 // shape (Section 6.9, Table tile_ablation): rows per super-tile (documents
 // per MMA run) and CTAs per SM, copies of the query blocks stacked in M
 // (query tokens per epilogue warp), at most `stages` chunk stages (0: as
-// many as fit) and `qslots` query-tile slots (0: whichever gives more
-// stages).
+// many as fit), `qslots` resident query-tile slots (0: whichever gives
+// more stages), or (qstream) the query streamed with each chunk stage
+// instead of held resident -- the paper's dimension tiling applied to the
+// query tile too.
 struct Config {
     int str;
     int ctas;
     int reps;
     int stages;
     int qslots;
+    int qstream;
 };
 
 // Configurations chosen by the autotuner, per device and launch shape.
@@ -1229,16 +1256,16 @@ inline TuneKey group_key(int device, int kind, int nchunks, int n_queries) {
 template <int H, bool SH, int KIND>
 inline int config_shapes(Config* out) {
     if (H == 2 || KIND == kTF32) {
-        out[0] = {128, 1, 0, 0, 0};
+        out[0] = {128, 1, 0, 0, 0, 0};
         return 1;
     }
     if (KIND == kPQ) {  // one query half
-        out[0] = {256, 1, 0, 0, 0};
+        out[0] = {256, 1, 0, 0, 0, 0};
         return 1;
     }
-    out[0] = {256, 1, 0, 0, 0};
-    out[1] = {128, 1, 0, 0, 0};
-    out[2] = {128, 2, 0, 0, 0};
+    out[0] = {256, 1, 0, 0, 0, 0};
+    out[1] = {128, 1, 0, 0, 0, 0};
+    out[2] = {128, 2, 0, 0, 0, 0};
     return 3;
 }
 
@@ -1254,7 +1281,8 @@ inline int config_shapes(Config* out) {
 // and a.bpc / a.qbox: per-query ceil(nq / 32) and 32 bpc, shared mode the
 // group size and 32.  `force` (the autotuner's) overrides the choice;
 // TMS_ERR_UNSUPPORTED when it does not fit.
-// The resolved launch configuration: every field of Config set.
+// The resolved launch configuration: every field of Config set (qslots 0:
+// the query is streamed).
 struct Plan {
     int str, ctas, reps, stages, qslots;
     bool operator==(const Plan& o) const {
@@ -1275,15 +1303,17 @@ tms_status plan_tc(const DeviceInfo& dev, const Args& a, const Config* force, Pl
     // the query-slot count (2, else 1) that gives the most stages; the
     // plan fits with at least 4 chunk stages (2 with one CTA per SM).
     const int max_reps = H == 2 ? 1 : (a.bpc == 3 ? 1 : 4 / a.bpc);
-    auto fits = [&](int str, int ctas, int rp, int need, int& stages, int& qslots, int cap = 0, int want_qs = 0) {
+    auto fits = [&](int str, int ctas, int rp, int need, int& stages, int& qslots, int cap = 0, int want_qs = 0,
+                    bool stream = false) {
         if (rp < 1 || rp > max_reps) return false;
+        if (stream && (TF || PQ)) return false;  // their query tiles are split / decompressed in place
         const int limit = ctas == 2 ? dev.smem_per_sm / 2 - dev.smem_reserved - 1024
                                     : std::min(kSmemLimit, dev.max_smem_optin) - 1024;
         int best = -1;
-        for (int qs = 2; qs >= 1; --qs) {
-            if (want_qs && qs != want_qs) continue;
-            const Layout L0 =
-                make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, acc_count(H, str, ctas), SH || a.bpc == 1);
+        for (int qs = stream ? 0 : 2; qs >= (stream ? 0 : 1); --qs) {
+            if (!stream && want_qs && qs != want_qs) continue;
+            const Layout L0 = make_layout(0, qs, a.nchunks, 32 * a.bpc * rp, str, KIND, acc_count(H, str, ctas),
+                                          SH || a.bpc == 1, stream ? 128 * H : 0);
             int sts = std::min(kMaxStages, (limit - L0.total) / (L0.stage_stride + 24));
             if (cap > 0 && sts > cap) sts = cap;
             if (sts > best) {
@@ -1305,7 +1335,7 @@ tms_status plan_tc(const DeviceInfo& dev, const Args& a, const Config* force, Pl
         return false;
     };
     int stages = 0, qslots = 1, reps = 0, str = 0, ctas = 0;
-    Config tuned{0, 0, 0, 0, 0};
+    Config tuned{0, 0, 0, 0, 0, 0};
     if (!force) {
         std::lock_guard<std::mutex> lk(tune_mutex());
         const auto it = tune_table().find(TuneKey{dev.ordinal, KIND, H, SH ? 1 : 0, a.nchunks, a.bpc});
@@ -1313,7 +1343,7 @@ tms_status plan_tc(const DeviceInfo& dev, const Args& a, const Config* force, Pl
     }
     const Config* want = force ? force : (tuned.ctas ? &tuned : nullptr);
     if (want) {
-        if (fits(want->str, want->ctas, want->reps, 2, stages, qslots, want->stages, want->qslots)) {
+        if (fits(want->str, want->ctas, want->reps, 2, stages, qslots, want->stages, want->qslots, want->qstream != 0)) {
             str = want->str;
             ctas = want->ctas;
             reps = want->reps;
@@ -1339,6 +1369,18 @@ tms_status plan_tc(const DeviceInfo& dev, const Args& a, const Config* force, Pl
             if (plan(256, 1, stages, qslots, reps)) str = 256, ctas = 1;
             else if (plan(128, 1, stages, qslots, reps)) str = 128, ctas = 1;
         }
+    }
+    if (ctas == 0 && !TF && !PQ) {
+        // the resident query tile leaves no room: stream it with every chunk
+        // stage (the copies a 128-row half needs, at least two stages)
+        const int sh[2][2] = {{H == 2 ? 128 : 256, 1}, {128, 1}};
+        for (int i = 0; i < 2 && ctas == 0; ++i)
+            for (int rp = max_reps; rp >= 1 && ctas == 0; rp /= 2)
+                if (fits(sh[i][0], sh[i][1], rp, 2, stages, qslots, 0, 0, true)) {
+                    str = sh[i][0];
+                    ctas = sh[i][1];
+                    reps = rp;
+                }
     }
     if (ctas == 0) return TMS_ERR_UNSUPPORTED;
     *out = Plan{str, ctas, reps, stages, qslots};
@@ -1383,8 +1425,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     a.idesc = make_idesc(128, 0, TF ? 2u : ((!F8 && dtype == TMS_BF16) ? 1u : 0u));
     a.stages = stages;
     a.qslots = qslots;
-    const Layout L =
-        make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND, acc_count(H, str, ctas), SH || a.bpc == 1);
+    const Layout L = make_layout(stages, qslots, a.nchunks, a.rows_alloc, str, KIND, acc_count(H, str, ctas),
+                                 SH || a.bpc == 1, qslots == 0 ? 128 * H : 0);
     const int smem = L.total + 1024;
     void (*kern)(const Maps, const Args);
     if constexpr (H == 2) {
@@ -1405,8 +1447,9 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
 }
 
 // Autotuner: time every configuration this instantiation has kernels for
-// that fits the launch -- super-tile shape x copies x query slots (1 / 2) x
-// stage cap (all that fit / 4), skipping caps that change nothing -- with 3
+// that fits the launch -- super-tile shape x copies x query tile (resident
+// in 1 or 2 slots, or streamed) x stage cap (all that fit / 4), skipping
+// plans already timed -- with 3
 // timed launches after one warm-up each (CUDA events on `stream`), remember
 // the fastest for the launch shape, and report how many were timed and the
 // best mean time per launch.  Each launch writes the scores, so the last
@@ -1424,16 +1467,16 @@ tms_status tune_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype, 
         return TMS_ERR_CUDA;
     }
     float best_ms = 0.f;
-    Config best{0, 0, 0, 0, 0};
+    Config best{0, 0, 0, 0, 0, 0};
     int timed = 0;
     tms_status st = TMS_OK;
     Plan seen[64];
     int nseen = 0;
     for (int i = 0; i < ns && st == TMS_OK; ++i) {
         for (int rp = 4; rp >= 1 && st == TMS_OK; rp /= 2) {
-            for (int qs = 1; qs <= 2 && st == TMS_OK; ++qs) {
+            for (int qs = 0; qs <= 2 && st == TMS_OK; ++qs) {  // 0: the query streamed
                 for (int cap = 0; cap <= 4 && st == TMS_OK; cap += 4) {
-                    const Config c{shapes[i].str, shapes[i].ctas, rp, cap, qs};
+                    const Config c{shapes[i].str, shapes[i].ctas, rp, cap, qs, qs == 0 ? 1 : 0};
                     Plan pl;
                     if (plan_tc<H, SH, KIND>(dev, a, &c, &pl) != TMS_OK) continue;
                     bool dup = false;

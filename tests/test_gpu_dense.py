@@ -17,7 +17,8 @@ from tests._common import assert_scores_close, assert_topk_consistent, assert_to
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(32, 128), (1, 64), (7, 72), (33, 200), (64, 384), (128, 128), (32, 768), (16, 8), (96, 256), (96, 576),
-          (64, 512), (128, 576), (96, 832), (64, 1024), (128, 704), (96, 960)]
+          (64, 512), (128, 576), (96, 832), (64, 1024), (128, 704), (96, 960), (128, 768), (96, 1024),
+          (128, 1024)]
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16", "f32"])
@@ -38,19 +39,6 @@ def test_dense_edge_grid(cuda_lib, dtype, nq, d):
     assert flags & tms.TMS_DEVERR_BAD_ID
     assert not flags & tms.TMS_DEVERR_TIMEOUT
     assert not flags & tms.TMS_DEVERR_BAD_CSR
-
-
-@pytest.mark.parametrize("nq,d", [(128, 768), (128, 1024), (96, 1024)])
-def test_dense_query_tile_too_large_is_unsupported(cuda_lib, nq, d):
-    """The whole fp16 query tile must fit one CTA's shared memory beside two
-    16 KB stages of 128-row super-tiles: nq * d * 2 bytes (nq rounded to 32,
-    d to 64) above 188,416 is refused with TMS_ERR_UNSUPPORTED."""
-    from paper_2606_26439_gb300 import tms
-    tok, off, ln = synth.dense_corpus(4, np.array([3, 4, 5, 6], np.int32), d, "f16", 9)
-    Q = synth.queries(1, nq, d, "f16", 9)
-    with pytest.raises(tms.TmsError) as e:
-        gc.gpu_dense(Q, tok, off, ln, [np.array([0, 1], np.int32)])
-    assert e.value.status == tms.TMS_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16", "f32"])
