@@ -34,10 +34,11 @@ def _oracle_all(Q, tok, off, ln, cand):
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 @pytest.mark.parametrize("n_queries,nq,d", [(2, 32, 128), (3, 7, 72), (5, 32, 200), (8, 1, 64), (9, 32, 128),
-                                            (17, 16, 256), (12, 32, 768), (11, 32, 512)])
+                                            (17, 16, 256), (12, 32, 768), (11, 32, 512), (9, 32, 1024)])
 def test_shared_parity_edge_corpus(cuda_lib, dtype, n_queries, nq, d):
     """Groups of 2/4/8 queries (a partial last group included), ragged and
-    empty documents, duplicate and out-of-range ids."""
+    empty documents, duplicate and out-of-range ids; at d >= 512 the
+    group-of-8 query tile is streamed with each dimension chunk."""
     from paper_2606_26439_gb300 import tms
     seed = 3000 + n_queries * 13 + d
     tok, off, ln = gc.edge_corpus(d, dtype, seed, n_random=60)
