@@ -121,22 +121,41 @@ __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm)
                 }
             }
             __syncthreads();
+            // The largest digit whose suffix count (keys with that digit or
+            // a larger one) reaches `need`: thread t < 256 holds the count
+            // of digit 255 - t, an inclusive scan over the first 8 warps
+            // gives the suffix counts, and the one thread whose bin crosses
+            // `need` records the digit and what is still needed below it.
+            if (threadIdx.x == 0) {
+                sm.digit = 0;
+                sm.need = need;
+            }
             if (threadIdx.x < 256) {
-                uint32_t tot = 0;
-                for (int w = 0; w < kWarps; ++w) tot += sm.whist[w][threadIdx.x];
-                sm.hist[threadIdx.x] = tot;
+                const int dgt = 255 - threadIdx.x;
+                int tot = 0;
+                for (int w = 0; w < kWarps; ++w) tot += static_cast<int>(sm.whist[w][dgt]);
+                int inc = tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += v;
+                }
+                if (lane == 31) sm.scan_buf[warp] = inc;
+                sm.hist[dgt] = static_cast<uint32_t>(inc);  // within-warp suffix count, completed below
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                // largest digit whose suffix count reaches `need`
-                int acc = 0;
-                int dgt = 255;
-                for (; dgt >= 0; --dgt) {
-                    if (acc + static_cast<int>(sm.hist[dgt]) >= need) break;
-                    acc += static_cast<int>(sm.hist[dgt]);
+            if (threadIdx.x < 256) {
+                const int dgt = 255 - threadIdx.x;
+                int before = 0;  // keys with a digit above this warp's bins
+                for (int w = 0; w < warp; ++w) before += sm.scan_buf[w];
+                const int incl = before + static_cast<int>(sm.hist[dgt]);
+                const int tot = static_cast<int>(sm.hist[dgt]) -
+                                (lane > 0 ? static_cast<int>(sm.hist[dgt + 1]) : 0);  // this digit's count
+                const int excl = incl - tot;
+                if (incl >= need && excl < need) {
+                    sm.digit = static_cast<uint32_t>(dgt);
+                    sm.need = need - excl;
                 }
-                sm.digit = static_cast<uint32_t>(dgt < 0 ? 0 : dgt);
-                sm.need = need - acc;
             }
             __syncthreads();
             prefix |= sm.digit << shift;
