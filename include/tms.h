@@ -83,8 +83,9 @@ typedef enum { TMS_F16 = 0, TMS_BF16 = 1, TMS_F32 = 2 } tms_dtype;
  * dimension tiling applied to the query as well), so every nq and d above
  * is supported.  fp16/bf16 run on the tensor cores
  * (tcgen05, fp32 accumulation in tensor memory); fp32 runs split TF32 on
- * the tensor cores (x = hi + lo, hi = x rounded to TF32; hi.hi + hi.lo +
- * lo.hi, FP32-level accuracy) when its doubled query tile fits, else an
+ * the tensor cores (x = hi + lo, hi = x with its 13 low mantissa bits
+ * cleared, lo the exact rest; hi.hi + hi.lo + lo.hi, FP32-level accuracy)
+ * when its doubled query tile fits, else an
  * exact fp32 CUDA-core kernel (any supported nq, d).  A candidate with a bad id or row range scores NaN and sets
  * TMS_DEVERR_BAD_ID / TMS_DEVERR_BAD_RANGE.
  */

@@ -4,9 +4,10 @@
 // for every candidate of every query, in one persistent launch, with the
 // document and query rows stored as fp16 / bf16, as FP8 E4M3 codes with one
 // fp32 scale per row (F8), or as fp32 scored by split TF32 (TF: each
-// operand x = hi + lo with hi = x rounded to TF32 and lo the exact rest;
-// hi.hi + hi.lo + lo.hi on the tensor cores, the lo.lo term of relative
-// size 2^-22 dropped -- FP32-level accuracy).
+// operand x = hi + lo with hi = x with its 13 low mantissa bits cleared --
+// the value a kind::tf32 MMA reads from an fp32 element -- and lo = x - hi
+// exact; hi.hi + hi.lo + lo.hi on the tensor cores, the lo.lo term of
+// relative size below 2^-20 dropped -- FP32-level accuracy).
 //
 // Orientation: the MMA computes S^T = Q D^T, query tokens along M (tensor-
 // memory lanes, one per epilogue thread) and document rows along N
@@ -278,13 +279,9 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
     }
 }
 
-// x rounded to the nearest TF32 value (ties away from zero), as an fp32
-// bit pattern with the low 13 mantissa bits zero.
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
+// x with its 13 low mantissa bits cleared: the TF32 value a kind::tf32 MMA
+// reads from an fp32 element.
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
 
 // Maxima of the four 8-column sub-blocks of 32 accumulator columns.
 // Document tiles start on 8-column boundaries, so a tile covers whole
@@ -858,11 +855,12 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         }
     } else if (TF && warp > kLoaderWarp) {
         // ------------------------------------------------------ splitters
-        // Split each new query tile and every landed chunk stage into
-        // hi = x rounded to TF32 (in place) and lo = x - hi (exact) in the
-        // twin region, then publish the split to the MMA thread.  Elements
-        // are independent, so the 128-byte swizzle needs no decoding: hi and
-        // lo keep the same byte positions.
+        // Split each new query tile and every landed chunk stage: the MMA
+        // reads an fp32 element as hi = tf32_trunc(x), so x stays in place
+        // as its own hi part and lo = x - hi (exact, |lo| < 2^-10 |x|) goes
+        // to the twin region; then publish the split to the MMA thread.
+        // Elements are independent, so the 128-byte swizzle needs no
+        // decoding: x and lo keep the same byte positions.
         const int tid = (warp - kLoaderWarp - 1) * 32 + lane;
         constexpr int kSplitThreads = 32 * kSplitWarps;
         auto split = [&](uint8_t* hi_p, uint8_t* lo_p, int bytes) {
@@ -870,9 +868,8 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
             float4* lv = reinterpret_cast<float4*>(lo_p);
             for (int v = tid; v < bytes / 16; v += kSplitThreads) {
                 const float4 x = hv[v];
-                const float4 h = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
-                lv[v] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-                hv[v] = h;
+                lv[v] = make_float4(x.x - tf32_trunc(x.x), x.y - tf32_trunc(x.y), x.z - tf32_trunc(x.z),
+                                    x.w - tf32_trunc(x.w));
             }
             fence_proxy_async_smem();  // generic-proxy writes, read next by the tensor cores
             __syncwarp();
