@@ -31,7 +31,7 @@
 namespace tms {
 namespace topk {
 
-constexpr int kThreads = 1024;
+constexpr int kThreads = 1024;  // four quarters of 256 threads: the histogram sums below rely on it
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxK = 1024;
 constexpr int kMaxSlices = 64;
@@ -60,8 +60,13 @@ struct Smem {
     int scan_buf[33];
     uint32_t digit;
     int need;
+    int eq;  // keys equal to the k-th largest (set by the last radix pass)
     int count;
 };
+
+// Elements a thread reads ahead of processing them, so that their loads
+// overlap instead of each waiting in turn.
+constexpr int kAhead = 8;
 
 // Exclusive scan of one int per thread over the CTA; returns the prefix and
 // writes the total to *total.  `buf` holds kWarps + 1 ints.
@@ -108,16 +113,24 @@ __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm)
         for (int shift = 24; shift >= 0; shift -= 8) {
             for (int b = threadIdx.x; b < kWarps * 256; b += kThreads) (&sm.whist[0][0])[b] = 0;
             __syncthreads();
-            for (int base = 0; base < n; base += kThreads) {
-                const int i = base + threadIdx.x;
-                const bool in = i < n;
-                const uint32_t key = in ? key_at(i) : 0u;
-                const bool match = in && ((key & mask) == prefix);
-                const unsigned active = __ballot_sync(0xffffffffu, match);
-                if (match) {
-                    const uint32_t dgt = (key >> shift) & 255u;
-                    const unsigned peers = __match_any_sync(active, dgt);
-                    if (lane == __ffs(peers) - 1) sm.whist[warp][dgt] += __popc(peers);
+            for (int base = 0; base < n; base += kAhead * kThreads) {
+                uint32_t keys[kAhead];
+#pragma unroll
+                for (int u = 0; u < kAhead; ++u) {
+                    const int i = base + u * kThreads + threadIdx.x;
+                    keys[u] = i < n ? key_at(i) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kAhead; ++u) {
+                    const int i = base + u * kThreads + threadIdx.x;
+                    const uint32_t key = keys[u];
+                    const bool match = i < n && ((key & mask) == prefix);
+                    const unsigned active = __ballot_sync(0xffffffffu, match);
+                    if (match) {
+                        const uint32_t dgt = (key >> shift) & 255u;
+                        const unsigned peers = __match_any_sync(active, dgt);
+                        if (lane == __ffs(peers) - 1) sm.whist[warp][dgt] += __popc(peers);
+                    }
                 }
             }
             __syncthreads();
@@ -129,11 +142,25 @@ __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm)
             if (threadIdx.x == 0) {
                 sm.digit = 0;
                 sm.need = need;
+                sm.eq = -1;
             }
+            // the 32 warp histograms summed in two steps: four quarters of
+            // 8 warps in parallel (each quarter's sum left in its first
+            // warp's row), then the four quarter sums
+            {
+                const int qtr = threadIdx.x >> 8;
+                const int dgt = 255 - (threadIdx.x & 255);
+                uint32_t t = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps / 4; ++w) t += sm.whist[qtr * (kWarps / 4) + w][dgt];
+                sm.whist[qtr * (kWarps / 4)][dgt] = t;  // only this thread reads or writes column dgt of the quarter
+            }
+            __syncthreads();
             if (threadIdx.x < 256) {
                 const int dgt = 255 - threadIdx.x;
                 int tot = 0;
-                for (int w = 0; w < kWarps; ++w) tot += static_cast<int>(sm.whist[w][dgt]);
+#pragma unroll
+                for (int qtr = 0; qtr < 4; ++qtr) tot += static_cast<int>(sm.whist[qtr * (kWarps / 4)][dgt]);
                 int inc = tot;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -155,6 +182,7 @@ __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm)
                 if (incl >= need && excl < need) {
                     sm.digit = static_cast<uint32_t>(dgt);
                     sm.need = need - excl;
+                    sm.eq = tot;  // after the last pass: the keys equal to T
                 }
             }
             __syncthreads();
@@ -165,24 +193,47 @@ __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm)
         }
     }
     // prefix is now the k-th largest key T (when !select_all); `need` keys
-    // equal to T are taken, lowest positions first.
+    // equal to T are taken, lowest positions first.  When every key equal
+    // to T is taken (always, unless T is tied across the cut) no ranking is
+    // needed: the survivors are the same set whatever order they arrive in,
+    // and the sort below fixes their order.
+    const bool all_eq = select_all || sm.eq == need;
     if (threadIdx.x == 0) sm.count = 0;
     __syncthreads();
-    int taken_eq = 0;
-    for (int base = 0; base < n; base += kThreads) {
-        const int i = base + threadIdx.x;
-        const bool in = i < n;
-        const uint32_t key = in ? key_at(i) : 0u;
-        const bool gt = in && (select_all || key > prefix);
-        const bool eq = in && !select_all && key == prefix;
-        int eq_total = 0;
-        const int rank = block_exclusive_scan(eq ? 1 : 0, sm.scan_buf, &eq_total);
-        const bool take = gt || (eq && taken_eq + rank < need);
-        if (take) {
-            const int slot = atomicAdd(&sm.count, 1);
-            if (slot < kMaxK) sm.sel[slot] = pack(key, pos_at(i));
+    if (all_eq) {
+        for (int base = 0; base < n; base += kAhead * kThreads) {
+            uint32_t keys[kAhead];
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u) {
+                const int i = base + u * kThreads + threadIdx.x;
+                keys[u] = i < n ? key_at(i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u) {
+                const int i = base + u * kThreads + threadIdx.x;
+                if (i < n && (select_all || keys[u] >= prefix)) {
+                    const int slot = atomicAdd(&sm.count, 1);
+                    if (slot < kMaxK) sm.sel[slot] = pack(keys[u], pos_at(i));
+                }
+            }
         }
-        taken_eq += eq_total;
+    } else {
+        int taken_eq = 0;
+        for (int base = 0; base < n; base += kThreads) {
+            const int i = base + threadIdx.x;
+            const bool in = i < n;
+            const uint32_t key = in ? key_at(i) : 0u;
+            const bool gt = in && key > prefix;
+            const bool eq = in && key == prefix;
+            int eq_total = 0;
+            const int rank = block_exclusive_scan(eq ? 1 : 0, sm.scan_buf, &eq_total);
+            const bool take = gt || (eq && taken_eq + rank < need);
+            if (take) {
+                const int slot = atomicAdd(&sm.count, 1);
+                if (slot < kMaxK) sm.sel[slot] = pack(key, pos_at(i));
+            }
+            taken_eq += eq_total;
+        }
     }
     __syncthreads();
     const int cnt = min(sm.count, kMaxK);
