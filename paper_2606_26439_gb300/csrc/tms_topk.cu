@@ -9,7 +9,9 @@
 //      to the top-k;
 //   3. one pass in element order keeps every key > T and the first keys ==
 //      T, using a block-wide ordered scan -- the lowest positions, because
-//      equal keys always appear in ascending position order;
+//      equal keys always appear in ascending position order; when every
+//      key equal to T is kept (no tie across the cut) the pass keeps every
+//      key >= T in any order, without the scan;
 //   4. a bitonic sort orders the <= k survivors by (key desc, position asc).
 //
 // tms_topk: one CTA per query selects from the whole list.
