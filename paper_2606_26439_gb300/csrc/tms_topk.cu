@@ -6,7 +6,9 @@
 //   2. a byte-wise radix select (four histogram passes, warp-private
 //      histograms filled with match_any so equal digits cost one update)
 //      finds the k-th largest key T and how many keys equal to T belong
-//      to the top-k;
+//      to the top-k; a list of up to 12 x 1024 keys is read once and kept
+//      in registers for all passes, a longer one is re-read per pass with
+//      eight loads in flight per thread;
 //   3. one pass in element order keeps every key > T and the first keys ==
 //      T, using a block-wide ordered scan -- the lowest positions, because
 //      equal keys always appear in ascending position order; when every
@@ -67,8 +69,11 @@ struct Smem {
 };
 
 // Elements a thread reads ahead of processing them, so that their loads
-// overlap instead of each waiting in turn.
+// overlap instead of each waiting in turn; a list of at most
+// kResident * kThreads elements is instead read once and kept in registers
+// for every pass.
 constexpr int kAhead = 8;
+constexpr int kResident = 12;
 
 // Exclusive scan of one int per thread over the CTA; returns the prefix and
 // writes the total to *total.  `buf` holds kWarps + 1 ints.
@@ -104,26 +109,37 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* buf, int* total)
 // pos_at(i); elements with equal keys must come in ascending position
 // order).  Leaves the min(k, n) survivors sorted by (key desc, position
 // asc) in sm.sel[0 .. count) and returns count.  Every thread of the CTA
-// calls it.
-template <class KeyAt, class PosAt>
+// calls it.  RES: n <= kResident * kThreads, keys held in registers.
+template <bool RES, class KeyAt, class PosAt>
 __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int A = RES ? kResident : kAhead;  // elements per thread per step
     uint32_t prefix = 0, mask = 0;
     int need = min(k, n);  // how many of the keys matching prefix/mask still to take
     const bool select_all = n <= k;
+    uint32_t rkeys[RES ? kResident : 1];
+    if constexpr (RES) {
+#pragma unroll
+        for (int u = 0; u < kResident; ++u) {
+            const int i = u * kThreads + threadIdx.x;
+            rkeys[u] = i < n ? key_at(i) : 0u;
+        }
+    }
     if (!select_all) {
         for (int shift = 24; shift >= 0; shift -= 8) {
             for (int b = threadIdx.x; b < kWarps * 256; b += kThreads) (&sm.whist[0][0])[b] = 0;
             __syncthreads();
-            for (int base = 0; base < n; base += kAhead * kThreads) {
-                uint32_t keys[kAhead];
+            for (int base = 0; base < n; base += A * kThreads) {
+                uint32_t keys[A];
 #pragma unroll
-                for (int u = 0; u < kAhead; ++u) {
+                for (int u = 0; u < A; ++u) {
                     const int i = base + u * kThreads + threadIdx.x;
-                    keys[u] = i < n ? key_at(i) : 0u;
+                    if constexpr (RES) keys[u] = rkeys[u];
+                    else keys[u] = i < n ? key_at(i) : 0u;
                 }
 #pragma unroll
-                for (int u = 0; u < kAhead; ++u) {
+                for (int u = 0; u < A; ++u) {
+                    if (RES && u * kThreads >= n) break;  // the same for the whole CTA
                     const int i = base + u * kThreads + threadIdx.x;
                     const uint32_t key = keys[u];
                     const bool match = i < n && ((key & mask) == prefix);
@@ -203,15 +219,17 @@ __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm)
     if (threadIdx.x == 0) sm.count = 0;
     __syncthreads();
     if (all_eq) {
-        for (int base = 0; base < n; base += kAhead * kThreads) {
-            uint32_t keys[kAhead];
+        for (int base = 0; base < n; base += A * kThreads) {
+            uint32_t keys[A];
 #pragma unroll
-            for (int u = 0; u < kAhead; ++u) {
+            for (int u = 0; u < A; ++u) {
                 const int i = base + u * kThreads + threadIdx.x;
-                keys[u] = i < n ? key_at(i) : 0u;
+                if constexpr (RES) keys[u] = rkeys[u];
+                else keys[u] = i < n ? key_at(i) : 0u;
             }
 #pragma unroll
-            for (int u = 0; u < kAhead; ++u) {
+            for (int u = 0; u < A; ++u) {
+                if (RES && u * kThreads >= n) break;
                 const int i = base + u * kThreads + threadIdx.x;
                 if (i < n && (select_all || keys[u] >= prefix)) {
                     const int slot = atomicAdd(&sm.count, 1);
@@ -264,6 +282,14 @@ __device__ int select_sorted(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm)
     return cnt;
 }
 
+// select_sorted with the keys held in registers when the list is short
+// enough (n is the same for the whole CTA).
+template <class KeyAt, class PosAt>
+__device__ int select_any(int n, int k, KeyAt key_at, PosAt pos_at, Smem& sm) {
+    return n <= kResident * kThreads ? select_sorted<true>(n, k, key_at, pos_at, sm)
+                                     : select_sorted<false>(n, k, key_at, pos_at, sm);
+}
+
 // The list [c0, c1) of query q, checked: a negative start or a decreasing
 // pair is a CSR error -- flagged (when err is given), and the list read as
 // empty (negative start) or clamped to its start, never read below it.
@@ -307,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t c0, c1;
     query_list(cand_offsets, q, err, &c0, &c1);
     const float* s = scores + c0;
-    const int cnt = select_sorted(
+    const int cnt = select_any(
         list_len(c0, c1), k, [&](int i) { return score_key(s[i]); }, [](int i) { return static_cast<uint32_t>(i); },
         sm);
     write_out(sm, cnt, k, s, out_scores + static_cast<int64_t>(q) * k, out_pos + static_cast<int64_t>(q) * k);
@@ -326,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t len = list_len(c0, c1);
     const int64_t a = len * sl / S, b = len * (sl + 1) / S;  // slice [a, b) of the list
     const float* s = scores + c0 + a;
-    const int cnt = select_sorted(
+    const int cnt = select_any(
         static_cast<int>(b - a), k, [&](int i) { return score_key(s[i]); },
         [&](int i) { return static_cast<uint32_t>(a + i); }, sm);
     unsigned long long* dst = ws + static_cast<int64_t>(blockIdx.x) * k;
@@ -343,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t c0, c1;
     query_list(cand_offsets, q, nullptr, &c0, &c1);
     const unsigned long long* e = ws + static_cast<int64_t>(q) * S * k;
-    const int cnt = select_sorted(
+    const int cnt = select_any(
         S * k, k, [&](int i) { return key_of(e[i]); }, [&](int i) { return pos_of(e[i]); }, sm);
     write_out(sm, cnt, k, scores + c0, out_scores + static_cast<int64_t>(q) * k,
               out_pos + static_cast<int64_t>(q) * k);
