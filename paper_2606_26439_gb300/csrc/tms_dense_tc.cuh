@@ -438,6 +438,10 @@ __global__ void __launch_bounds__(kernel_threads(KIND), CTAS)
         tmem_alloc(tmem_slot, TCOLS);
         tmem_relinquish();
     }
+    // Nothing above reads global memory: the previous kernel of the stream
+    // may still be running until here.
+    griddep_wait();
+    griddep_launch_dependents();
     if constexpr (PQ) {
         // the codebook, rounded to fp16 (nearest even), for all 256 codes:
         // codes >= pq_k get zeros
@@ -1452,8 +1456,8 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
-    kern<<<static_cast<unsigned>(grid), kernel_threads(KIND), smem, stream>>>(maps, a);
-    return launch_status(cudaGetLastError());
+    return launch_status(launch_dependent(kern, dim3(static_cast<unsigned>(grid)), dim3(kernel_threads(KIND)),
+                                          static_cast<size_t>(smem), stream, maps, a));
 }
 
 // Autotuner: time every configuration this instantiation has kernels for

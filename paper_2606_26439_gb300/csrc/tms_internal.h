@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/tms.h"
 
 namespace tms {
@@ -42,6 +44,29 @@ inline tms_status launch_status(cudaError_t e) {
     if (e == cudaSuccess) return TMS_OK;
     (void)cudaGetLastError();  // clear the sticky-free launch error
     return TMS_ERR_CUDA;
+}
+
+// Launch with programmatic stream serialization: the kernel may be
+// scheduled while the previous kernel of the stream is finishing (once all
+// of its CTAs have issued griddepcontrol.launch_dependents or exited), and
+// runs only its own set-up (barriers, tensor memory, descriptor prefetch)
+// before griddepcontrol.wait, which returns when that kernel has completed
+// and its memory is visible.  Every kernel launched this way waits before
+// its first global-memory access.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 }  // namespace tms

@@ -329,6 +329,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     topk_kernel(const float* __restrict__ scores, const int64_t* __restrict__ cand_offsets, int k,
                 float* __restrict__ out_scores, int32_t* __restrict__ out_pos, unsigned int* err) {
     __shared__ Smem sm;
+    griddep_wait();
+    griddep_launch_dependents();
     const int q = blockIdx.x;
     int64_t c0, c1;
     query_list(cand_offsets, q, err, &c0, &c1);
@@ -345,6 +347,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     topk_slice_kernel(const float* __restrict__ scores, const int64_t* __restrict__ cand_offsets, int k, int S,
                       unsigned long long* __restrict__ ws, unsigned int* err) {
     __shared__ Smem sm;
+    griddep_wait();
+    griddep_launch_dependents();
     const int q = blockIdx.x / S;
     const int sl = blockIdx.x - q * S;
     int64_t c0, c1;
@@ -365,6 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const unsigned long long* __restrict__ ws, float* __restrict__ out_scores,
                       int32_t* __restrict__ out_pos) {
     __shared__ Smem sm;
+    griddep_wait();
+    griddep_launch_dependents();
     const int q = blockIdx.x;
     int64_t c0, c1;
     query_list(cand_offsets, q, nullptr, &c0, &c1);
@@ -401,9 +407,9 @@ extern "C" tms_status tms_topk(const float* scores, const int64_t* cand_offsets,
     DeviceInfo dev;
     tms_status st = current_device(&dev);
     if (st != TMS_OK) return st;
-    topk::topk_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(scores, cand_offsets, topk,
-                                                                                        out_scores, out_pos, dev.err);
-    return launch_status(cudaGetLastError());
+    return launch_status(launch_dependent(topk::topk_kernel, dim3(static_cast<unsigned>(n_queries)),
+                                          dim3(topk::kThreads), 0, stream, scores, cand_offsets, topk, out_scores,
+                                          out_pos, dev.err));
 }
 
 extern "C" tms_status tms_topk_workspace_size(int n_queries, int topk, int64_t n_cand, int64_t* bytes) {
@@ -429,20 +435,19 @@ extern "C" tms_status tms_topk_split(const float* scores, const int64_t* cand_of
     if (st != TMS_OK) return st;
     const int S = topk::slices(dev.sm_count, n_queries, topk, n_cand);
     if (S == 1) {
-        topk::topk_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(
-            scores, cand_offsets, topk, out_scores, out_pos, dev.err);
-        return launch_status(cudaGetLastError());
+        return launch_status(launch_dependent(topk::topk_kernel, dim3(static_cast<unsigned>(n_queries)),
+                                              dim3(topk::kThreads), 0, stream, scores, cand_offsets, topk, out_scores,
+                                              out_pos, dev.err));
     }
     const int64_t need = static_cast<int64_t>(n_queries) * S * topk * 8;
     if (workspace == nullptr || !aligned16(workspace) || workspace_bytes < need) return TMS_ERR_INVALID_ARG;
     auto* ws = static_cast<unsigned long long*>(workspace);
-    topk::topk_slice_kernel<<<static_cast<unsigned>(n_queries * S), topk::kThreads, 0, stream>>>(
-        scores, cand_offsets, topk, S, ws, dev.err);
-    st = launch_status(cudaGetLastError());
+    st = launch_status(launch_dependent(topk::topk_slice_kernel, dim3(static_cast<unsigned>(n_queries * S)),
+                                        dim3(topk::kThreads), 0, stream, scores, cand_offsets, topk, S, ws, dev.err));
     if (st != TMS_OK) return st;
-    topk::topk_merge_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(
-        scores, cand_offsets, topk, S, ws, out_scores, out_pos);
-    return launch_status(cudaGetLastError());
+    return launch_status(launch_dependent(topk::topk_merge_kernel, dim3(static_cast<unsigned>(n_queries)),
+                                          dim3(topk::kThreads), 0, stream, scores, cand_offsets, topk, S, ws,
+                                          out_scores, out_pos));
 }
 
 // ---------------------------------------------------------------------------
@@ -492,9 +497,9 @@ extern "C" tms_status tms_topk_split_noalloc(const float* scores, const int64_t*
     if (st != TMS_OK) return st;
     const int S = topk::slices(dev.sm_count, n_queries, topk, n_cand);
     if (S == 1) {  // one CTA per query: no scratch at all
-        topk::topk_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(
-            scores, cand_offsets, topk, out_scores, out_pos, dev.err);
-        return launch_status(cudaGetLastError());
+        return launch_status(launch_dependent(topk::topk_kernel, dim3(static_cast<unsigned>(n_queries)),
+                                              dim3(topk::kThreads), 0, stream, scores, cand_offsets, topk, out_scores,
+                                              out_pos, dev.err));
     }
     const int64_t need = static_cast<int64_t>(n_queries) * S * topk * 8;
     if (need > topk::kNoAllocScratchBytes) return TMS_ERR_UNSUPPORTED;
@@ -503,11 +508,10 @@ extern "C" tms_status tms_topk_split_noalloc(const float* scores, const int64_t*
     if (st != TMS_OK) return st;
     // Every slice writes all k of its entries (padding included), so nothing
     // from an earlier call is ever read.
-    topk::topk_slice_kernel<<<static_cast<unsigned>(n_queries * S), topk::kThreads, 0, stream>>>(
-        scores, cand_offsets, topk, S, ws, dev.err);
-    st = launch_status(cudaGetLastError());
+    st = launch_status(launch_dependent(topk::topk_slice_kernel, dim3(static_cast<unsigned>(n_queries * S)),
+                                        dim3(topk::kThreads), 0, stream, scores, cand_offsets, topk, S, ws, dev.err));
     if (st != TMS_OK) return st;
-    topk::topk_merge_kernel<<<static_cast<unsigned>(n_queries), topk::kThreads, 0, stream>>>(
-        scores, cand_offsets, topk, S, ws, out_scores, out_pos);
-    return launch_status(cudaGetLastError());
+    return launch_status(launch_dependent(topk::topk_merge_kernel, dim3(static_cast<unsigned>(n_queries)),
+                                          dim3(topk::kThreads), 0, stream, scores, cand_offsets, topk, S, ws,
+                                          out_scores, out_pos));
 }
