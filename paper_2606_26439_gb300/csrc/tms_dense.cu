@@ -21,6 +21,8 @@ constexpr int kF32Chunk = 64;
 __global__ void __launch_bounds__(kF32Warps * 32)
     dense_f32_kernel(const float* __restrict__ queries, const float* __restrict__ tokens, const Args a, int d) {
     extern __shared__ float qs[];  // [32][d + 4]
+    griddep_wait();
+    griddep_launch_dependents();
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int pitch = d + 4;
@@ -173,9 +175,10 @@ tms_status score_dense(const void* queries, tms_dtype dtype, int n_queries, int 
             return launch_status(cudaErrorInvalidValue);
         const int64_t want = (n_cand + dense::kF32Warps - 1) / dense::kF32Warps;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(int64_t(dev.sm_count) * 4, want));
-        dense::dense_f32_kernel<<<static_cast<unsigned>(grid), dense::kF32Warps * 32, smem, stream>>>(
-            static_cast<const float*>(queries), static_cast<const float*>(doc_tokens), a, d);
-        return launch_status(cudaGetLastError());
+        return launch_status(launch_dependent(dense::dense_f32_kernel, dim3(static_cast<unsigned>(grid)),
+                                              dim3(dense::kF32Warps * 32), static_cast<size_t>(smem), stream,
+                                              static_cast<const float*>(queries),
+                                              static_cast<const float*>(doc_tokens), a, d));
     }
     a.nchunks = (d + dense::chunk_elems(dense::kF16) - 1) / dense::chunk_elems(dense::kF16);
     return tune ? dense::tune_tc<1, false, dense::kF16>(dev, queries, dtype, n_queries, nq, d, doc_tokens, n_tokens, a,

@@ -49,6 +49,8 @@ __device__ __forceinline__ float to_f32<float>(float v) { return v; }
 template <typename QT>
 __global__ void lut_kernel(const QT* __restrict__ queries, int d, const float* __restrict__ codebook, int M, int K,
                            float* __restrict__ lut, int64_t total) {
+    griddep_wait();
+    griddep_launch_dependents();
     const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int k = static_cast<int>(idx % K);
@@ -126,6 +128,8 @@ template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel(const Args a) {
     extern __shared__ float lut_s[];  // [M/4][K][4][8]
     __shared__ int next_local;
+    griddep_wait();
+    griddep_launch_dependents();
     const int lane = threadIdx.x & 31;
     const int g = lane >> 3;  // subspace group
     const int i = lane & 7;   // query token within the chunk
@@ -339,6 +343,8 @@ __host__ __device__ constexpr int staged_table_bytes(int M) { return ((M / 8 - 1
 
 template <int M, bool H16>
 __global__ void __launch_bounds__(kWarps * 32, 1) score_kernel_staged(const Args a, int lut_bytes) {
+    griddep_wait();
+    griddep_launch_dependents();
     constexpr int kPiece = kPieceBytes / M;  // tokens per piece
     constexpr int KS = 4096 / M;             // table rows per block
     constexpr int QC = H16 ? 16 : kQC;       // query tokens per chunk
@@ -607,16 +613,16 @@ extern "C" tms_status tms_build_pq_lut(const void* queries, tms_dtype qdtype, in
     const int64_t total = static_cast<int64_t>(n_queries) * nq * m * k;
     const int threads = 256;
     const int64_t blocks = (total + threads - 1) / threads;
+    const dim3 grid(static_cast<unsigned>(blocks)), block(threads);
     if (qdtype == TMS_F16)
-        pq::lut_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(static_cast<const __half*>(queries), d,
-                                                                              codebook, m, k, lut, total);
-    else if (qdtype == TMS_BF16)
-        pq::lut_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-            static_cast<const __nv_bfloat16*>(queries), d, codebook, m, k, lut, total);
-    else
-        pq::lut_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(static_cast<const float*>(queries), d,
-                                                                              codebook, m, k, lut, total);
-    return launch_status(cudaGetLastError());
+        return launch_status(launch_dependent(pq::lut_kernel<__half>, grid, block, 0, stream,
+                                              static_cast<const __half*>(queries), d, codebook, m, k, lut, total));
+    if (qdtype == TMS_BF16)
+        return launch_status(launch_dependent(pq::lut_kernel<__nv_bfloat16>, grid, block, 0, stream,
+                                              static_cast<const __nv_bfloat16*>(queries), d, codebook, m, k, lut,
+                                              total));
+    return launch_status(launch_dependent(pq::lut_kernel<float>, grid, block, 0, stream,
+                                          static_cast<const float*>(queries), d, codebook, m, k, lut, total));
 }
 
 namespace tms {
@@ -666,12 +672,12 @@ tms_status score(const float* lut, int n_queries, int nq, int m, int k, const ui
     const unsigned threads = kWarps * 32;
     auto staged = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
-        if (e == cudaSuccess) kernel<<<grid, threads, smem_st, stream>>>(a, tbl_st);
+        if (e == cudaSuccess) e = launch_dependent(kernel, dim3(grid), dim3(threads), smem_st, stream, a, tbl_st);
         return e;
     };
     auto plain = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) kernel<<<grid, threads, smem, stream>>>(a);
+        if (e == cudaSuccess) e = launch_dependent(kernel, dim3(grid), dim3(threads), smem, stream, a);
         return e;
     };
     cudaError_t e;

@@ -29,6 +29,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "tms_common.cuh"
 #include "tms_internal.h"
 
 namespace tms {
@@ -196,6 +197,8 @@ constexpr int kCsrThreads = 1024;
 __global__ void __launch_bounds__(kCsrThreads) shortlist_csr(const int64_t* __restrict__ co, int nb, int rk,
                                                              int64_t* __restrict__ cor) {
     __shared__ int64_t warp_tot[kCsrThreads / 32];
+    griddep_wait();
+    griddep_launch_dependents();
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     int64_t v[4], sum = 0;
 #pragma unroll
@@ -239,6 +242,8 @@ __global__ void __launch_bounds__(kCsrThreads) shortlist_csr(const int64_t* __re
 __global__ void shortlist_ids(const int32_t* __restrict__ pos, int rk, const int64_t* __restrict__ co,
                               const int64_t* __restrict__ cor, const int32_t* __restrict__ cands, int nb,
                               int32_t* __restrict__ out) {
+    griddep_wait();
+    griddep_launch_dependents();
     const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= static_cast<int64_t>(nb) * rk) return;
     const int i = static_cast<int>(idx / rk);
@@ -304,14 +309,16 @@ void launch(tms_server* s, Slot& sl, std::vector<RequestPtr>& batch) {
                     total_r += n < rk ? n : rk;
                 }
                 if (rc == TMS_OK) {
-                    shortlist_csr<<<1, kCsrThreads, 0, s->stream[st]>>>(sl.d_co[st], nb, rk, sl.d_cor);
-                    if (!cuda_ok(cudaGetLastError())) rc = TMS_ERR_CUDA;
+                    if (!cuda_ok(launch_dependent(shortlist_csr, dim3(1), dim3(kCsrThreads), 0, s->stream[st],
+                                                  sl.d_co[st], nb, rk, sl.d_cor)))
+                        rc = TMS_ERR_CUDA;
                 }
                 if (rc == TMS_OK) {
                     const int64_t n = static_cast<int64_t>(nb) * rk;
-                    shortlist_ids<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s->stream[st]>>>(
-                        sl.d_rtp, rk, sl.d_co[st], sl.d_cor, sl.d_c[st], nb, sl.d_cr);
-                    if (!cuda_ok(cudaGetLastError())) rc = TMS_ERR_CUDA;
+                    if (!cuda_ok(launch_dependent(shortlist_ids, dim3(static_cast<unsigned>((n + 255) / 256)),
+                                                  dim3(256), 0, s->stream[st], sl.d_rtp, rk, sl.d_co[st], sl.d_cor,
+                                                  sl.d_c[st], nb, sl.d_cr)))
+                        rc = TMS_ERR_CUDA;
                 }
                 if (rc == TMS_OK)
                     rc = tms_score_dense(sl.d_q[st], c.dtype, nb, c.nq, c.d, c.doc_tokens, c.n_tokens, c.doc_offsets,
