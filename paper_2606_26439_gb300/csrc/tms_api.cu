@@ -2,7 +2,10 @@
 #include <cudaTypedefs.h>
 
 #include <atomic>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "tms_internal.h"
 
@@ -27,7 +30,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 bool g_have[kMaxDevices] = {};
 DeviceInfo g_info[kMaxDevices];
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 }  // namespace
 
 tms_status current_device(DeviceInfo* out) {
@@ -60,8 +63,9 @@ tms_status current_device(DeviceInfo* out) {
 
 namespace {
 bool load_encoder() {
+    if (g_encode.load(std::memory_order_acquire) != nullptr) return true;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_encode == nullptr) {
+    if (g_encode.load(std::memory_order_relaxed) == nullptr) {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q{};
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
@@ -70,25 +74,72 @@ bool load_encoder() {
             (void)cudaGetLastError();
             return false;
         }
-        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        g_encode.store(reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn), std::memory_order_release);
     }
     return true;
 }
+
+// A tensor map holds only an address, a shape, strides and a box, so equal
+// arguments always encode to the same map: each host thread remembers its
+// last kTmapCache encodings (round-robin replacement).
+struct TmapKey {
+    CUtensorMapDataType dtype;
+    const void* base;
+    uint64_t cols, rows, row_bytes;
+    uint32_t box_cols, box_rows;
+    bool operator==(const TmapKey& o) const {
+        return dtype == o.dtype && base == o.base && cols == o.cols && rows == o.rows && row_bytes == o.row_bytes &&
+               box_cols == o.box_cols && box_rows == o.box_rows;
+    }
+};
+constexpr int kTmapCache = 32;
+struct TmapCache {
+    TmapKey key[kTmapCache];
+    CUtensorMap map[kTmapCache];
+    int used = 0, next = 0;
+};
+thread_local TmapCache t_tmaps;
+
+std::mutex g_smem_mutex;
+std::map<std::pair<int, const void*>, int> g_smem_set;  // (device, kernel) -> largest dynamic smem set
 }  // namespace
+
+cudaError_t set_max_dynamic_smem(const void* kernel, int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    int& have = g_smem_set[{dev, kernel}];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
 
 tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
                           uint64_t rows, uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows) {
     if (!load_encoder()) return TMS_ERR_CUDA;
+    const TmapKey key{dtype, base, cols, rows, row_bytes, box_cols, box_rows};
+    TmapCache& c = t_tmaps;
+    for (int i = 0; i < c.used; ++i)
+        if (c.key[i] == key) {
+            std::memcpy(map, &c.map[i], sizeof(CUtensorMap));
+            return TMS_OK;
+        }
     // A zero-row tensor is not encodable; callers never load from it then,
     // so describe one row (the box reads zero fill beyond it).
     const cuuint64_t dims[2] = {cols, rows > 0 ? rows : 1};
     const cuuint64_t strides[1] = {row_bytes};
     const cuuint32_t box[2] = {box_cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? TMS_OK : TMS_ERR_INVALID_ARG;
+    CUresult r = g_encode.load(std::memory_order_relaxed)(
+        map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return TMS_ERR_INVALID_ARG;
+    const int slot = c.used < kTmapCache ? c.used++ : (c.next++ % kTmapCache);
+    c.key[slot] = key;
+    std::memcpy(&c.map[slot], map, sizeof(CUtensorMap));
+    return TMS_OK;
 }
 
 }  // namespace tms
