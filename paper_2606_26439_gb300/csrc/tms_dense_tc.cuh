@@ -1453,7 +1453,7 @@ tms_status launch_tc(const DeviceInfo& dev, const void* queries, tms_dtype dtype
         kern = str == 256 ? dense_tc_kernel<1, 256, 1, SH, KIND>
                           : (ctas == 2 ? dense_tc_kernel<1, 128, 2, SH, KIND> : dense_tc_kernel<1, 128, 1, SH, KIND>);
     }
-    if (set_max_dynamic_smem(reinterpret_cast<const void*>(kern), smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return launch_status(cudaErrorInvalidValue);
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(dev.sm_count) * ctas, a.n_flat);
     return launch_status(launch_dependent(kern, dim3(static_cast<unsigned>(grid)), dim3(kernel_threads(KIND)),
