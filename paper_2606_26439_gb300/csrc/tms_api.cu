@@ -3,9 +3,7 @@
 
 #include <atomic>
 #include <cstring>
-#include <map>
 #include <mutex>
-#include <utility>
 
 #include "tms_internal.h"
 
@@ -99,22 +97,7 @@ struct TmapCache {
     int used = 0, next = 0;
 };
 thread_local TmapCache t_tmaps;
-
-std::mutex g_smem_mutex;
-std::map<std::pair<int, const void*>, int> g_smem_set;  // (device, kernel) -> largest dynamic smem set
 }  // namespace
-
-cudaError_t set_max_dynamic_smem(const void* kernel, int bytes) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(g_smem_mutex);
-    int& have = g_smem_set[{dev, kernel}];
-    if (bytes <= have) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) have = bytes;
-    return e;
-}
 
 tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
                           uint64_t rows, uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows) {

@@ -170,7 +170,8 @@ tms_status score_dense(const void* queries, tms_dtype dtype, int n_queries, int 
         if (st != TMS_ERR_UNSUPPORTED) return st;
         const int smem = 32 * (d + 4) * 4;
         if (smem > dev.max_smem_optin) return TMS_ERR_UNSUPPORTED;
-        if (set_max_dynamic_smem(reinterpret_cast<const void*>(dense::dense_f32_kernel), smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(dense::dense_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess)
             return launch_status(cudaErrorInvalidValue);
         const int64_t want = (n_cand + dense::kF32Warps - 1) / dense::kF32Warps;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(int64_t(dev.sm_count) * 4, want));

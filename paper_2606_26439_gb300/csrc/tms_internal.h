@@ -36,11 +36,6 @@ tms_status encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, const voi
 // bound of every pipeline wait in SM cycles (0 = the kernels' default) and
 // the fault to inject (0 = none).
 long long debug_wait_budget();
-
-// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for `kernel` on the
-// current device, called only when `bytes` exceeds what was already set
-// there (the attribute is a ceiling, so a larger earlier value serves).
-cudaError_t set_max_dynamic_smem(const void* kernel, int bytes);
 int debug_fault();
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

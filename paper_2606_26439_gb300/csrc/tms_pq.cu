@@ -671,12 +671,12 @@ tms_status score(const float* lut, int n_queries, int nq, int m, int k, const ui
     const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(dev.sm_count, n_cand)));
     const unsigned threads = kWarps * 32;
     auto staged = [&](auto kernel) {
-        cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(kernel), smem_st);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st);
         if (e == cudaSuccess) e = launch_dependent(kernel, dim3(grid), dim3(threads), smem_st, stream, a, tbl_st);
         return e;
     };
     auto plain = [&](auto kernel) {
-        cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(kernel), smem);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess) e = launch_dependent(kernel, dim3(grid), dim3(threads), smem, stream, a);
         return e;
     };
