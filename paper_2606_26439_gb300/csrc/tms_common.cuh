@@ -269,7 +269,9 @@ __device__ __forceinline__ void scale32(float (&v)[32], const float* s) {
 // previous kernel of the stream to complete, and let the next one be
 // scheduled.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // 32 consecutive accumulator columns of this warp's 32 lanes into r,
 // without waiting: r is valid after tmem_ld_wait32 (several loads may be
